@@ -1,0 +1,181 @@
+/*
+ * lbsc: two-component Shan-Chen lattice Boltzmann (D3Q19) on one GB300 GPU.
+ *
+ * The method is that of Schmieschek & Harting, "Contact angle determination
+ * in multicomponent lattice Boltzmann simulations":
+ *   - Sec. 2, Eq. LBeqs     evolution n_k(x + c_k, t+1) - n_k(x, t) = Omega_k
+ *   - Sec. 2                BGK collision Omega_k = -(n_k - n_k^eq)/tau
+ *   - Sec. 2, Eq. Equil     cubic equilibrium n_k^eq(rho, u)
+ *   - Sec. 2, Eq. SCforce   F^a = -psi^a g sum_{x'} psi^abar(x') (x' - x),
+ *                           psi = 1 - exp(-rho), velocity shift tau F / rho
+ *   - Sec. 2                walls: mid-grid bounce-back, and the wall acting as
+ *                           an extra species with a pseudo-density
+ *   - Sec. 3, Eq. geoCA     geometric contact angle from base, height, radius
+ *
+ * Conventions shared by every entry point:
+ *   - Status: every function returns LB_OK (0) or a negative LB_ERR_* code and
+ *     never throws; lb_last_error() gives the message of the last failure.
+ *   - Host arrays are owned by the caller and are only read or written during
+ *     the call. Field arrays hold nx*ny*nz values indexed x + nx*(y + ny*z).
+ *   - Device memory is owned by the context (allocated in lb_init, released
+ *     by lb_free) unless the caller passes its own buffer to lb_init_external.
+ *   - Work is queued on the CUDA stream given at init, in order. lb_step is
+ *     asynchronous; device-side errors surface at the next call that waits
+ *     (lb_moments, lb_contact_angle, lb_save, lb_sync).
+ *   - Lattice units throughout. x and y are periodic; z is periodic unless
+ *     walled off by solid nodes. The default geometry has solid layers at
+ *     z = 0 and z = nz - 1, i.e. mid-grid wall planes at z = 0.5 and
+ *     z = nz - 1.5.
+ */
+#ifndef LBSC_H
+#define LBSC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define LB_OK 0
+#define LB_ERR_ARG (-1)              /* invalid argument (null pointer, bad size or value) */
+#define LB_ERR_CUDA (-2)             /* a CUDA call failed (out of memory, launch failure) */
+#define LB_ERR_NAN (-3)              /* the state holds non-finite populations */
+#define LB_ERR_BARRIER_TIMEOUT (-4)  /* a bounded device-side wait gave up */
+#define LB_ERR_STATE (-5)            /* call not valid in the context's current state */
+#define LB_ERR_UNSUPPORTED (-6)      /* combination of options not built */
+
+/* population storage */
+#define LB_F32 0   /* populations in FP32 */
+#define LB_F16 1   /* FP16 deviations e_k = n_k/zeta_k - rho_ref, FP32 arithmetic */
+#define LB_BF16 2  /* BF16 deviations, as above */
+
+/* neighbour weights G_k of the Shan-Chen force sum */
+#define LB_WEIGHTS_UNIT 0  /* G_k = 1 for the 18 neighbours, as Eq. SCforce is printed */
+#define LB_WEIGHTS_W36 1   /* G_k = 36 zeta_k: 2 on axes, 1 on diagonals */
+
+typedef struct lb_ctx lb_ctx;
+
+/* Model parameters (Sec. 2).
+ *   tau_r, tau_b   BGK relaxation times, > 0.5 (kinematic viscosity (2 tau - 1)/6)
+ *   g_br           inter-component coupling g_{r b}, > 0 repulsive
+ *   eta_wall_r     wall pseudo-density standing in for psi^r at solid nodes (felt by b)
+ *   eta_wall_b     wall pseudo-density standing in for psi^b at solid nodes (felt by r)
+ *                  A signed wettability w maps to (eta_wall_r, eta_wall_b) = (-w, +w):
+ *                  w > 0 repels the r droplet.
+ *   force_weights  LB_WEIGHTS_UNIT or LB_WEIGHTS_W36
+ *   force_scale    multiplier kappa on every force term (1 = the printed force) */
+typedef struct {
+    double tau_r, tau_b, g_br, eta_wall_r, eta_wall_b;
+    int force_weights;
+    double force_scale;
+} lb_params;
+
+/* Geometric droplet measurement (Sec. 3). */
+typedef struct {
+    double theta_deg;     /* contact angle from Eq. geoCA, read as atan2(b/2, r - h) */
+    double theta_fit_deg; /* contact angle of a least-squares sphere through interface points */
+    double h;             /* apex height of the phi = 0 surface above the wall plane z = 0.5 */
+    double b;             /* base diameter at the wall, from r and h */
+    double r;             /* sphere radius from the cap above the reference plane */
+    double base_ref;      /* equivalent-circle diameter of {phi > 0} at the reference plane */
+    double xc, yc, zc;    /* fitted sphere centre */
+    double r_fit;         /* fitted sphere radius */
+    int ok;               /* 1 if theta_deg, h, b, r are defined */
+    int n_points;         /* interface points in the sphere fit */
+} lb_droplet;
+
+/* Create a context on the current CUDA device.
+ * nx, ny, nz >= 1 (nz >= 3 with the default walls); precision LB_F32/LB_F16/LB_BF16.
+ * rho_r, rho_b: host arrays (nx*ny*nz doubles) of initial densities; populations
+ * start at rest equilibrium n_k = zeta_k rho (Eq. Equil at u = 0). Values on
+ * solid nodes are ignored. For 16-bit storage the deviation reference rho_ref
+ * of each component is the mean of its initial density over fluid nodes.
+ * cuda_stream: a cudaStream_t (NULL = legacy default stream) on which all work
+ * of this context is queued. Parameters start as tau = 1, g_br = 0, no wall
+ * force, unit weights, force_scale 1. On error *out is NULL. */
+int lb_init(lb_ctx** out, int nx, int ny, int nz, int precision,
+            const double* rho_r, const double* rho_b, void* cuda_stream);
+
+/* Bytes of device memory lb_init_external needs for this lattice. */
+int lb_required_bytes(int nx, int ny, int nz, int precision, size_t* bytes);
+
+/* As lb_init, but the populations and scratch live in a caller-owned device
+ * buffer of at least lb_required_bytes bytes, 256-byte aligned, that must
+ * outlive the context. The context allocates no population memory itself. */
+int lb_init_external(lb_ctx** out, int nx, int ny, int nz, int precision,
+                     const double* rho_r, const double* rho_b, void* cuda_stream,
+                     void* device_buffer, size_t buffer_bytes);
+
+/* Set the solid mask: host array of nx*ny*nz bytes, 1 = solid (mid-grid
+ * bounce-back, Sec. 2; the wall pseudo-densities act from solid nodes).
+ * A mask with solid layers exactly at z = 0 and z = nz - 1 selects the
+ * planar-wall kernels; any other mask the general kernels. Must leave at
+ * least one fluid node. Populations already on solid nodes are discarded. */
+int lb_set_geometry(lb_ctx* ctx, const uint8_t* solid);
+
+/* Set the model parameters (copied). LB_ERR_ARG if tau <= 0.5, a value is
+ * not finite, or force_weights is unknown. */
+int lb_set_params(lb_ctx* ctx, const lb_params* params);
+
+/* Advance nsteps >= 0 time steps of Eq. LBeqs (moments, psi, Shan-Chen and
+ * wall force, force-shifted cubic equilibrium, BGK, streaming with mid-grid
+ * bounce-back) on the context's stream. Asynchronous. */
+int lb_step(lb_ctx* ctx, int nsteps);
+
+/* Wait for the stream and report a device-side failure, if any. */
+int lb_sync(lb_ctx* ctx);
+
+/* Read densities and conservation sums (Sec. 2, moments). Any output may be NULL.
+ * rho_r, rho_b: nx*ny*nz doubles. u: 3*nx*ny*nz doubles (component-major),
+ * the barycentric velocity (sum_a j^a + F/2)/sum_a rho^a with F the total
+ * Shan-Chen force. cons[8] = {mass_r, mass_b, Px, Py, Pz (sum of j over
+ * nodes and components), non-finite population count, fluid nodes, steps
+ * taken}, summed in FP64 on the device in a fixed order.
+ * Returns LB_ERR_NAN (after filling the outputs) if any population is not finite. */
+int lb_moments(lb_ctx* ctx, double* rho_r, double* rho_b, double* u, double cons[8]);
+
+/* Conservation sums only (cons as in lb_moments), without field copies. */
+int lb_conservation(lb_ctx* ctx, double cons[8]);
+
+/* Contact angle of the r droplet on the bottom wall (Sec. 3): phi = rho_r -
+ * rho_b = 0 located by linear interpolation, apex height h, base b' at the
+ * reference plane `offset` above the wall plane (the paper uses 5 l.u.),
+ * sphere radius r from that cap, base b at the wall from r and h, then theta.
+ * Needs the default wall at z = 0 and offset >= 0. out->ok = 0 (and LB_OK)
+ * when no cap is found. */
+int lb_contact_angle(lb_ctx* ctx, double offset, lb_droplet* out);
+
+/* Checkpoint: bytes of the state, and copies to / from a host buffer of that
+ * size. The state is the population array plus the step counter; params and
+ * geometry are not part of it. */
+int lb_state_bytes(lb_ctx* ctx, size_t* bytes);
+int lb_save(lb_ctx* ctx, void* host, size_t bytes);
+int lb_load(lb_ctx* ctx, const void* host, size_t bytes);
+
+/* Copy the populations to a host array of 2*19*nx*ny*nz doubles laid out
+ * [component][k][z][y][x], decoded to n_k. Velocity order: k = 0 rest,
+ * 1..6 = +x,-x,+y,-y,+z,-z, 7..18 = (1,1,0),(-1,-1,0),(1,-1,0),(-1,1,0),
+ * (1,0,1),(-1,0,-1),(1,0,-1),(-1,0,1),(0,1,1),(0,-1,-1),(0,1,-1),(0,-1,1). */
+int lb_get_populations(lb_ctx* ctx, double* n);
+
+/* Replace the populations from a host array laid out as in lb_get_populations. */
+int lb_set_populations(lb_ctx* ctx, const double* n);
+
+/* Choose the step kernel's tile height (4, 8 or 16 rows of 32 nodes) and the
+ * number of z segments per tile column (0 = automatic). */
+int lb_set_schedule(lb_ctx* ctx, int tile_y, int z_segments);
+
+/* Message of the last failure on this context (or of the last failed lb_init
+ * when ctx is NULL). Never NULL. */
+const char* lb_last_error(const lb_ctx* ctx);
+
+/* Release the context and the device memory it owns. NULL is a no-op. */
+void lb_free(lb_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBSC_H */

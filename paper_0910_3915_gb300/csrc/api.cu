@@ -1,0 +1,711 @@
+// C ABI of the lbsc library (declared in include/lbsc.h): context life
+// cycle, geometry, parameters, stepping (eager launches and CUDA graphs),
+// readback, contact angle and checkpoints.
+#include "../../include/lbsc.h"
+#include "lb_fields.cuh"
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+using namespace lbsc;
+
+namespace lbsc {
+int step_occupancy(int precision, int tile_y, bool general, bool tau_one);
+}
+
+struct lb_ctx {
+    int nx = 0, ny = 0, nz = 0, prec = LB_F32;
+    Layout L{};
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap = nullptr;  // private stream for graph capture
+    int device = 0, nsm = 0;
+    bool owns = false;
+    char* mem = nullptr;
+    size_t mem_bytes = 0;
+    void* f[2] = {nullptr, nullptr};
+    int cur = 0;
+    uint32_t* nbmask = nullptr;
+    bool general = false;
+    int zlo = 0, zhi = 0;
+    long long fluid_nodes = 0;
+    double* part = nullptr;
+    double* red = nullptr;
+    double* h_red = nullptr;  // pinned
+    Scratch W{};
+    lb_params prm{};
+    KParams kp{};
+    int tile_y = 8, nseg_req = 0;
+    int nseg_cache = 0;  // segments per tile column for the current schedule (0 = not computed)
+    long long steps = 0;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    static constexpr int kGraphSteps = 32;
+    std::string err;
+};
+
+static thread_local std::string g_init_err;
+
+static int fail(lb_ctx* c, int code, const std::string& msg)
+{
+    if (c) c->err = msg;
+    else g_init_err = msg;
+    return code;
+}
+
+static int cuda_fail(lb_ctx* c, cudaError_t e, const char* where)
+{
+    return fail(c, LB_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define LB_CUDA(c, call)                                   \
+    do {                                                   \
+        cudaError_t e_ = (call);                           \
+        if (e_ != cudaSuccess) return cuda_fail(c, e_, #call); \
+    } while (0)
+
+static size_t elem_size(int prec) { return prec == LB_F32 ? 4 : 2; }
+static size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
+
+static Layout make_layout(int nx, int ny, int nz)
+{
+    Layout L;
+    L.nx = nx;
+    L.ny = ny;
+    L.nz = nz;
+    L.px = (nx + 31) / 32 * 32;
+    L.plane = (long long)L.px * ny;
+    L.slot = (L.plane * nz + 127) / 128 * 128;
+    return L;
+}
+
+// memory plan: [f0][f1][nbmask][scratch fields][partials][reduction out]
+struct Plan {
+    size_t f, mask, scratch, part, red, total;
+};
+static Plan make_plan(const Layout& L, int prec)
+{
+    Plan p;
+    const long long N = (long long)L.nx * L.ny * L.nz;
+    p.f = align256((size_t)2 * Q * L.slot * elem_size(prec));
+    p.mask = align256((size_t)L.plane * L.nz * sizeof(uint32_t));
+    p.scratch = align256((size_t)10 * N * sizeof(float));
+    p.part = align256((size_t)kRedBlocks * kAngleVals * sizeof(double));
+    p.red = align256(64 * sizeof(double));
+    p.total = 2 * p.f + p.mask + p.scratch + p.part + p.red;
+    return p;
+}
+
+static bool dims_ok(int nx, int ny, int nz) { return nx >= 1 && ny >= 1 && nz >= 1 && (long long)nx * ny * nz <= (1LL << 34); }
+
+static FieldArgs field_args(const lb_ctx* c)
+{
+    FieldArgs F;
+    F.L = c->L;
+    F.P = c->kp;
+    F.general = c->general ? 1 : 0;
+    F.nbmask = c->nbmask;
+    return F;
+}
+
+static void drop_graphs(lb_ctx* c)
+{
+    c->nseg_cache = 0;
+    for (int i = 0; i < 2; ++i)
+        if (c->graph[i]) {
+            cudaGraphExecDestroy(c->graph[i]);
+            c->graph[i] = nullptr;
+        }
+}
+
+static void set_kparams(lb_ctx* c)
+{
+    const lb_params& p = c->prm;
+    c->kp.gk = (float)(p.g_br * p.force_scale);
+    c->kp.Gax = p.force_weights == LB_WEIGHTS_W36 ? 2.0f : 1.0f;
+    c->kp.Gdi = 1.0f;
+    c->kp.tau[0] = (float)p.tau_r;
+    c->kp.tau[1] = (float)p.tau_b;
+    c->kp.itau[0] = (float)(1.0 / p.tau_r);
+    c->kp.itau[1] = (float)(1.0 / p.tau_b);
+    c->kp.eta[0] = (float)p.eta_wall_r;
+    c->kp.eta[1] = (float)p.eta_wall_b;
+}
+
+static bool tau_one(const lb_ctx* c) { return c->prm.tau_r == 1.0 && c->prm.tau_b == 1.0; }
+
+static int nseg_for(lb_ctx* c, int ncol)
+{
+    if (c->nseg_cache > 0) return c->nseg_cache;
+    const int nzf = c->zhi - c->zlo;
+    if (c->nseg_req > 0) return c->nseg_cache = (c->nseg_req < nzf ? c->nseg_req : nzf);
+    int occ = step_occupancy(c->prec, c->tile_y, c->general, tau_one(c));
+    if (occ < 1) occ = 1;
+    const long long target = (long long)c->nsm * occ;
+    long long s = (target + ncol - 1) / ncol;
+    const long long smax = nzf / 16 > 1 ? nzf / 16 : 1;  // segments of at least 16 planes
+    if (s > smax) s = smax;
+    if (s < 1) s = 1;
+    c->nseg_cache = (int)s;
+    return (int)s;
+}
+
+template <class S>
+static StepArgs<S> step_args(lb_ctx* c, int src)
+{
+    StepArgs<S> A;
+    A.src = (const S*)c->f[src];
+    A.dst = (S*)c->f[1 - src];
+    A.nbmask = c->nbmask;
+    A.L = c->L;
+    A.P = c->kp;
+    A.tiles_x = (c->nx + 31) / 32;
+    A.tiles_y = (c->ny + c->tile_y - 1) / c->tile_y;
+    A.zlo = c->zlo;
+    A.zhi = c->zhi;
+    A.nseg = nseg_for(c, A.tiles_x * A.tiles_y);
+    return A;
+}
+
+static cudaError_t launch_steps(lb_ctx* c, int n, int& parity, cudaStream_t st)
+{
+    const bool t1 = tau_one(c);
+    for (int i = 0; i < n; ++i) {
+        cudaError_t e;
+        switch (c->prec) {
+        case LB_F32: e = launch_step<float>(step_args<float>(c, parity), c->tile_y, c->general, t1, st); break;
+        case LB_F16: e = launch_step<__half>(step_args<__half>(c, parity), c->tile_y, c->general, t1, st); break;
+        default: e = launch_step<__nv_bfloat16>(step_args<__nv_bfloat16>(c, parity), c->tile_y, c->general, t1, st); break;
+        }
+        if (e != cudaSuccess) return e;
+        parity ^= 1;
+    }
+    return cudaSuccess;
+}
+
+template <class S>
+static cudaError_t run_init(lb_ctx* c, const double* drr, const double* drb)
+{
+    return launch_init<S>(field_args(c), (S*)c->f[0], drr, drb, c->stream);
+}
+
+static int planar_default(lb_ctx* c)
+{
+    if (c->nz >= 3) {
+        c->general = false;
+        c->zlo = 1;
+        c->zhi = c->nz - 1;
+        c->fluid_nodes = (long long)c->nx * c->ny * (c->nz - 2);
+    } else {
+        // too thin for walls: fully periodic through an all-fluid mask
+        LB_CUDA(c, cudaMemsetAsync(c->nbmask, 0, (size_t)c->L.plane * c->nz * sizeof(uint32_t), c->stream));
+        c->general = true;
+        c->zlo = 0;
+        c->zhi = c->nz;
+        c->fluid_nodes = (long long)c->nx * c->ny * c->nz;
+    }
+    return LB_OK;
+}
+
+static int init_common(lb_ctx** out, int nx, int ny, int nz, int precision, const double* rho_r,
+                       const double* rho_b, void* stream, void* ext, size_t ext_bytes)
+{
+    if (!out) return fail(nullptr, LB_ERR_ARG, "lb_init: out is NULL");
+    *out = nullptr;
+    if (!dims_ok(nx, ny, nz)) return fail(nullptr, LB_ERR_ARG, "lb_init: bad lattice dimensions");
+    if (precision != LB_F32 && precision != LB_F16 && precision != LB_BF16)
+        return fail(nullptr, LB_ERR_ARG, "lb_init: unknown precision");
+    if (!rho_r || !rho_b) return fail(nullptr, LB_ERR_ARG, "lb_init: density array is NULL");
+    const long long N = (long long)nx * ny * nz;
+    for (long long i = 0; i < N; ++i)
+        if (!std::isfinite(rho_r[i]) || !std::isfinite(rho_b[i]) || rho_r[i] < 0 || rho_b[i] < 0)
+            return fail(nullptr, LB_ERR_ARG, "lb_init: densities must be finite and non-negative");
+
+    lb_ctx* c = new (std::nothrow) lb_ctx();
+    if (!c) return fail(nullptr, LB_ERR_CUDA, "lb_init: out of host memory");
+    c->nx = nx;
+    c->ny = ny;
+    c->nz = nz;
+    c->prec = precision;
+    c->stream = (cudaStream_t)stream;
+    c->L = make_layout(nx, ny, nz);
+    const Plan p = make_plan(c->L, precision);
+    auto bail = [&](int code, const std::string& msg) {
+        g_init_err = msg;
+        lb_free(c);
+        return code;
+    };
+    cudaError_t e = cudaGetDevice(&c->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, c->device);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return bail(LB_ERR_CUDA, std::string("lb_init: ") + cudaGetErrorString(e));
+    if (ext) {
+        if (ext_bytes < p.total || ((uintptr_t)ext & 255u))
+            return bail(LB_ERR_ARG, "lb_init_external: buffer too small or not 256-byte aligned");
+        c->mem = (char*)ext;
+        c->owns = false;
+    } else {
+        e = cudaMalloc((void**)&c->mem, p.total);
+        if (e != cudaSuccess) return bail(LB_ERR_CUDA, std::string("lb_init: cudaMalloc: ") + cudaGetErrorString(e));
+        c->owns = true;
+    }
+    c->mem_bytes = p.total;
+    char* q = c->mem;
+    c->f[0] = q;
+    q += p.f;
+    c->f[1] = q;
+    q += p.f;
+    c->nbmask = (uint32_t*)q;
+    q += p.mask;
+    float* sf = (float*)q;
+    q += p.scratch;
+    c->part = (double*)q;
+    q += p.part;
+    c->red = (double*)q;
+    const long long Nn = N;
+    c->W.rho[0] = sf + 0 * Nn;
+    c->W.rho[1] = sf + 1 * Nn;
+    for (int d = 0; d < 3; ++d) c->W.j[d] = sf + (2 + d) * Nn;
+    c->W.psi[0] = sf + 5 * Nn;
+    c->W.psi[1] = sf + 6 * Nn;
+    for (int d = 0; d < 3; ++d) c->W.u[d] = sf + (7 + d) * Nn;
+    e = cudaMallocHost((void**)&c->h_red, 64 * sizeof(double));
+    if (e != cudaSuccess) return bail(LB_ERR_CUDA, std::string("lb_init: cudaMallocHost: ") + cudaGetErrorString(e));
+
+    if (planar_default(c) != LB_OK) return bail(LB_ERR_CUDA, c->err);
+    // 16-bit deviation references: mean initial density over fluid nodes
+    double sum[2] = {0, 0};
+    long long cnt = 0;
+    for (int z = c->zlo; z < c->zhi; ++z)
+        for (long long i = (long long)z * nx * ny; i < (long long)(z + 1) * nx * ny; ++i) {
+            sum[0] += rho_r[i];
+            sum[1] += rho_b[i];
+            ++cnt;
+        }
+    c->kp.ref[0] = precision == LB_F32 ? 0.f : (float)(sum[0] / (double)cnt);
+    c->kp.ref[1] = precision == LB_F32 ? 0.f : (float)(sum[1] / (double)cnt);
+    c->prm = lb_params{1.0, 1.0, 0.0, 0.0, 0.0, LB_WEIGHTS_UNIT, 1.0};
+    set_kparams(c);
+
+    // stage the densities in the scratch fields (FP64: 2 N doubles fit in 10 N floats)
+    double* drr = (double*)sf;
+    double* drb = drr + N;
+    e = cudaMemcpyAsync(drr, rho_r, N * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(drb, rho_b, N * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) {
+        switch (precision) {
+        case LB_F32: e = run_init<float>(c, drr, drb); break;
+        case LB_F16: e = run_init<__half>(c, drr, drb); break;
+        default: e = run_init<__nv_bfloat16>(c, drr, drb); break;
+        }
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return bail(LB_ERR_CUDA, std::string("lb_init: ") + cudaGetErrorString(e));
+    *out = c;
+    return LB_OK;
+}
+
+extern "C" {
+
+int lb_init(lb_ctx** out, int nx, int ny, int nz, int precision, const double* rho_r, const double* rho_b,
+            void* cuda_stream)
+{
+    return init_common(out, nx, ny, nz, precision, rho_r, rho_b, cuda_stream, nullptr, 0);
+}
+
+int lb_required_bytes(int nx, int ny, int nz, int precision, size_t* bytes)
+{
+    if (!bytes || !dims_ok(nx, ny, nz)) return fail(nullptr, LB_ERR_ARG, "lb_required_bytes: bad argument");
+    if (precision != LB_F32 && precision != LB_F16 && precision != LB_BF16)
+        return fail(nullptr, LB_ERR_ARG, "lb_required_bytes: unknown precision");
+    *bytes = make_plan(make_layout(nx, ny, nz), precision).total;
+    return LB_OK;
+}
+
+int lb_init_external(lb_ctx** out, int nx, int ny, int nz, int precision, const double* rho_r,
+                     const double* rho_b, void* cuda_stream, void* device_buffer, size_t buffer_bytes)
+{
+    if (!device_buffer) return fail(nullptr, LB_ERR_ARG, "lb_init_external: device_buffer is NULL");
+    return init_common(out, nx, ny, nz, precision, rho_r, rho_b, cuda_stream, device_buffer, buffer_bytes);
+}
+
+int lb_set_geometry(lb_ctx* c, const uint8_t* solid)
+{
+    if (!c || !solid) return fail(c, LB_ERR_ARG, "lb_set_geometry: NULL argument");
+    const int nx = c->nx, ny = c->ny, nz = c->nz;
+    const long long N = (long long)nx * ny * nz, NP = (long long)nx * ny;
+    long long fluid = 0;
+    bool planar = nz >= 3;
+    for (long long i = 0; i < N; ++i) {
+        const bool s = solid[i] != 0;
+        fluid += !s;
+        const long long z = i / NP;
+        if (s != (z == 0 || z == nz - 1)) planar = false;
+    }
+    if (fluid == 0) return fail(c, LB_ERR_ARG, "lb_set_geometry: no fluid node");
+    LB_CUDA(c, cudaStreamSynchronize(c->stream));
+    drop_graphs(c);
+    c->fluid_nodes = fluid;
+    if (planar) {
+        c->general = false;
+        c->zlo = 1;
+        c->zhi = nz - 1;
+        return LB_OK;
+    }
+    std::vector<uint32_t> m((size_t)c->L.plane * nz, 0u);
+    auto at = [&](int x, int y, int z) { return solid[(long long)x + (long long)nx * (y + (long long)ny * z)] != 0; };
+    for (int z = 0; z < nz; ++z)
+        for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x) {
+                uint32_t b = at(x, y, z) ? kSelfSolid : 0u;
+                for (int k = 1; k < Q; ++k)
+                    if (at(wrapi(x + cx(k), nx), wrapi(y + cy(k), ny), wrapi(z + cz(k), nz))) b |= 1u << k;
+                m[(size_t)z * c->L.plane + (size_t)y * c->L.px + x] = b;
+            }
+    LB_CUDA(c, cudaMemcpy(c->nbmask, m.data(), m.size() * sizeof(uint32_t), cudaMemcpyHostToDevice));
+    c->general = true;
+    c->zlo = 0;
+    c->zhi = nz;
+    return LB_OK;
+}
+
+int lb_set_params(lb_ctx* c, const lb_params* p)
+{
+    if (!c || !p) return fail(c, LB_ERR_ARG, "lb_set_params: NULL argument");
+    const double v[] = {p->tau_r, p->tau_b, p->g_br, p->eta_wall_r, p->eta_wall_b, p->force_scale};
+    for (double x : v)
+        if (!std::isfinite(x)) return fail(c, LB_ERR_ARG, "lb_set_params: non-finite value");
+    if (p->tau_r <= 0.5 || p->tau_b <= 0.5) return fail(c, LB_ERR_ARG, "lb_set_params: tau must exceed 1/2");
+    if (p->force_weights != LB_WEIGHTS_UNIT && p->force_weights != LB_WEIGHTS_W36)
+        return fail(c, LB_ERR_ARG, "lb_set_params: unknown force_weights");
+    drop_graphs(c);
+    c->prm = *p;
+    set_kparams(c);
+    return LB_OK;
+}
+
+int lb_set_schedule(lb_ctx* c, int tile_y, int z_segments)
+{
+    if (!c) return fail(c, LB_ERR_ARG, "lb_set_schedule: NULL context");
+    if ((tile_y != 4 && tile_y != 8 && tile_y != 16) || z_segments < 0)
+        return fail(c, LB_ERR_ARG, "lb_set_schedule: tile_y must be 4, 8 or 16 and z_segments >= 0");
+    drop_graphs(c);
+    c->tile_y = tile_y;
+    c->nseg_req = z_segments;
+    return LB_OK;
+}
+
+int lb_step(lb_ctx* c, int nsteps)
+{
+    if (!c || nsteps < 0) return fail(c, LB_ERR_ARG, "lb_step: bad argument");
+    const int G = lb_ctx::kGraphSteps;
+    int n = nsteps;
+    if (n >= G) {
+        int& par = c->cur;
+        if (!c->graph[par]) {
+            cudaGraph_t g = nullptr;
+            nseg_for(c, ((c->nx + 31) / 32) * ((c->ny + c->tile_y - 1) / c->tile_y));
+            LB_CUDA(c, cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
+            int p2 = par;
+            cudaError_t e = launch_steps(c, G, p2, c->cap);
+            cudaError_t e2 = cudaStreamEndCapture(c->cap, &g);
+            if (e != cudaSuccess) return cuda_fail(c, e, "lb_step: capture");
+            if (e2 != cudaSuccess) return cuda_fail(c, e2, "lb_step: end capture");
+            e = cudaGraphInstantiate(&c->graph[par], g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) return cuda_fail(c, e, "lb_step: graph instantiate");
+        }
+        while (n >= G) {
+            LB_CUDA(c, cudaGraphLaunch(c->graph[par], c->stream));
+            n -= G;  // G is even: parity unchanged
+        }
+    }
+    int par = c->cur;
+    cudaError_t e = launch_steps(c, n, par, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "lb_step: launch");
+    c->cur = par;
+    c->steps += nsteps;
+    return LB_OK;
+}
+
+int lb_sync(lb_ctx* c)
+{
+    if (!c) return fail(c, LB_ERR_ARG, "lb_sync: NULL context");
+    LB_CUDA(c, cudaStreamSynchronize(c->stream));
+    LB_CUDA(c, cudaGetLastError());
+    return LB_OK;
+}
+
+}  // extern "C"
+
+template <class S>
+static cudaError_t run_cons(lb_ctx* c)
+{
+    return launch_conservation<S>(field_args(c), (const S*)c->f[c->cur], c->part, c->red, c->stream);
+}
+template <class S>
+static cudaError_t run_fields(lb_ctx* c, bool vel)
+{
+    return launch_fields<S>(field_args(c), (const S*)c->f[c->cur], c->W, vel, c->stream);
+}
+
+static cudaError_t dispatch_cons(lb_ctx* c)
+{
+    switch (c->prec) {
+    case LB_F32: return run_cons<float>(c);
+    case LB_F16: return run_cons<__half>(c);
+    default: return run_cons<__nv_bfloat16>(c);
+    }
+}
+static cudaError_t dispatch_fields(lb_ctx* c, bool vel)
+{
+    switch (c->prec) {
+    case LB_F32: return run_fields<float>(c, vel);
+    case LB_F16: return run_fields<__half>(c, vel);
+    default: return run_fields<__nv_bfloat16>(c, vel);
+    }
+}
+
+extern "C" {
+
+int lb_conservation(lb_ctx* c, double cons[8])
+{
+    if (!c || !cons) return fail(c, LB_ERR_ARG, "lb_conservation: NULL argument");
+    LB_CUDA(c, dispatch_cons(c));
+    LB_CUDA(c, cudaMemcpyAsync(c->h_red, c->red, 8 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    LB_CUDA(c, cudaStreamSynchronize(c->stream));
+    for (int i = 0; i < 7; ++i) cons[i] = c->h_red[i];
+    cons[7] = (double)c->steps;
+    if (cons[5] > 0) return fail(c, LB_ERR_NAN, "non-finite populations in the state");
+    return LB_OK;
+}
+
+int lb_moments(lb_ctx* c, double* rho_r, double* rho_b, double* u, double cons[8])
+{
+    if (!c) return fail(c, LB_ERR_ARG, "lb_moments: NULL context");
+    const long long N = (long long)c->nx * c->ny * c->nz;
+    if (rho_r || rho_b || u) {
+        LB_CUDA(c, dispatch_fields(c, u != nullptr));
+        std::vector<float> tmp((size_t)N);
+        auto pull = [&](const float* src, double* dst) -> int {
+            LB_CUDA(c, cudaMemcpyAsync(tmp.data(), src, N * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+            LB_CUDA(c, cudaStreamSynchronize(c->stream));
+            for (long long i = 0; i < N; ++i) dst[i] = tmp[i];
+            return LB_OK;
+        };
+        int rc;
+        if (rho_r && (rc = pull(c->W.rho[0], rho_r)) != LB_OK) return rc;
+        if (rho_b && (rc = pull(c->W.rho[1], rho_b)) != LB_OK) return rc;
+        if (u)
+            for (int d = 0; d < 3; ++d)
+                if ((rc = pull(c->W.u[d], u + d * N)) != LB_OK) return rc;
+    }
+    double tmp[8];
+    int rc = lb_conservation(c, tmp);
+    if (cons) memcpy(cons, tmp, sizeof(tmp));
+    return rc;
+}
+
+static int solve4(double M[4][4], double v[4], double s[4])
+{
+    for (int col = 0; col < 4; ++col) {
+        int piv = col;
+        for (int r = col + 1; r < 4; ++r)
+            if (std::fabs(M[r][col]) > std::fabs(M[piv][col])) piv = r;
+        if (std::fabs(M[piv][col]) < 1e-300) return -1;
+        if (piv != col) {
+            for (int k = 0; k < 4; ++k) std::swap(M[col][k], M[piv][k]);
+            std::swap(v[col], v[piv]);
+        }
+        for (int r = col + 1; r < 4; ++r) {
+            const double f = M[r][col] / M[col][col];
+            for (int k = col; k < 4; ++k) M[r][k] -= f * M[col][k];
+            v[r] -= f * v[col];
+        }
+    }
+    for (int r = 3; r >= 0; --r) {
+        double a = v[r];
+        for (int k = r + 1; k < 4; ++k) a -= M[r][k] * s[k];
+        s[r] = a / M[r][r];
+    }
+    return 0;
+}
+
+int lb_contact_angle(lb_ctx* c, double offset, lb_droplet* out)
+{
+    if (!c || !out || !(offset >= 0) || !std::isfinite(offset)) return fail(c, LB_ERR_ARG, "lb_contact_angle: bad argument");
+    memset(out, 0, sizeof(*out));
+    const double zw = 0.5, zref = zw + offset;
+    LB_CUDA(c, dispatch_fields(c, false));
+    LB_CUDA(c, launch_angle(field_args(c), c->W, zref, c->part, c->red, c->stream));
+    LB_CUDA(c, cudaMemcpyAsync(c->h_red, c->red, kAngleVals * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    LB_CUDA(c, cudaStreamSynchronize(c->stream));
+    const double* v = c->h_red;
+    const double top = v[0], area = v[1];
+    const int npts = (int)v[2];
+    const double h = top - zw;
+    const double pi = 3.14159265358979323846;
+    const double bref = 2.0 * std::sqrt(area / pi), hp = h - offset;
+    out->h = h;
+    out->base_ref = bref;
+    const int z0 = (int)std::floor(zref);
+    if (top > -1e299 && z0 >= 0 && z0 + 1 < c->nz && hp > 0 && bref > 0) {
+        // cap above the reference plane: height hp, base bref -> sphere radius (Fig. 2 relation)
+        const double r = (0.25 * bref * bref + hp * hp) / (2.0 * hp);
+        const double arg = r * r - (r - h) * (r - h);
+        const double b = 2.0 * std::sqrt(arg > 0 ? arg : 0.0);
+        out->r = r;
+        out->b = b;
+        out->theta_deg = std::atan2(0.5 * b, r - h) * 180.0 / pi;
+        out->ok = 1;
+    }
+    out->n_points = npts;
+    if (npts >= 4) {
+        double M[4][4], rhs[4], s[4];
+        int m = 3;
+        for (int r = 0; r < 4; ++r)
+            for (int q = r; q < 4; ++q) M[r][q] = M[q][r] = v[m++];
+        for (int r = 0; r < 4; ++r) rhs[r] = v[13 + r];
+        if (solve4(M, rhs, s) == 0) {
+            const double R2 = s[3] + s[0] * s[0] + s[1] * s[1] + s[2] * s[2];
+            if (R2 > 0) {
+                const double R = std::sqrt(R2);
+                double cth = -(s[2] - zw) / R;
+                cth = cth > 1 ? 1 : (cth < -1 ? -1 : cth);
+                out->xc = s[0];
+                out->yc = s[1];
+                out->zc = s[2];
+                out->r_fit = R;
+                out->theta_fit_deg = std::acos(cth) * 180.0 / pi;
+            }
+        }
+    }
+    return LB_OK;
+}
+
+struct StateHeader {
+    char magic[8];
+    int nx, ny, nz, prec;
+    long long steps;
+    long long payload;
+};
+
+static size_t payload_bytes(const lb_ctx* c) { return (size_t)2 * Q * c->L.slot * elem_size(c->prec); }
+
+int lb_state_bytes(lb_ctx* c, size_t* bytes)
+{
+    if (!c || !bytes) return fail(c, LB_ERR_ARG, "lb_state_bytes: NULL argument");
+    *bytes = sizeof(StateHeader) + payload_bytes(c);
+    return LB_OK;
+}
+
+int lb_save(lb_ctx* c, void* host, size_t bytes)
+{
+    if (!c || !host) return fail(c, LB_ERR_ARG, "lb_save: NULL argument");
+    const size_t pb = payload_bytes(c);
+    if (bytes < sizeof(StateHeader) + pb) return fail(c, LB_ERR_ARG, "lb_save: buffer too small");
+    StateHeader h;
+    memcpy(h.magic, "LBSCST01", 8);
+    h.nx = c->nx;
+    h.ny = c->ny;
+    h.nz = c->nz;
+    h.prec = c->prec;
+    h.steps = c->steps;
+    h.payload = (long long)pb;
+    memcpy(host, &h, sizeof(h));
+    LB_CUDA(c, cudaMemcpyAsync((char*)host + sizeof(h), c->f[c->cur], pb, cudaMemcpyDeviceToHost, c->stream));
+    LB_CUDA(c, cudaStreamSynchronize(c->stream));
+    return LB_OK;
+}
+
+int lb_load(lb_ctx* c, const void* host, size_t bytes)
+{
+    if (!c || !host) return fail(c, LB_ERR_ARG, "lb_load: NULL argument");
+    const size_t pb = payload_bytes(c);
+    if (bytes < sizeof(StateHeader)) return fail(c, LB_ERR_ARG, "lb_load: truncated state");
+    StateHeader h;
+    memcpy(&h, host, sizeof(h));
+    if (memcmp(h.magic, "LBSCST01", 8) != 0) return fail(c, LB_ERR_ARG, "lb_load: not an lbsc state");
+    if (h.nx != c->nx || h.ny != c->ny || h.nz != c->nz || h.prec != c->prec || h.payload != (long long)pb)
+        return fail(c, LB_ERR_ARG, "lb_load: state does not match this context");
+    if (bytes < sizeof(StateHeader) + pb) return fail(c, LB_ERR_ARG, "lb_load: truncated state");
+    LB_CUDA(c, cudaMemcpyAsync(c->f[c->cur], (const char*)host + sizeof(h), pb, cudaMemcpyHostToDevice, c->stream));
+    LB_CUDA(c, cudaStreamSynchronize(c->stream));
+    c->steps = h.steps;
+    return LB_OK;
+}
+
+}  // extern "C"
+
+template <class S>
+static cudaError_t run_get(lb_ctx* c, double* d)
+{
+    return launch_get_pop<S>(field_args(c), (const S*)c->f[c->cur], d, c->stream);
+}
+template <class S>
+static cudaError_t run_set(lb_ctx* c, const double* d)
+{
+    return launch_set_pop<S>(field_args(c), (S*)c->f[c->cur], d, c->stream);
+}
+
+extern "C" {
+
+int lb_get_populations(lb_ctx* c, double* n)
+{
+    if (!c || !n) return fail(c, LB_ERR_ARG, "lb_get_populations: NULL argument");
+    const size_t bytes = (size_t)2 * Q * c->nx * c->ny * c->nz * sizeof(double);
+    double* d = nullptr;
+    LB_CUDA(c, cudaMalloc((void**)&d, bytes));
+    cudaError_t e;
+    switch (c->prec) {
+    case LB_F32: e = run_get<float>(c, d); break;
+    case LB_F16: e = run_get<__half>(c, d); break;
+    default: e = run_get<__nv_bfloat16>(c, d); break;
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(n, d, bytes, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    cudaFree(d);
+    if (e != cudaSuccess) return cuda_fail(c, e, "lb_get_populations");
+    return LB_OK;
+}
+
+int lb_set_populations(lb_ctx* c, const double* n)
+{
+    if (!c || !n) return fail(c, LB_ERR_ARG, "lb_set_populations: NULL argument");
+    const size_t bytes = (size_t)2 * Q * c->nx * c->ny * c->nz * sizeof(double);
+    double* d = nullptr;
+    LB_CUDA(c, cudaMalloc((void**)&d, bytes));
+    cudaError_t e = cudaMemcpyAsync(d, n, bytes, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) {
+        switch (c->prec) {
+        case LB_F32: e = run_set<float>(c, d); break;
+        case LB_F16: e = run_set<__half>(c, d); break;
+        default: e = run_set<__nv_bfloat16>(c, d); break;
+        }
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    cudaFree(d);
+    if (e != cudaSuccess) return cuda_fail(c, e, "lb_set_populations");
+    return LB_OK;
+}
+
+const char* lb_last_error(const lb_ctx* c)
+{
+    if (!c) return g_init_err.c_str();
+    return c->err.c_str();
+}
+
+void lb_free(lb_ctx* c)
+{
+    if (!c) return;
+    if (c->stream || c->mem) cudaStreamSynchronize(c->stream);
+    drop_graphs(c);
+    if (c->owns && c->mem) cudaFree(c->mem);
+    if (c->h_red) cudaFreeHost(c->h_red);
+    if (c->cap) cudaStreamDestroy(c->cap);
+    delete c;
+}
+
+}  // extern "C"

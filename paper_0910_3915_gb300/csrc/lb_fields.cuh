@@ -1,0 +1,42 @@
+// Declarations shared by the kernels' translation units and the C-ABI layer.
+#pragma once
+
+#include "lb_internal.cuh"
+
+namespace lbsc {
+
+constexpr int kRedThreads = 256;  // threads per reduction block
+constexpr int kRedBlocks = 512;   // fixed grid of the reductions: fixed summation order
+constexpr int kAngleVals = 17;    // contact-angle partial sums per block
+
+// Geometry and parameters for the non-step kernels.
+struct FieldArgs {
+    Layout L;
+    KParams P;
+    int general;                    // 0: solid layers z = 0 and z = nz-1; 1: nbmask
+    const uint32_t* nbmask;
+};
+
+// Unpadded float fields (index x + nx*(y + ny*z)) used by readback kernels.
+struct Scratch {
+    float* rho[2];
+    float* j[3];
+    float* psi[2];
+    float* u[3];
+};
+
+template <class S>
+cudaError_t launch_step(const StepArgs<S>& A, int tile_y, bool general, bool tau_one, cudaStream_t st);
+template <class S>
+cudaError_t launch_init(const FieldArgs& F, S* f, const double* rr, const double* rb, cudaStream_t st);
+template <class S>
+cudaError_t launch_conservation(const FieldArgs& F, const S* f, double* part, double* out, cudaStream_t st);
+template <class S>
+cudaError_t launch_fields(const FieldArgs& F, const S* f, const Scratch& W, bool velocity, cudaStream_t st);
+cudaError_t launch_angle(const FieldArgs& F, const Scratch& W, double zref, double* part, double* out, cudaStream_t st);
+template <class S>
+cudaError_t launch_get_pop(const FieldArgs& F, const S* f, double* out, cudaStream_t st);
+template <class S>
+cudaError_t launch_set_pop(const FieldArgs& F, S* f, const double* in, cudaStream_t st);
+
+}  // namespace lbsc

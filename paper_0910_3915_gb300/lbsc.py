@@ -1,0 +1,268 @@
+"""Python binding of the lbsc C ABI (include/lbsc.h): argument marshalling only.
+
+Every computation runs in the CUDA library ``liblbsc.so`` next to this file;
+this module converts numpy arrays to pointers, passes a CUDA stream handle
+and turns status codes into exceptions. There is no CPU fallback: if the
+library is missing or cannot be loaded, ``load()`` raises.
+
+Field arrays are numpy arrays of shape (nz, ny, nx) (x fastest), i.e. the
+C ABI's index x + nx*(y + ny*z).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "liblbsc.so")
+
+LB_OK = 0
+LB_ERR_ARG = -1
+LB_ERR_CUDA = -2
+LB_ERR_NAN = -3
+LB_ERR_BARRIER_TIMEOUT = -4
+LB_ERR_STATE = -5
+LB_ERR_UNSUPPORTED = -6
+
+LB_F32, LB_F16, LB_BF16 = 0, 1, 2
+PRECISIONS = {"f32": LB_F32, "f16": LB_F16, "bf16": LB_BF16}
+LB_WEIGHTS_UNIT, LB_WEIGHTS_W36 = 0, 1
+
+
+class LBError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"lbsc error {code}: {msg}")
+        self.code = code
+
+
+class lb_params(ctypes.Structure):
+    _fields_ = [("tau_r", ctypes.c_double), ("tau_b", ctypes.c_double), ("g_br", ctypes.c_double),
+                ("eta_wall_r", ctypes.c_double), ("eta_wall_b", ctypes.c_double),
+                ("force_weights", ctypes.c_int), ("force_scale", ctypes.c_double)]
+
+
+class lb_droplet(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in
+                ("theta_deg", "theta_fit_deg", "h", "b", "r", "base_ref", "xc", "yc", "zc", "r_fit")] + \
+               [("ok", ctypes.c_int), ("n_points", ctypes.c_int)]
+
+
+@dataclass
+class Params:
+    """Model parameters (lb_params). ``eta_wall_r`` stands in for psi^r at solid
+    nodes (felt by b), ``eta_wall_b`` for psi^b (felt by r)."""
+    tau_r: float = 1.0
+    tau_b: float = 1.0
+    g_br: float = 0.0
+    eta_wall_r: float = 0.0
+    eta_wall_b: float = 0.0
+    force_weights: int = LB_WEIGHTS_UNIT
+    force_scale: float = 1.0
+
+    def c(self) -> lb_params:
+        return lb_params(self.tau_r, self.tau_b, self.g_br, self.eta_wall_r, self.eta_wall_b,
+                         int(self.force_weights), self.force_scale)
+
+
+_lib = None
+
+_VP = ctypes.c_void_p
+_DP = ctypes.POINTER(ctypes.c_double)
+_I = ctypes.c_int
+
+# (name, restype, argtypes) of every entry point declared in include/lbsc.h
+SIGNATURES = [
+    ("lb_init", _I, [ctypes.POINTER(_VP), _I, _I, _I, _I, _DP, _DP, _VP]),
+    ("lb_required_bytes", _I, [_I, _I, _I, _I, ctypes.POINTER(ctypes.c_size_t)]),
+    ("lb_init_external", _I, [ctypes.POINTER(_VP), _I, _I, _I, _I, _DP, _DP, _VP, _VP, ctypes.c_size_t]),
+    ("lb_set_geometry", _I, [_VP, ctypes.POINTER(ctypes.c_uint8)]),
+    ("lb_set_params", _I, [_VP, ctypes.POINTER(lb_params)]),
+    ("lb_step", _I, [_VP, _I]),
+    ("lb_sync", _I, [_VP]),
+    ("lb_moments", _I, [_VP, _DP, _DP, _DP, _DP]),
+    ("lb_conservation", _I, [_VP, _DP]),
+    ("lb_contact_angle", _I, [_VP, ctypes.c_double, ctypes.POINTER(lb_droplet)]),
+    ("lb_state_bytes", _I, [_VP, ctypes.POINTER(ctypes.c_size_t)]),
+    ("lb_save", _I, [_VP, _VP, ctypes.c_size_t]),
+    ("lb_load", _I, [_VP, _VP, ctypes.c_size_t]),
+    ("lb_get_populations", _I, [_VP, _DP]),
+    ("lb_set_populations", _I, [_VP, _DP]),
+    ("lb_set_schedule", _I, [_VP, _I, _I]),
+    ("lb_last_error", ctypes.c_char_p, [_VP]),
+    ("lb_free", None, [_VP]),
+]
+
+
+def load(path: str = _LIB_PATH):
+    """Load the CUDA library (raises if it is not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise RuntimeError(f"lbsc CUDA library not found at {path}; run __graft_entry__.build()")
+        lib = ctypes.CDLL(path)
+        for name, res, args in SIGNATURES:
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def _check(rc: int, ctx=None):
+    if rc != LB_OK:
+        msg = load().lb_last_error(ctx)
+        raise LBError(rc, msg.decode() if msg else "")
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _dp(a: np.ndarray):
+    return a.ctypes.data_as(_DP)
+
+
+def _current_stream():
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    except ImportError:
+        pass
+    return ctypes.c_void_p(None)
+
+
+class Lattice:
+    """One lattice on the current CUDA device (a ``lb_ctx``).
+
+    rho_r, rho_b: initial densities (nz, ny, nx). precision: "f32", "f16" or "bf16".
+    stream: a CUDA stream handle (int) or None for torch's current stream.
+    torch_memory: place the lattice in a torch-allocated device buffer
+    (lb_init_external); otherwise the library allocates it (lb_init).
+    """
+
+    def __init__(self, rho_r, rho_b, precision: str = "f32", stream=None, torch_memory: bool = False):
+        lib = load()
+        rr, rb = _f64(rho_r), _f64(rho_b)
+        if rr.shape != rb.shape or rr.ndim != 3:
+            raise ValueError("rho_r and rho_b must have the same 3-D shape (nz, ny, nx)")
+        self.nz, self.ny, self.nx = rr.shape
+        self.precision = precision
+        st = _current_stream() if stream is None else ctypes.c_void_p(stream)
+        ctx = ctypes.c_void_p()
+        self._buf = None
+        if torch_memory:
+            import torch
+            nbytes = ctypes.c_size_t()
+            _check(lib.lb_required_bytes(self.nx, self.ny, self.nz, PRECISIONS[precision], ctypes.byref(nbytes)))
+            self._buf = torch.empty(nbytes.value + 256, dtype=torch.uint8, device="cuda")
+            ptr = (self._buf.data_ptr() + 255) // 256 * 256
+            rc = lib.lb_init_external(ctypes.byref(ctx), self.nx, self.ny, self.nz, PRECISIONS[precision],
+                                      _dp(rr), _dp(rb), st, ctypes.c_void_p(ptr), nbytes.value)
+        else:
+            rc = lib.lb_init(ctypes.byref(ctx), self.nx, self.ny, self.nz, PRECISIONS[precision],
+                             _dp(rr), _dp(rb), st)
+        _check(rc)
+        self._ctx = ctx
+        self._params = Params()
+
+    # ------------------------------------------------------------ configuration
+    @property
+    def shape(self):
+        return self.nz, self.ny, self.nx
+
+    @property
+    def params(self) -> Params:
+        return self._params
+
+    def set_params(self, params: Params | None = None, **kw) -> "Lattice":
+        p = params if params is not None else Params(**{**self._params.__dict__, **kw})
+        cp = p.c()
+        _check(load().lb_set_params(self._ctx, ctypes.byref(cp)), self._ctx)
+        self._params = p
+        return self
+
+    def set_geometry(self, solid) -> "Lattice":
+        s = np.ascontiguousarray(solid, dtype=np.uint8)
+        if s.shape != self.shape:
+            raise ValueError("solid mask must have shape (nz, ny, nx)")
+        _check(load().lb_set_geometry(self._ctx, s.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))), self._ctx)
+        return self
+
+    def set_schedule(self, tile_y: int = 8, z_segments: int = 0) -> "Lattice":
+        _check(load().lb_set_schedule(self._ctx, tile_y, z_segments), self._ctx)
+        return self
+
+    # ------------------------------------------------------------ stepping
+    def step(self, n: int = 1) -> "Lattice":
+        _check(load().lb_step(self._ctx, int(n)), self._ctx)
+        return self
+
+    def sync(self) -> "Lattice":
+        _check(load().lb_sync(self._ctx), self._ctx)
+        return self
+
+    # ------------------------------------------------------------ readback
+    def moments(self, velocity: bool = False):
+        """(rho_r, rho_b, u or None, cons[8])"""
+        rr = np.empty(self.shape)
+        rb = np.empty(self.shape)
+        u = np.empty((3,) + self.shape) if velocity else None
+        cons = np.empty(8)
+        _check(load().lb_moments(self._ctx, _dp(rr), _dp(rb), _dp(u) if u is not None else None, _dp(cons)),
+               self._ctx)
+        return rr, rb, u, cons
+
+    def conservation(self) -> np.ndarray:
+        cons = np.empty(8)
+        _check(load().lb_conservation(self._ctx, _dp(cons)), self._ctx)
+        return cons
+
+    def contact_angle(self, offset: float = 5.0) -> dict:
+        d = lb_droplet()
+        _check(load().lb_contact_angle(self._ctx, float(offset), ctypes.byref(d)), self._ctx)
+        return {f: getattr(d, f) for f, _ in lb_droplet._fields_}
+
+    def populations(self) -> np.ndarray:
+        n = np.empty((2, 19) + self.shape)
+        _check(load().lb_get_populations(self._ctx, _dp(n)), self._ctx)
+        return n
+
+    def set_populations(self, n) -> "Lattice":
+        a = _f64(n)
+        if a.shape != (2, 19) + self.shape:
+            raise ValueError("populations must have shape (2, 19, nz, ny, nx)")
+        _check(load().lb_set_populations(self._ctx, _dp(a)), self._ctx)
+        return self
+
+    # ------------------------------------------------------------ checkpoints
+    def save(self) -> bytes:
+        nb = ctypes.c_size_t()
+        _check(load().lb_state_bytes(self._ctx, ctypes.byref(nb)), self._ctx)
+        buf = ctypes.create_string_buffer(nb.value)
+        _check(load().lb_save(self._ctx, buf, nb.value), self._ctx)
+        return buf.raw
+
+    def load(self, state: bytes) -> "Lattice":
+        _check(load().lb_load(self._ctx, state, len(state)), self._ctx)
+        return self
+
+    # ------------------------------------------------------------ lifetime
+    def close(self):
+        if getattr(self, "_ctx", None) is not None and self._ctx.value:
+            load().lb_free(self._ctx)
+            self._ctx = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -1,0 +1,92 @@
+"""Host-side checks of the C ABI that need no GPU: the library loads, it
+exports every entry point include/lbsc.h declares, the binding's constants
+match the header, and argument validation fails before any CUDA call."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "lbsc.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_0910_3915_gb300 import build, lbsc
+    build.build()
+    return lbsc.load()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:int|void|const char\*)\s+(lb_\w+)\s*\(", text, flags=re.M)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("lb_init", "lb_set_geometry", "lb_set_params", "lb_step", "lb_moments",
+                     "lb_contact_angle", "lb_last_error", "lb_free"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    from paper_0910_3915_gb300 import lbsc
+    names = declared_functions()
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+    assert sorted(n for n, _, _ in lbsc.SIGNATURES) == names
+
+
+def test_constants_match_header():
+    from paper_0910_3915_gb300 import lbsc
+    text = open(HEADER).read()
+    defs = dict(re.findall(r"#define\s+(LB_\w+)\s+\(?(-?\d+)\)?", text))
+    for name in ("LB_OK", "LB_ERR_ARG", "LB_ERR_CUDA", "LB_ERR_NAN", "LB_ERR_BARRIER_TIMEOUT",
+                 "LB_ERR_STATE", "LB_ERR_UNSUPPORTED", "LB_F32", "LB_F16", "LB_BF16",
+                 "LB_WEIGHTS_UNIT", "LB_WEIGHTS_W36"):
+        assert int(defs[name]) == getattr(lbsc, name), name
+
+
+def test_struct_layouts_match_header(lib):
+    from paper_0910_3915_gb300 import lbsc
+    assert ctypes.sizeof(lbsc.lb_params) == 7 * 8
+    assert ctypes.sizeof(lbsc.lb_droplet) == 10 * 8 + 2 * 4
+
+
+def test_argument_errors_before_cuda(lib):
+    from paper_0910_3915_gb300 import lbsc
+    ctx = ctypes.c_void_p()
+    rr = np.ones(8)
+    dp = rr.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    assert lib.lb_init(ctypes.byref(ctx), 0, 2, 4, lbsc.LB_F32, dp, dp, None) == lbsc.LB_ERR_ARG
+    assert b"dimensions" in lib.lb_last_error(None)
+    assert lib.lb_init(ctypes.byref(ctx), 2, 2, 2, 7, dp, dp, None) == lbsc.LB_ERR_ARG
+    assert lib.lb_init(ctypes.byref(ctx), 2, 2, 2, lbsc.LB_F32, None, dp, None) == lbsc.LB_ERR_ARG
+    bad = np.array([1.0, np.nan, 1, 1, 1, 1, 1, 1])
+    assert lib.lb_init(ctypes.byref(ctx), 2, 2, 2, lbsc.LB_F32,
+                       bad.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), dp, None) == lbsc.LB_ERR_ARG
+    assert ctx.value is None
+    assert lib.lb_step(None, 1) == lbsc.LB_ERR_ARG
+    assert lib.lb_set_params(None, None) == lbsc.LB_ERR_ARG
+    assert lib.lb_moments(None, None, None, None, None) == lbsc.LB_ERR_ARG
+    nb = ctypes.c_size_t()
+    assert lib.lb_required_bytes(128, 128, 128, lbsc.LB_F32, ctypes.byref(nb)) == lbsc.LB_OK
+    # two population buffers of 38 planes dominate: 304 B per node in FP32
+    assert 304 * 128 ** 3 < nb.value < 360 * 128 ** 3
+    assert lib.lb_required_bytes(128, 128, 128, lbsc.LB_BF16, ctypes.byref(nb)) == lbsc.LB_OK
+    assert nb.value < 200 * 128 ** 3
+    lib.lb_free(None)
+
+
+def test_binding_fails_loudly_without_library(tmp_path):
+    from paper_0910_3915_gb300 import lbsc
+    saved = lbsc._lib
+    try:
+        lbsc._lib = None
+        with pytest.raises(RuntimeError, match="not found"):
+            lbsc.load(str(tmp_path / "missing.so"))
+    finally:
+        lbsc._lib = saved

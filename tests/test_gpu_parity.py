@@ -1,0 +1,275 @@
+"""Parity of the CUDA step (through the C ABI) with the FP64 oracle.
+
+Bar: per-node relative density error <= 1e-5 after 100 FP32 steps; contact
+angle within 0.5 deg at steady state. Inputs are seeded droplet-on-wall
+lattices from paper_0910_3915_gb300.workloads, identical on both sides.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_0910_3915_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+# the printed force (unit weights) and the droplet-forming reading used for angles
+PRINTED = dict(g_br=0.08, force_weights=0, force_scale=1.0)
+CONTACT = dict(g_br=0.08, force_weights=1, force_scale=1.25)
+
+
+@pytest.fixture(scope="module")
+def lbsc():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_0910_3915_gb300 import lbsc as m
+    m.load()
+    return m
+
+
+def run_pair(lbsc, rr, rb, solid, steps, prm, precision="f32", schedule=None, walls_default=True):
+    lat = lbsc.Lattice(rr, rb, precision)
+    if not walls_default:
+        lat.set_geometry(solid)
+    if schedule:
+        lat.set_schedule(*schedule)
+    lat.set_params(**prm)
+    lat.step(steps)
+    g = lat.moments()
+    lat.close()
+    o = oracle.State(rr, rb, solid, oracle.Params(**prm)).step(steps).moments()
+    return g, o
+
+
+def rel_err(g, o, solid):
+    fl = solid == 0
+    return max(np.max(np.abs(g[a] - o[a])[fl] / np.abs(o[a])[fl]) for a in (0, 1))
+
+
+@pytest.mark.parametrize("w", W.small_wall_params())
+@pytest.mark.parametrize("reading", ["printed", "contact"])
+def test_small_droplet_100_steps(lbsc, w, reading):
+    """32^3, R = 8 cap on the bottom wall, g_br = 0.08, five seeded wall values."""
+    nx = ny = nz = 32
+    rr, rb = W.droplet_fields(nx, ny, nz, 8.0, seed=0)
+    er, eb = W.wall_split(w)
+    prm = dict(PRINTED if reading == "printed" else CONTACT, eta_wall_r=er, eta_wall_b=eb)
+    g, o = run_pair(lbsc, rr, rb, W.wall_mask(nx, ny, nz), 100, prm)
+    assert rel_err(g, o, W.wall_mask(nx, ny, nz)) <= 1e-5
+
+
+@pytest.mark.parametrize("dims", [(45, 27, 19), (33, 9, 7), (5, 3, 6), (70, 41, 12)])
+def test_ragged_lattices(lbsc, dims):
+    """Sizes that leave ragged tiles in x and y and short z columns."""
+    nx, ny, nz = dims
+    rr, rb = W.droplet_fields(nx, ny, nz, min(nx, ny) / 3, seed=4)
+    prm = dict(CONTACT, eta_wall_r=-0.03, eta_wall_b=0.03)
+    g, o = run_pair(lbsc, rr, rb, W.wall_mask(nx, ny, nz), 100, prm)
+    assert rel_err(g, o, W.wall_mask(nx, ny, nz)) <= 1e-5
+
+
+def test_unequal_tau(lbsc):
+    """The general-tau collision path (tau_r = 0.8, tau_b = 1.3)."""
+    nx, ny, nz = 40, 30, 18
+    rr, rb = W.droplet_fields(nx, ny, nz, 8.0, seed=6)
+    prm = dict(CONTACT, tau_r=0.8, tau_b=1.3, eta_wall_r=0.02, eta_wall_b=-0.02)
+    g, o = run_pair(lbsc, rr, rb, W.wall_mask(nx, ny, nz), 100, prm)
+    assert rel_err(g, o, W.wall_mask(nx, ny, nz)) <= 1e-5
+
+
+@pytest.mark.parametrize("tau", [1.0, 0.9])
+def test_general_geometry(lbsc, tau):
+    """A solid post and a partial step on the wall: the mask-driven kernels."""
+    nx, ny, nz = 36, 20, 16
+    solid = W.wall_mask(nx, ny, nz)
+    solid[1:6, 8:12, 5:9] = 1
+    solid[1:3, :, 30:] = 1
+    rr, rb = W.droplet_fields(nx, ny, nz, 7.0, seed=8)
+    prm = dict(CONTACT, tau_r=tau, tau_b=tau, eta_wall_r=-0.04, eta_wall_b=0.04)
+    g, o = run_pair(lbsc, rr, rb, solid, 100, prm, walls_default=False)
+    assert rel_err(g, o, solid) <= 1e-5
+
+
+def test_fully_periodic_and_momentum(lbsc):
+    """No solid nodes: z periodic too; total momentum is conserved with forces on."""
+    nx, ny, nz = 24, 20, 16
+    solid = W.periodic_mask(nx, ny, nz)
+    rr, rb = W.droplet_fields(nx, ny, nz, 6.0, seed=9, centre=(12, 10, 8))
+    prm = dict(CONTACT)
+    lat = lbsc.Lattice(rr, rb).set_geometry(solid).set_params(**prm)
+    n0 = W.random_populations(nx, ny, nz, seed=12)
+    lat.set_populations(n0)
+    p0 = lat.conservation()[2:5]
+    lat.step(100)
+    g = lat.moments()
+    p1 = g[3][2:5]
+    st = oracle.State(rr, rb, solid, oracle.Params(**prm))
+    st.n[:] = n0
+    o = st.step(100).moments()
+    assert rel_err(g, o, solid) <= 1e-5
+    mass = g[3][0] + g[3][1]
+    assert np.abs(p1 - p0).max() < 1e-6 * mass
+
+
+def test_schedules_are_bitwise_identical(lbsc):
+    """Tile height and z segmentation change only the work split, never a value."""
+    nx, ny, nz = 37, 23, 21
+    rr, rb = W.droplet_fields(nx, ny, nz, 7.0, seed=1)
+    ref = None
+    for ty, seg in [(8, 1), (4, 3), (16, 2), (8, 5)]:
+        lat = lbsc.Lattice(rr, rb).set_schedule(ty, seg).set_params(**CONTACT, eta_wall_b=0.05)
+        lat.step(20)
+        out = lat.moments()[:2]
+        lat.close()
+        if ref is None:
+            ref = out
+        else:
+            assert np.array_equal(out[0], ref[0]) and np.array_equal(out[1], ref[1])
+
+
+def test_graph_replay_matches_eager(lbsc):
+    nx, ny, nz = 32, 16, 12
+    rr, rb = W.droplet_fields(nx, ny, nz, 5.0, seed=2)
+    a = lbsc.Lattice(rr, rb).set_params(**CONTACT)
+    b = lbsc.Lattice(rr, rb).set_params(**CONTACT)
+    a.step(70)
+    for _ in range(70):
+        b.step(1)
+    ra, rb_ = a.moments(), b.moments()
+    assert np.array_equal(ra[0], rb_[0]) and np.array_equal(ra[1], rb_[1])
+    assert ra[3][7] == 70 and rb_[3][7] == 70
+
+
+def test_save_load_resume_bitwise(lbsc):
+    nx, ny, nz = 32, 32, 16
+    rr, rb = W.droplet_fields(nx, ny, nz, 6.0, seed=3)
+    lat = lbsc.Lattice(rr, rb).set_params(**CONTACT, eta_wall_b=0.03, eta_wall_r=-0.03)
+    lat.step(100)
+    state = lat.save()
+    lat.step(100)
+    a = lat.moments()
+    lat.load(state)
+    assert lat.conservation()[7] == 100
+    lat.step(100)
+    b = lat.moments()
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    with pytest.raises(lbsc.LBError):
+        lat.load(state[:100])
+
+
+def test_mass_conservation_fp64_sums(lbsc):
+    nx = ny = nz = 32
+    rr, rb = W.droplet_fields(nx, ny, nz, 8.0, seed=0)
+    lat = lbsc.Lattice(rr, rb).set_params(**CONTACT, eta_wall_r=-0.05, eta_wall_b=0.05)
+    m0 = lat.conservation()[:2]
+    lat.step(1000)
+    m1 = lat.conservation()[:2]
+    assert np.all(np.abs(m1 - m0) / m0 < 1e-5)
+    ref = oracle.State(rr, rb, W.wall_mask(nx, ny, nz), oracle.Params(**CONTACT)).moments()[3]
+    assert np.allclose(m0, ref[:2], rtol=1e-6)
+
+
+def test_populations_roundtrip_and_layout(lbsc):
+    """lb_get_populations returns the oracle's layout and velocity order."""
+    nx, ny, nz = 12, 10, 8
+    rr, rb = W.droplet_fields(nx, ny, nz, 3.0, seed=5)
+    lat = lbsc.Lattice(rr, rb).set_params(**CONTACT)
+    lat.step(3)
+    st = oracle.State(rr, rb, W.wall_mask(nx, ny, nz), oracle.Params(**CONTACT)).step(3)
+    n = lat.populations()
+    fl = (W.wall_mask(nx, ny, nz) == 0)[None, None]
+    assert np.allclose(np.where(fl, n, 0), st.n, rtol=1e-5, atol=1e-7)
+    lat.set_populations(st.n)
+    assert np.allclose(np.where(fl, lat.populations(), 0), st.n, rtol=1e-7, atol=1e-9)
+
+
+# --------------------------------------------------------------- contact angle
+def test_contact_angle_measurement_on_analytic_caps(lbsc):
+    """The device reductions reproduce the oracle's construction on the same field."""
+    for theta in (60.0, 90.0, 120.0):
+        n, nz, R = 72, 48, 20.0
+        zc = 0.5 - R * math.cos(math.radians(theta))
+        z, y, x = np.meshgrid(np.arange(nz), np.arange(n), np.arange(n), indexing="ij")
+        phi = np.tanh((R - np.sqrt((x - n / 2) ** 2 + (y - n / 2) ** 2 + (z - zc) ** 2)) / 2.0)
+        rr, rb = 0.37 + 0.33 * phi, 0.37 - 0.33 * phi
+        lat = lbsc.Lattice(rr, rb)
+        g = lat.contact_angle(5.0)
+        lat.close()
+        o = oracle.contact_angle(rr, rb, W.wall_mask(n, n, nz), 5.0)
+        assert g["ok"] == 1
+        assert abs(g["theta_deg"] - theta) < 0.5
+        assert abs(g["theta_deg"] - o["theta_deg"]) < 0.01
+        assert abs(g["theta_fit_deg"] - o["theta_fit_deg"]) < 0.01
+        assert g["n_points"] == o["n_points"]
+
+
+@pytest.mark.parametrize("w", W.small_wall_params())
+def test_contact_angle_steady_state(lbsc, w):
+    """32^3 droplet, 2000 steps (the droplet-forming reading): theta within 0.5 deg."""
+    nx = ny = nz = 32
+    rr, rb = W.droplet_fields(nx, ny, nz, 8.0, seed=0)
+    er, eb = W.wall_split(w)
+    prm = dict(CONTACT, eta_wall_r=er, eta_wall_b=eb)
+    lat = lbsc.Lattice(rr, rb).set_params(**prm)
+    lat.step(2000)
+    g = lat.contact_angle(3.0)
+    gm = lat.moments()
+    st = oracle.State(rr, rb, W.wall_mask(nx, ny, nz), oracle.Params(**prm)).step(2000)
+    o = st.contact_angle(3.0)
+    assert o["ok"] == 1 and g["ok"] == 1
+    assert abs(g["theta_deg"] - o["theta_deg"]) < 0.5
+    assert abs(g["theta_fit_deg"] - o["theta_fit_deg"]) < 0.5
+    assert rel_err(gm, st.moments(), W.wall_mask(nx, ny, nz)) < 1e-3
+
+
+# --------------------------------------------------------------- full size, sampled
+def _oracle_node_update(n_t, solid, prm, z, y, x):
+    """The oracle's step on the 5x5x5 neighbourhood of (z, y, x) (clipped at solid
+    layers): the centre's new populations depend on nothing outside it."""
+    nz, ny, nx = solid.shape
+    zs = list(range(max(0, z - 2), min(nz, z + 3)))
+    ys = [(y + d) % ny for d in range(-2, 3)]
+    xs = [(x + d) % nx for d in range(-2, 3)]
+    blk = n_t[:, :, zs][:, :, :, ys][:, :, :, :, xs]
+    sb = solid[zs][:, ys][:, :, xs]
+    st = oracle.State(np.ones(sb.shape), np.ones(sb.shape), sb, oracle.Params(**prm))
+    st.n[:] = np.ascontiguousarray(blk) * (1 - sb)[None, None]
+    st.step(1)
+    return st.n[:, :, zs.index(z), 2, 2]
+
+
+@pytest.mark.parametrize("precision,dims,radius,tol", [
+    ("f32", (128, 128, 128), 30.0, 1e-5),
+    ("f16", (256, 256, 128), 60.0, 2e-3),
+    ("bf16", (256, 256, 128), 60.0, 2e-2),
+])
+def test_full_size_sampled_nodes(lbsc, precision, dims, radius, tol):
+    """Production sizes in the benchmark's launch configuration: after 6 steps,
+    one more step at 64 sampled nodes (walls, interface, bulk) against the
+    oracle's update of each node's neighbourhood."""
+    nx, ny, nz = dims
+    rr, rb = W.droplet_fields(nx, ny, nz, radius, seed=0)
+    prm = dict(CONTACT, eta_wall_r=-0.05, eta_wall_b=0.05)
+    lat = lbsc.Lattice(rr, rb, precision).set_params(**prm)
+    lat.step(6)
+    n6 = lat.populations()
+    lat.step(1)
+    n7 = lat.populations()
+    lat.close()
+    solid = W.wall_mask(nx, ny, nz)
+    rng = np.random.default_rng(7)
+    pts = [(1, ny // 2, nx // 2), (nz - 2, 0, 0), (1, 0, nx - 1)]
+    pts += [(int(rng.integers(1, nz - 1)), int(rng.integers(0, ny)), int(rng.integers(0, nx))) for _ in range(40)]
+    # nodes on the droplet interface
+    for _ in range(21):
+        th, ph = rng.uniform(0, math.pi / 2), rng.uniform(0, 2 * math.pi)
+        pts.append((max(1, int(0.5 + radius * math.cos(th))), int(ny / 2 + radius * math.sin(th) * math.sin(ph)),
+                    int(nx / 2 + radius * math.sin(th) * math.cos(ph))))
+    worst = 0.0
+    for z, y, x in pts:
+        ref = _oracle_node_update(n6, solid, prm, z, y, x)
+        got = n7[:, :, z, y, x]
+        worst = max(worst, float(np.max(np.abs(got - ref)) / np.max(np.abs(ref))))
+    assert worst <= tol, worst
