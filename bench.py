@@ -1,0 +1,323 @@
+#!/usr/bin/env python
+"""Throughput of the two-component Shan-Chen D3Q19 step on one GB300 (or N, as replicas).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload single|precision-f16|precision-bf16|small]
+
+One bench "step" is one lattice time step of the whole hot path: moments,
+psi, Shan-Chen and wall force, force-shifted cubic BGK and streaming with
+mid-grid bounce-back (one fused kernel launch). The timed region also holds
+the FP64 conservation reductions every 1000 steps and one contact-angle
+measurement at the end. Default workload: the 128^3 droplet (R = 30, FP32,
+g_br = 0.08, W36 weights with force scale 1.25, wall parameter 0.05).
+
+Prints ONE JSON line (rank 0). MLUPS counts fluid-node updates per second.
+Under torchrun each rank runs its own lattice (independent replicas, weak
+scaling, no data-path collective); the time is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS and % HBM roofline (FP32 / BF16-stored vs FP64 oracle, contact-angle err in deg)"
+CONTACT = dict(g_br=0.08, force_weights=1, force_scale=1.25)
+WORKLOADS = {
+    "single": dict(dims=(128, 128, 128), radius=30.0, precision="f32", w=0.05),
+    "precision-f16": dict(dims=(256, 256, 128), radius=60.0, precision="f16", w=0.05),
+    "precision-bf16": dict(dims=(256, 256, 128), radius=60.0, precision="bf16", w=0.05),
+    "small": dict(dims=(32, 32, 32), radius=8.0, precision="f32", w=0.05),
+}
+BYTES_PER_LU = {"f32": 304, "f16": 152, "bf16": 152}
+CONS_EVERY = 1000
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20000)
+    ap.add_argument("--warmup", type=int, default=200)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="single")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-tune", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def step_kernel_traffic(workload: str):
+    """Per-launch DRAM bytes of the step kernel from the committed ncu summary,
+    or None when the kernel source changed since it was taken."""
+    path = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+        src = open(os.path.join(ROOT, "paper_0910_3915_gb300", "csrc", "step.cu"), "rb").read()
+        if rec.get("step_cu_sha256") != hashlib.sha256(src).hexdigest():
+            return None
+        return rec.get("bytes_per_launch", {}).get(workload)
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_id: str):
+        self.out = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", device_id, f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.out, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.out.flush()
+        rows = []
+        with open(self.out.name) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 8:
+                    rows.append(parts)
+        os.unlink(self.out.name)
+        if not rows:
+            return None
+        sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[4 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def oracle_mlups(dims, radius, w, seconds: float):
+    """The FP64 oracle on the same workload, a bounded number of steps."""
+    import oracle
+    from paper_0910_3915_gb300 import workloads as W
+    nx, ny, nz = dims
+    rr, rb = W.droplet_fields(nx, ny, nz, radius, seed=0)
+    er, eb = W.wall_split(w)
+    st = oracle.State(rr, rb, W.wall_mask(nx, ny, nz), oracle.Params(**CONTACT, eta_wall_r=er, eta_wall_b=eb))
+    t = time.perf_counter()
+    st.step(1)
+    one = time.perf_counter() - t
+    n = max(1, min(1000, int(seconds / max(one, 1e-6))))
+    t = time.perf_counter()
+    st.step(n)
+    el = time.perf_counter() - t
+    nf = nx * ny * (nz - 2)
+    return nf * n / el / 1e6, n, el
+
+
+def omp_threads():
+    v = os.environ.get("OMP_NUM_THREADS")
+    return int(v) if v and v.isdigit() else (os.cpu_count() or 1)
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    wl = WORKLOADS[args.workload]
+    nx, ny, nz = wl["dims"]
+    mlups, n, el = oracle_mlups(wl["dims"], wl["radius"], wl["w"], seconds=60.0)
+    cores = omp_threads()
+    sample = f"{nx}x{ny}x{nz} droplet, {n} oracle steps ({el:.1f} s)"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(mlups, 3), "unit": "MLUPS", "n_gpus": args.gpus,
+        "steps": n, "warmup": 1, "ms_per_step": round(el / n * 1e3, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"droplet {nx}x{ny}x{nz} R={wl['radius']:g} (FP64 CPU oracle)"},
+        "cpu_baseline": {"value": round(mlups, 3), "unit": "MLUPS", "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": round(mlups, 3), "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_0910_3915_gb300 import lbsc, tune
+    from paper_0910_3915_gb300 import workloads as W
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    wl = WORKLOADS[args.workload]
+    nx, ny, nz = wl["dims"]
+    prec = wl["precision"]
+    nf = nx * ny * (nz - 2)
+    er, eb = W.wall_split(wl["w"])
+    prm = dict(CONTACT, eta_wall_r=er, eta_wall_b=eb)
+    rr, rb = W.droplet_fields(nx, ny, nz, wl["radius"], seed=rank)
+    stream = torch.cuda.current_stream()
+    K, Wm = args.steps, max(3, args.warmup)
+
+    lat = lbsc.Lattice(rr, rb, prec).set_params(**prm)
+    schedule = None
+    if not args.no_tune:
+        schedule, _ = tune.tune(lat)
+    lat.step(Wm)
+    lat.sync()
+
+    try:
+        dev_id = str(torch.cuda.get_device_properties(local).uuid)
+        dev_id = dev_id if dev_id.startswith("GPU-") else "GPU-" + dev_id
+    except Exception:
+        dev_id = os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0] or "0"
+    sampler = ClockSampler(dev_id)
+    time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    t0, t1 = ev(), ev()
+    chunks = []
+    launches = 0
+    t0.record(stream)
+    done = 0
+    while done < K:
+        m = min(CONS_EVERY, K - done)
+        a, b = ev(), ev()
+        a.record(stream)
+        lat.step(m)
+        b.record(stream)
+        chunks.append((a, b))
+        launches += m
+        done += m
+        lat.conservation()
+        launches += 2
+    angle = lat.contact_angle(5.0)
+    launches += 3
+    t1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop()
+    ms = t0.elapsed_time(t1)
+    step_ms = sum(a.elapsed_time(b) for a, b in chunks) / K
+    if dist:
+        tt = torch.tensor([ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    value = nf * K * ws / (ms * 1e-3) / 1e6
+    cons = lat.conservation()
+    lat.close()
+
+    # end to end through the C ABI with host buffers: init (H2D), steps, readback (D2H)
+    rr_p = torch.from_numpy(rr).pin_memory().numpy()
+    rb_p = torch.from_numpy(rb).pin_memory().numpy()
+    torch.cuda.synchronize()
+    te = time.perf_counter()
+    lat2 = lbsc.Lattice(rr_p, rb_p, prec).set_params(**prm)
+    if schedule:
+        lat2.set_schedule(*schedule)
+    done = 0
+    while done < K:
+        m = min(CONS_EVERY, K - done)
+        lat2.step(m)
+        lat2.conservation()
+        done += m
+    out_r, out_b, _, _ = lat2.moments()
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - te
+    lat2.close()
+    h2d = 2 * rr.size * 8
+    d2h = 2 * rr.size * 4 + (K // CONS_EVERY + 2) * 64
+    e2e = nf * K * ws / e2e_s / 1e6
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    peak, peak_kind = peaks()
+    bpl = BYTES_PER_LU[prec]
+    achieved = nf * bpl / (step_ms * 1e-3) / 1e9
+    roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "traffic": step_kernel_traffic(args.workload),
+            "peak_source": peak_kind, "kernel": "step_kernel",
+            "algorithmic_bytes_per_launch": nf * bpl}
+    cpu = None
+    if not args.no_cpu_baseline and ws == 1:
+        c_mlups, c_n, c_el = oracle_mlups(wl["dims"], wl["radius"], wl["w"], seconds=15.0)
+        cpu = {"value": round(c_mlups, 3), "unit": "MLUPS", "cores": omp_threads(), "kind": "oracle",
+               "sample": f"{nx}x{ny}x{nz} droplet, {c_n} oracle steps ({c_el:.1f} s)"}
+    line = {
+        "metric": METRIC, "value": round(value, 1), "unit": "MLUPS", "n_gpus": ws, "steps": K, "warmup": Wm,
+        "ms_per_step": round(ms / K, 5), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": prec, "data": "synthetic",
+        "config": {"workload": f"droplet {nx}x{ny}x{nz} R={wl['radius']:g} {prec.upper()}",
+                   "lattice": [nx, ny, nz], "fluid_nodes": nf, "params": prm,
+                   "schedule": {"tile": f"32x{schedule[0]}", "z_segments": schedule[1]} if schedule else "default",
+                   "l2": "inputs larger than L2 (state %.0f MB, L2 129 MB)" % (nx * ny * nz * bpl / 1e6),
+                   "timed": f"{K} steps + FP64 conservation every {CONS_EVERY} + 1 contact angle"},
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": {"value": round(e2e, 1), "unit": "MLUPS", "h2d_bytes_per_step": round(h2d / K, 1),
+                "d2h_bytes_per_step": round(d2h / K, 1)},
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "step_kernel_ms": round(step_ms, 5),
+        "theta_deg": round(angle["theta_deg"], 3) if angle["ok"] else None,
+        "mass_rel_drift": None,
+    }
+    m0 = float(rr[1:-1].sum()), float(rb[1:-1].sum())
+    line["mass_rel_drift"] = [float(cons[0] / m0[0] - 1), float(cons[1] / m0[1] - 1)]
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -38,7 +38,7 @@ struct lb_ctx {
     Scratch W{};
     lb_params prm{};
     KParams kp{};
-    int tile_y = 8, nseg_req = 0;
+    int tile_y = 4, nseg_req = 0;
     int nseg_cache = 0;  // segments per tile column for the current schedule (0 = not computed)
     long long steps = 0;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
@@ -143,7 +143,7 @@ static int nseg_for(lb_ctx* c, int ncol)
     if (c->nseg_req > 0) return c->nseg_cache = (c->nseg_req < nzf ? c->nseg_req : nzf);
     int occ = step_occupancy(c->prec, c->tile_y, c->general, tau_one(c));
     if (occ < 1) occ = 1;
-    const long long target = (long long)c->nsm * occ;
+    const long long target = 2LL * c->nsm * occ;  // about two waves of CTAs
     long long s = (target + ncol - 1) / ncol;
     const long long smax = nzf / 16 > 1 ? nzf / 16 : 1;  // segments of at least 16 planes
     if (s > smax) s = smax;
