@@ -253,7 +253,7 @@ def run_ours(args):
     te = time.perf_counter()
     lat2 = lbsc.Lattice(rr_p, rb_p, prec).set_params(**prm)
     if schedule:
-        lat2.set_schedule(*schedule)
+        tune.apply(lat2, schedule)
     done = 0
     while done < K:
         m = min(CONS_EVERY, K - done)
@@ -291,7 +291,8 @@ def run_ours(args):
         "dtype": prec, "data": "synthetic",
         "config": {"workload": f"droplet {nx}x{ny}x{nz} R={wl['radius']:g} {prec.upper()}",
                    "lattice": [nx, ny, nz], "fluid_nodes": nf, "params": prm,
-                   "schedule": {"tile": f"32x{schedule[0]}", "z_segments": schedule[1]} if schedule else "default",
+                   "schedule": ({"variant": schedule[0], "stages": schedule[1], "tile": f"32x{schedule[2]}",
+                                 "z_segments": schedule[3]} if schedule else "default"),
                    "l2": "inputs larger than L2 (state %.0f MB, L2 129 MB)" % (nx * ny * nz * bpl / 1e6),
                    "timed": f"{K} steps + FP64 conservation every {CONS_EVERY} + 1 contact angle"},
         "roofline": roof,

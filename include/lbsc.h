@@ -51,6 +51,11 @@ extern "C" {
 #define LB_F16 1   /* FP16 deviations e_k = n_k/zeta_k - rho_ref, FP32 arithmetic */
 #define LB_BF16 2  /* BF16 deviations, as above */
 
+/* step kernel variants (lb_set_step_variant) */
+#define LB_STEP_AUTO 0  /* TMA-staged kernel for planar walls, load-from-global otherwise */
+#define LB_STEP_LDG 1   /* every plane loaded from global memory by the compute threads */
+#define LB_STEP_TMA 2   /* planes staged into shared memory by TMA (planar walls only) */
+
 /* neighbour weights G_k of the Shan-Chen force sum */
 #define LB_WEIGHTS_UNIT 0  /* G_k = 1 for the 18 neighbours, as Eq. SCforce is printed */
 #define LB_WEIGHTS_W36 1   /* G_k = 36 zeta_k: 2 on axes, 1 on diagonals */
@@ -166,6 +171,13 @@ int lb_set_populations(lb_ctx* ctx, const double* n);
 /* Choose the step kernel's tile height (4, 8 or 16 rows of 32 nodes) and the
  * number of z segments per tile column (0 = automatic). */
 int lb_set_schedule(lb_ctx* ctx, int tile_y, int z_segments);
+
+/* Choose the step kernel: LB_STEP_AUTO, LB_STEP_LDG or LB_STEP_TMA, and for
+ * the TMA kernel the number of shared-memory stages (2 or 3; 0 = automatic).
+ * Every variant computes bit-identical results. LB_STEP_TMA with a
+ * non-planar geometry, or a (tile height, stages) pair that is not built for
+ * the precision, falls back to LB_STEP_LDG. */
+int lb_set_step_variant(lb_ctx* ctx, int variant, int stages);
 
 /* Message of the last failure on this context (or of the last failed lb_init
  * when ctx is NULL). Never NULL. */

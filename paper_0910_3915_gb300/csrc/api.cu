@@ -42,6 +42,10 @@ struct lb_ctx {
     int nseg_cache = 0;  // segments per tile column for the current schedule (0 = not computed)
     long long steps = 0;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    int variant = LB_STEP_AUTO, stages = 0;  // step kernel selection
+    CUtensorMap tmap[2][3];                  // per buffer, per tile height 4/8/16
+    bool tmap_ok[2][3] = {{false, false, false}, {false, false, false}};
+    int* dev_err = nullptr;                  // device status word of the step kernels
     static constexpr int kGraphSteps = 32;
     std::string err;
 };
@@ -69,14 +73,19 @@ static int cuda_fail(lb_ctx* c, cudaError_t e, const char* where)
 static size_t elem_size(int prec) { return prec == LB_F32 ? 4 : 2; }
 static size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
-static Layout make_layout(int nx, int ny, int nz)
+static size_t elem_size_of(int prec) { return prec == LB_F32 ? 4 : 2; }
+
+// rows of nx nodes with 16 bytes of ghost images on each side, one ghost row
+// above and below each plane
+static Layout make_layout(int nx, int ny, int nz, int prec)
 {
     Layout L;
     L.nx = nx;
     L.ny = ny;
     L.nz = nz;
-    L.px = (nx + 31) / 32 * 32;
-    L.plane = (long long)L.px * ny;
+    L.gx = (int)(16 / elem_size_of(prec));
+    L.px = (nx + 2 * L.gx + 31) / 32 * 32;
+    L.plane = (long long)L.px * (ny + 2);
     L.slot = (L.plane * nz + 127) / 128 * 128;
     return L;
 }
@@ -136,12 +145,16 @@ static void set_kparams(lb_ctx* c)
 
 static bool tau_one(const lb_ctx* c) { return c->prm.tau_r == 1.0 && c->prm.tau_b == 1.0; }
 
+static int tma_stages(lb_ctx* c);
+static long long tma_call(int op, lb_ctx* c, int ty, int ns);
+
 static int nseg_for(lb_ctx* c, int ncol)
 {
     if (c->nseg_cache > 0) return c->nseg_cache;
     const int nzf = c->zhi - c->zlo;
     if (c->nseg_req > 0) return c->nseg_cache = (c->nseg_req < nzf ? c->nseg_req : nzf);
-    int occ = step_occupancy(c->prec, c->tile_y, c->general, tau_one(c));
+    const int ns = tma_stages(c);
+    int occ = ns ? (int)tma_call(2, c, c->tile_y, ns) : step_occupancy(c->prec, c->tile_y, c->general, tau_one(c));
     if (occ < 1) occ = 1;
     const long long target = 2LL * c->nsm * occ;  // about two waves of CTAs
     long long s = (target + ncol - 1) / ncol;
@@ -152,6 +165,95 @@ static int nseg_for(lb_ctx* c, int ncol)
     return (int)s;
 }
 
+
+// ---------------------------------------------------------------- TMA step support
+static const int kTmaTiles[3] = {4, 8, 16};
+static int tile_index(int ty) { return ty == 4 ? 0 : (ty == 8 ? 1 : 2); }
+
+template <class S>
+static long long tma_op(int op, lb_ctx* c, int ty, int ns, const CUtensorMap* m, const StepArgs<S>* A,
+                        cudaStream_t st)
+{
+    return tma_step<S>(op, ty, ns, tau_one(c), m, A, st);
+}
+
+static long long tma_call(int op, lb_ctx* c, int ty, int ns)
+{
+    switch (c->prec) {
+    case LB_F32: return tma_op<float>(op, c, ty, ns, nullptr, nullptr, nullptr);
+    case LB_F16: return tma_op<__half>(op, c, ty, ns, nullptr, nullptr, nullptr);
+    default: return tma_op<__nv_bfloat16>(op, c, ty, ns, nullptr, nullptr, nullptr);
+    }
+}
+
+// raise the shared-memory limit of every TMA kernel built for this precision
+static cudaError_t tma_prepare(lb_ctx* c)
+{
+    for (int ty : kTmaTiles)
+        for (int ns = 2; ns <= 3; ++ns) {
+            const long long e = tma_call(1, c, ty, ns);  // cudaErrorInvalidValue: pair not built
+            if (e != (long long)cudaSuccess && e != (long long)cudaErrorInvalidValue) return (cudaError_t)e;
+        }
+    return cudaSuccess;
+}
+
+// stages used by the TMA kernel for the current schedule, 0 if not available
+static int tma_stages(lb_ctx* c)
+{
+    if (c->general || c->variant == LB_STEP_LDG) return 0;
+    const int want[2] = {c->stages ? c->stages : 3, c->stages ? c->stages : 2};
+    for (int ns : want) {
+        // occupancy 0: the pair is not built for this precision (or does not fit)
+        const long long occ = tma_call(2, c, c->tile_y, ns);
+        if (occ > 0) return ns;
+    }
+    return 0;
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn()
+{
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)p;
+    }
+    return fn;
+}
+
+// 5-D map over a population buffer: (x incl. ghosts, y incl. ghost rows, z, k, a);
+// box = tile of 32 + 2*ghost columns, TY + 2 rows, one plane, all 38 slots
+static int tensor_map(lb_ctx* c, int buf, int ty)
+{
+    const int ti = tile_index(ty);
+    if (c->tmap_ok[buf][ti]) return LB_OK;
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) return fail(c, LB_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
+    const size_t es = elem_size_of(c->prec);
+    const Layout& L = c->L;
+    const cuuint64_t dims[5] = {(cuuint64_t)L.px, (cuuint64_t)(L.ny + 2), (cuuint64_t)L.nz, (cuuint64_t)Q, 2};
+    const cuuint64_t strides[4] = {(cuuint64_t)L.px * es, (cuuint64_t)L.plane * es, (cuuint64_t)L.slot * es,
+                                   (cuuint64_t)Q * L.slot * es};
+    const cuuint32_t box[5] = {(cuuint32_t)(es == 4 ? 40 : 48), (cuuint32_t)(ty + 2), 1, (cuuint32_t)Q, 2};
+    const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+    const CUtensorMapDataType dt = c->prec == LB_F32   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                   : c->prec == LB_F16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                                       : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    const CUresult r = enc(&c->tmap[buf][ti], dt, 5, c->f[buf], dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                           CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(c, LB_ERR_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
+    c->tmap_ok[buf][ti] = true;
+    return LB_OK;
+}
+
 template <class S>
 static StepArgs<S> step_args(lb_ctx* c, int src)
 {
@@ -159,6 +261,7 @@ static StepArgs<S> step_args(lb_ctx* c, int src)
     A.src = (const S*)c->f[src];
     A.dst = (S*)c->f[1 - src];
     A.nbmask = c->nbmask;
+    A.err = c->dev_err;
     A.L = c->L;
     A.P = c->kp;
     A.tiles_x = (c->nx + 31) / 32;
@@ -169,11 +272,33 @@ static StepArgs<S> step_args(lb_ctx* c, int src)
     return A;
 }
 
+template <class S>
+static cudaError_t launch_tma(lb_ctx* c, int parity, int ns, cudaStream_t st)
+{
+    const StepArgs<S> A = step_args<S>(c, parity);
+    return (cudaError_t)tma_step<S>(0, c->tile_y, ns, tau_one(c), &c->tmap[parity][tile_index(c->tile_y)], &A, st);
+}
+
 static cudaError_t launch_steps(lb_ctx* c, int n, int& parity, cudaStream_t st)
 {
     const bool t1 = tau_one(c);
+    const int ns = tma_stages(c);
+    if (ns) {
+        for (int b = 0; b < 2; ++b)
+            if (tensor_map(c, b, c->tile_y) != LB_OK) return cudaErrorInvalidValue;
+    }
     for (int i = 0; i < n; ++i) {
         cudaError_t e;
+        if (ns) {
+            switch (c->prec) {
+            case LB_F32: e = launch_tma<float>(c, parity, ns, st); break;
+            case LB_F16: e = launch_tma<__half>(c, parity, ns, st); break;
+            default: e = launch_tma<__nv_bfloat16>(c, parity, ns, st); break;
+            }
+            if (e != cudaSuccess) return e;
+            parity ^= 1;
+            continue;
+        }
         switch (c->prec) {
         case LB_F32: e = launch_step<float>(step_args<float>(c, parity), c->tile_y, c->general, t1, st); break;
         case LB_F16: e = launch_step<__half>(step_args<__half>(c, parity), c->tile_y, c->general, t1, st); break;
@@ -230,7 +355,7 @@ static int init_common(lb_ctx** out, int nx, int ny, int nz, int precision, cons
     c->nz = nz;
     c->prec = precision;
     c->stream = (cudaStream_t)stream;
-    c->L = make_layout(nx, ny, nz);
+    c->L = make_layout(nx, ny, nz, precision);
     const Plan p = make_plan(c->L, precision);
     auto bail = [&](int code, const std::string& msg) {
         g_init_err = msg;
@@ -264,6 +389,7 @@ static int init_common(lb_ctx** out, int nx, int ny, int nz, int precision, cons
     c->part = (double*)q;
     q += p.part;
     c->red = (double*)q;
+    c->dev_err = (int*)(c->red + 48);
     const long long Nn = N;
     c->W.rho[0] = sf + 0 * Nn;
     c->W.rho[1] = sf + 1 * Nn;
@@ -275,6 +401,9 @@ static int init_common(lb_ctx** out, int nx, int ny, int nz, int precision, cons
     if (e != cudaSuccess) return bail(LB_ERR_CUDA, std::string("lb_init: cudaMallocHost: ") + cudaGetErrorString(e));
 
     if (planar_default(c) != LB_OK) return bail(LB_ERR_CUDA, c->err);
+    e = cudaMemsetAsync(c->dev_err, 0, sizeof(int), c->stream);
+    if (e == cudaSuccess) e = tma_prepare(c);
+    if (e != cudaSuccess) return bail(LB_ERR_CUDA, std::string("lb_init: ") + cudaGetErrorString(e));
     // 16-bit deviation references: mean initial density over fluid nodes
     double sum[2] = {0, 0};
     long long cnt = 0;
@@ -320,7 +449,7 @@ int lb_required_bytes(int nx, int ny, int nz, int precision, size_t* bytes)
     if (!bytes || !dims_ok(nx, ny, nz)) return fail(nullptr, LB_ERR_ARG, "lb_required_bytes: bad argument");
     if (precision != LB_F32 && precision != LB_F16 && precision != LB_BF16)
         return fail(nullptr, LB_ERR_ARG, "lb_required_bytes: unknown precision");
-    *bytes = make_plan(make_layout(nx, ny, nz), precision).total;
+    *bytes = make_plan(make_layout(nx, ny, nz, precision), precision).total;
     return LB_OK;
 }
 
@@ -362,7 +491,7 @@ int lb_set_geometry(lb_ctx* c, const uint8_t* solid)
                 uint32_t b = at(x, y, z) ? kSelfSolid : 0u;
                 for (int k = 1; k < Q; ++k)
                     if (at(wrapi(x + cx(k), nx), wrapi(y + cy(k), ny), wrapi(z + cz(k), nz))) b |= 1u << k;
-                m[(size_t)z * c->L.plane + (size_t)y * c->L.px + x] = b;
+                m[(size_t)c->L.off(x, y, z)] = b;
             }
     LB_CUDA(c, cudaMemcpy(c->nbmask, m.data(), m.size() * sizeof(uint32_t), cudaMemcpyHostToDevice));
     c->general = true;
@@ -383,6 +512,17 @@ int lb_set_params(lb_ctx* c, const lb_params* p)
     drop_graphs(c);
     c->prm = *p;
     set_kparams(c);
+    return LB_OK;
+}
+
+int lb_set_step_variant(lb_ctx* c, int variant, int stages)
+{
+    if (!c) return fail(c, LB_ERR_ARG, "lb_set_step_variant: NULL context");
+    if (variant < LB_STEP_AUTO || variant > LB_STEP_TMA || (stages != 0 && stages != 2 && stages != 3))
+        return fail(c, LB_ERR_ARG, "lb_set_step_variant: unknown variant or stages");
+    drop_graphs(c);
+    c->variant = variant;
+    c->stages = stages;
     return LB_OK;
 }
 
@@ -430,12 +570,14 @@ int lb_step(lb_ctx* c, int nsteps)
     return LB_OK;
 }
 
+static int check_device_status(lb_ctx* c);
+
 int lb_sync(lb_ctx* c)
 {
     if (!c) return fail(c, LB_ERR_ARG, "lb_sync: NULL context");
     LB_CUDA(c, cudaStreamSynchronize(c->stream));
     LB_CUDA(c, cudaGetLastError());
-    return LB_OK;
+    return check_device_status(c);
 }
 
 }  // extern "C"
@@ -478,6 +620,8 @@ int lb_conservation(lb_ctx* c, double cons[8])
     LB_CUDA(c, cudaStreamSynchronize(c->stream));
     for (int i = 0; i < 7; ++i) cons[i] = c->h_red[i];
     cons[7] = (double)c->steps;
+    const int st = check_device_status(c);
+    if (st != LB_OK) return st;
     if (cons[5] > 0) return fail(c, LB_ERR_NAN, "non-finite populations in the state");
     return LB_OK;
 }
@@ -581,6 +725,18 @@ int lb_contact_angle(lb_ctx* c, double offset, lb_droplet* out)
                 out->theta_fit_deg = std::acos(cth) * 180.0 / pi;
             }
         }
+    }
+    return LB_OK;
+}
+
+// Read and clear the step kernels' device status word (the stream is idle).
+static int check_device_status(lb_ctx* c)
+{
+    int h = 0;
+    LB_CUDA(c, cudaMemcpy(&h, c->dev_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (h != 0) {
+        LB_CUDA(c, cudaMemset(c->dev_err, 0, sizeof(int)));
+        return fail(c, LB_ERR_BARRIER_TIMEOUT, "a bounded wait in the step kernel gave up (TMA stage never landed)");
     }
     return LB_OK;
 }

@@ -78,14 +78,13 @@ __global__ void init_kernel(FieldArgs F, S* __restrict__ f, const double* __rest
     const long long N = (long long)F.L.nx * F.L.ny * F.L.nz;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
         const int x = (int)(i % F.L.nx), y = (int)((i / F.L.nx) % F.L.ny), z = (int)(i / ((long long)F.L.nx * F.L.ny));
-        const long long off = (long long)z * F.L.plane + (long long)y * F.L.px + x;
         for (int a = 0; a < 2; ++a) {
             const float rho = (float)(a == 0 ? rr[i] : rb[i]);
             for (int k = 0; k < Q; ++k) {
                 float v;
                 if constexpr (Codec<S>::kDeviation) v = rho - F.P.ref[a];
                 else v = zeta(k) * rho;
-                Codec<S>::store(f + (long long)(a * Q + k) * F.L.slot + off, v);
+                put<S>(f + (long long)(a * Q + k) * F.L.slot, F.L, x, y, (long long)z * F.L.plane, v);
             }
         }
     }
@@ -100,7 +99,7 @@ __global__ void __launch_bounds__(kRedThreads) cons_kernel(FieldArgs F, const S*
     const long long N = (long long)F.L.nx * F.L.ny * F.L.nz;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
         const int x = (int)(i % F.L.nx), y = (int)((i / F.L.nx) % F.L.ny), z = (int)(i / ((long long)F.L.nx * F.L.ny));
-        const long long off = (long long)z * F.L.plane + (long long)y * F.L.px + x;
+        const long long off = F.L.off(x, y, z);
         if (node_solid(F, x, y, z, off)) continue;
         acc[6] += 1.0;
         for (int a = 0; a < 2; ++a) {
@@ -130,7 +129,7 @@ __global__ void fields_kernel(FieldArgs F, const S* __restrict__ f, Scratch W)
     const long long N = (long long)F.L.nx * F.L.ny * F.L.nz;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
         const int x = (int)(i % F.L.nx), y = (int)((i / F.L.nx) % F.L.ny), z = (int)(i / ((long long)F.L.nx * F.L.ny));
-        const long long off = (long long)z * F.L.plane + (long long)y * F.L.px + x;
+        const long long off = F.L.off(x, y, z);
         float rho[2] = {0.f, 0.f}, j[3] = {0.f, 0.f, 0.f};
         const bool solid = node_solid(F, x, y, z, off);
         if (!solid) {
@@ -157,7 +156,7 @@ __global__ void velocity_kernel(FieldArgs F, Scratch W)
     const long long N = (long long)nx * ny * nz;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
         const int x = (int)(i % nx), y = (int)((i / nx) % ny), z = (int)(i / ((long long)nx * ny));
-        const long long off = (long long)z * F.L.plane + (long long)y * F.L.px + x;
+        const long long off = F.L.off(x, y, z);
         const float tot = W.rho[0][i] + W.rho[1][i];
         float u[3] = {0.f, 0.f, 0.f};
         if (!node_solid(F, x, y, z, off) && tot > 0.f) {
@@ -199,7 +198,7 @@ __global__ void __launch_bounds__(kRedThreads) angle_kernel(FieldArgs F, Scratch
         return (double)W.rho[0][i] - (double)W.rho[1][i];
     };
     auto solid = [&](int x, int y, int z) -> bool {
-        const long long off = (long long)z * F.L.plane + (long long)y * F.L.px + x;
+        const long long off = F.L.off(x, y, z);
         return node_solid(F, x, y, z, off);
     };
     const long long ncols = (long long)nx * ny;
@@ -255,7 +254,7 @@ __global__ void get_pop_kernel(FieldArgs F, const S* __restrict__ f, double* __r
         const long long n = i % N;
         const int a = ak / Q, k = ak % Q;
         const int x = (int)(n % F.L.nx), y = (int)((n / F.L.nx) % F.L.ny), z = (int)(n / ((long long)F.L.nx * F.L.ny));
-        const long long off = (long long)z * F.L.plane + (long long)y * F.L.px + x;
+        const long long off = F.L.off(x, y, z);
         out[i] = decode<S>(f + (long long)ak * F.L.slot + off, k, F.P.ref[a]);
     }
 }
@@ -269,10 +268,10 @@ __global__ void set_pop_kernel(FieldArgs F, S* __restrict__ f, const double* __r
         const long long n = i % N;
         const int a = ak / Q, k = ak % Q;
         const int x = (int)(n % F.L.nx), y = (int)((n / F.L.nx) % F.L.ny), z = (int)(n / ((long long)F.L.nx * F.L.ny));
-        const long long off = (long long)z * F.L.plane + (long long)y * F.L.px + x;
+        const long long off = F.L.off(x, y, z);
         float v = (float)in[i];
         if constexpr (Codec<S>::kDeviation) v = (float)(in[i] / (double)zeta(k) - (double)F.P.ref[a]);
-        Codec<S>::store(f + (long long)ak * F.L.slot + off, v);
+        put<S>(f + (long long)ak * F.L.slot, F.L, x, y, (long long)z * F.L.plane, v);
     }
 }
 

@@ -1,6 +1,8 @@
 // Declarations shared by the kernels' translation units and the C-ABI layer.
 #pragma once
 
+#include <cuda.h>
+
 #include "lb_internal.cuh"
 
 namespace lbsc {
@@ -27,6 +29,12 @@ struct Scratch {
 
 template <class S>
 cudaError_t launch_step(const StepArgs<S>& A, int tile_y, bool general, bool tau_one, cudaStream_t st);
+// TMA-staged step for planar walls: op 0 launches (returns a cudaError_t),
+// op 1 sets the kernels' shared-memory attribute, op 2 returns resident CTAs
+// per SM (0 if the (tile_y, stages) pair is not built for S).
+template <class S>
+long long tma_step(int op, int tile_y, int stages, bool tau_one, const CUtensorMap* map, const StepArgs<S>* args,
+                   cudaStream_t stream);
 template <class S>
 cudaError_t launch_init(const FieldArgs& F, S* f, const double* rr, const double* rb, cudaStream_t st);
 template <class S>

@@ -1,5 +1,6 @@
 // Internal definitions of the lbsc CUDA library: the D3Q19 lattice, the
-// population storage codecs and the argument blocks of the kernels.
+// population storage codecs, the ghosted storage layout and the argument
+// blocks of the kernels.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -48,28 +49,67 @@ template <>
 struct Codec<float> {
     static constexpr bool kDeviation = false;
     static __device__ __forceinline__ float load(const float* p) { return __ldg(p); }
+    static __device__ __forceinline__ float val(float v) { return v; }
+    static __device__ __forceinline__ float round(float v) { return v; }
     static __device__ __forceinline__ void store(float* p, float v) { *p = v; }
 };
 template <>
 struct Codec<__half> {
     static constexpr bool kDeviation = true;
     static __device__ __forceinline__ float load(const __half* p) { return __half2float(__ldg(p)); }
+    static __device__ __forceinline__ float val(__half v) { return __half2float(v); }
+    static __device__ __forceinline__ float round(float v) { return __half2float(__float2half_rn(v)); }
     static __device__ __forceinline__ void store(__half* p, float v) { *p = __float2half_rn(v); }
 };
 template <>
 struct Codec<__nv_bfloat16> {
     static constexpr bool kDeviation = true;
     static __device__ __forceinline__ float load(const __nv_bfloat16* p) { return __bfloat162float(__ldg(p)); }
+    static __device__ __forceinline__ float val(__nv_bfloat16 v) { return __bfloat162float(v); }
+    static __device__ __forceinline__ float round(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
     static __device__ __forceinline__ void store(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
 };
 
 // Lattice storage: 2*19 population planes of `slot` elements each, slot
-// index a*19 + k; inside a slot, node (x, y, z) at z*plane + y*px + x with the
-// row pitch px a multiple of 32 elements.
+// index a*19 + k. Inside a slot, node (x, y, z) sits at
+//   z*plane + (y + 1)*px + (x + gx),
+// i.e. every row carries gx ghost elements on each side (16 bytes) and every
+// plane one ghost row on each side. Ghost column x = -1 mirrors x = nx-1,
+// x = nx mirrors x = 0, and likewise for rows y = -1 and y = ny; every
+// writer keeps the images current, so a tile plus its one-node ring is a
+// contiguous, 16-byte aligned box even on the periodic edges.
 struct Layout {
-    int nx, ny, nz, px;
+    int nx, ny, nz, px, gx;
     long long plane, slot;
+    __host__ __device__ __forceinline__ long long off(int x, int y, int z) const
+    {
+        return (long long)z * plane + (long long)(y + 1) * px + (x + gx);
+    }
 };
+
+// Store v for node (x, y) of the plane at zoff into slot base p, with the
+// ghost images of edge nodes.
+template <class S>
+__device__ __forceinline__ void put(S* __restrict__ p, const Layout& L, int x, int y, long long zoff, float v)
+{
+    const long long row = zoff + (long long)(y + 1) * L.px + L.gx;
+    const bool xl = x == L.nx - 1, xr = x == 0;
+    Codec<S>::store(p + row + x, v);
+    if (xl) Codec<S>::store(p + row - 1, v);
+    if (xr) Codec<S>::store(p + row + L.nx, v);
+    if (y == L.ny - 1) {
+        const long long g = zoff + L.gx;  // row y = -1
+        Codec<S>::store(p + g + x, v);
+        if (xl) Codec<S>::store(p + g - 1, v);
+        if (xr) Codec<S>::store(p + g + L.nx, v);
+    }
+    if (y == 0) {
+        const long long g = zoff + (long long)(L.ny + 1) * L.px + L.gx;  // row y = ny
+        Codec<S>::store(p + g + x, v);
+        if (xl) Codec<S>::store(p + g - 1, v);
+        if (xr) Codec<S>::store(p + g + L.nx, v);
+    }
+}
 
 // Parameters as the kernels use them.
 struct KParams {
@@ -85,6 +125,7 @@ struct StepArgs {
     const S* __restrict__ src;
     S* __restrict__ dst;
     const uint32_t* __restrict__ nbmask;  // general geometry: bit k = (x + c_k solid), bit 31 = x solid
+    int* err;                             // device status word (bounded waits that gave up)
     Layout L;
     KParams P;
     int tiles_x, tiles_y;
@@ -95,5 +136,9 @@ struct StepArgs {
 constexpr uint32_t kSelfSolid = 1u << 31;
 
 __host__ __device__ __forceinline__ int wrapi(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
+
+// ghost columns per row side: 16 bytes
+template <class S>
+__host__ __device__ constexpr int ghost_x() { return 16 / (int)sizeof(S); }
 
 }  // namespace lbsc

@@ -1,0 +1,311 @@
+// Fused time step (Sec. 2) for the planar-wall geometry, with the next
+// planes' populations staged into shared memory by TMA.
+//
+// A CTA owns a 32 x TY tile of columns and a z segment, as in the
+// load-from-global kernel, but one thread streams whole planes of the tile
+// plus its one-node ring (all 38 population slots, one 5-D tensor box per
+// plane) into an NS-deep ring of shared-memory stages with
+// cp.async.bulk.tensor, completion tracked by one mbarrier per stage. The
+// compute warps reduce a landed plane to rho, j and psi out of shared memory
+// while the following planes are in flight, then collide and push the plane
+// below. Periodic x and y need no special case: the storage's ghost columns
+// and rows (kept current by every writer) make the tile plus ring one
+// 16-byte aligned box. Every wait is bounded: a wait that gives up writes an
+// error status, drains the CTA's copies in flight and leaves the kernel.
+#pragma once
+
+#include <cuda.h>
+
+#include "lb_fields.cuh"
+#include "step_common.cuh"
+
+namespace lbsc {
+
+constexpr uint32_t kSpinLimit = 1u << 22;  // try_wait rounds before a wait gives up
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// bounded wait for the completion of the phase with the given parity
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity)
+{
+    for (uint32_t i = 0; i < kSpinLimit; ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void tma_load_5d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1, int c2,
+                                            int c3, int c4)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Geometry of one stage: the box [a][k][row][col] of 2 x 19 x (TY+2) x BX
+// elements; column c holds x = x0 - GX + c, row r holds y = y0 - 1 + r.
+template <class S, int TY>
+struct TmaGeom {
+    static constexpr int TX = 32, HX = TX + 2, HY = TY + 2;
+    static constexpr int GX = ghost_x<S>();
+    static constexpr int BX = sizeof(S) == 4 ? 40 : 48;  // >= 32 + 2 GX, a multiple of 16 bytes
+    static constexpr int STAGE_ELEMS = 2 * Q * HY * BX;
+    static constexpr uint32_t STAGE_BYTES = STAGE_ELEMS * sizeof(S);
+    static constexpr int PSI_FLOATS = 4 * 2 * HY * HX;
+    static constexpr size_t smem(int NS) { return 128 + (size_t)NS * STAGE_BYTES + PSI_FLOATS * 4 + NS * 8; }
+};
+
+template <class S, int TY, int NS, bool kTauOne>
+__global__ void __launch_bounds__(32 * TY) step_tma_kernel(const __grid_constant__ CUtensorMap tmap, const StepArgs<S> A)
+{
+    using G = TmaGeom<S, TY>;
+    constexpr int TX = 32, NT = TX * TY, HX = G::HX, HY = G::HY, GX = G::GX, BX = G::BX;
+    constexpr int RING = 2 * HX + 2 * TY;
+    constexpr int NIT = (2 * RING + NT - 1) / NT;
+    static_assert(G::STAGE_BYTES % 128 == 0, "stages must stay 128-byte aligned");
+
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
+    S* stages = (S*)base;
+    float* sp = (float*)(base + (size_t)NS * G::STAGE_BYTES);  // psi ring [4][2][HY][HX]
+    uint64_t* bar = (uint64_t*)(sp + G::PSI_FLOATS);
+
+    const Layout L = A.L;
+    const int nx = L.nx, ny = L.ny, nz = L.nz;
+    const long long plane = L.plane;
+    S* __restrict__ dst = A.dst;
+    const float eta[2] = {A.P.eta[0], A.P.eta[1]};
+    const float ref[2] = {A.P.ref[0], A.P.ref[1]};
+    const float tau[2] = {A.P.tau[0], A.P.tau[1]};
+    const float itau[2] = {A.P.itau[0], A.P.itau[1]};
+    const float gk = A.P.gk, Gax = A.P.Gax, Gdi = A.P.Gdi;
+    const int tid = threadIdx.x, tx = tid % TX, ty = tid / TX;
+    const int ncol = A.tiles_x * A.tiles_y;
+    const int nzf = A.zhi - A.zlo;
+
+    if (tid == 0) {
+        for (int s = 0; s < NS; ++s) mbar_init(&bar[s], 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    uint32_t g = 0;  // planes this CTA has issued and consumed so far
+
+    for (int item = blockIdx.x; item < ncol * A.nseg; item += gridDim.x) {
+        const int col = item % ncol, seg = item / ncol;
+        const int za = A.zlo + (int)((long long)seg * nzf / A.nseg);
+        const int zb = A.zlo + (int)((long long)(seg + 1) * nzf / A.nseg);
+        if (za >= zb) continue;
+        const int x0 = (col % A.tiles_x) * TX, y0 = (col / A.tiles_x) * TY;
+        const int gx = x0 + tx, gy = y0 + ty;
+        const bool valid = gx < nx && gy < ny;
+        const int np = zb - za + 2;  // planes za-1 .. zb
+
+        int it_sm[NIT], it_st[NIT], it_a[NIT];
+#pragma unroll
+        for (int i = 0; i < NIT; ++i) {
+            const int it = tid + i * NT;
+            it_a[i] = -1;
+            if (it < 2 * RING) {
+                const int a = it >= RING, r = it - a * RING;
+                int ix, iy;
+                if (r < HX) { ix = r; iy = 0; }
+                else if (r < 2 * HX) { ix = r - HX; iy = HY - 1; }
+                else if (r < 2 * HX + TY) { ix = 0; iy = r - 2 * HX + 1; }
+                else { ix = HX - 1; iy = r - 2 * HX - TY + 1; }
+                it_a[i] = a;
+                it_sm[i] = iy * HX + ix;
+                it_st[i] = iy * BX + ix - 1 + GX;
+            }
+        }
+
+        auto issue = [&](int zp, uint32_t gi) {
+            uint64_t* b = &bar[gi % NS];
+            if (zp == 0 || zp == nz - 1) {
+                mbar_arrive(b);  // a solid plane: nothing to load
+            } else {
+                fence_proxy_async();
+                mbar_expect_tx(b, G::STAGE_BYTES);
+                tma_load_5d(stages + (size_t)(gi % NS) * G::STAGE_ELEMS, &tmap, b, x0, y0, zp, 0, 0);
+            }
+        };
+
+        // wait for plane i of the item, reduce it to psi (tile + ring) and own
+        // moments, then refill its stage with plane i + NS
+        auto consume = [&](int i, float (&rho)[2], float (&j)[2][3], float (&v)[2][Q]) -> bool {
+            const int zp = za - 1 + i;
+            const uint32_t gi = g + i;
+            const bool ok = mbar_wait(&bar[gi % NS], (gi / NS) & 1u);
+            float* spl = sp + (zp & 3) * (2 * HY * HX);
+            const bool solid = zp == 0 || zp == nz - 1;
+            if (ok) {
+                const S* st = stages + (size_t)(gi % NS) * G::STAGE_ELEMS;
+#pragma unroll
+                for (int a = 0; a < 2; ++a) {
+                    float ps = eta[a];
+                    rho[a] = 0.f;
+                    j[a][0] = j[a][1] = j[a][2] = 0.f;
+                    if (!solid) {
+                        float w[Q];
+#pragma unroll
+                        for (int k = 0; k < Q; ++k) w[k] = Codec<S>::val(st[((a * Q + k) * HY + ty + 1) * BX + tx + GX]);
+                        rho[a] = rho_of<S>(w, ref[a]);
+                        mom_of<S>(w, j[a]);
+                        ps = psi_of(rho[a]);
+                        if constexpr (!kTauOne) {
+#pragma unroll
+                            for (int k = 0; k < Q; ++k) v[a][k] = w[k];
+                        }
+                    }
+                    spl[(a * HY + ty + 1) * HX + tx + 1] = ps;
+                }
+#pragma unroll
+                for (int q = 0; q < NIT; ++q) {
+                    if (it_a[q] < 0) continue;
+                    const int a = it_a[q];
+                    float ps = eta[a];
+                    if (!solid) {
+                        float w[Q];
+#pragma unroll
+                        for (int k = 0; k < Q; ++k) w[k] = Codec<S>::val(st[(a * Q + k) * HY * BX + it_st[q]]);
+                        ps = psi_of(rho_of<S>(w, ref[a]));
+                    }
+                    spl[a * HY * HX + it_sm[q]] = ps;
+                }
+            }
+            const bool bad = __syncthreads_or(!ok);
+            if (bad) {
+                if (tid == 0) {
+                    atomicExch(A.err, 1);
+                    for (int k2 = i; k2 < np && k2 < i + NS; ++k2) mbar_wait(&bar[(g + k2) % NS], ((g + k2) / NS) & 1u);
+                }
+                return false;
+            }
+            if (tid == 0 && i + NS < np) issue(zp + NS, gi + NS);
+            return true;
+        };
+
+        float rc[2], jc[2][3], vc[2][Q];
+        float rn[2], jn[2][3], vn[2][Q];
+        __syncthreads();  // the previous item's collide is done with the psi ring
+        if (tid == 0)
+            for (int i = 0; i < NS && i < np; ++i) issue(za - 1 + i, g + i);
+        if (!consume(0, rn, jn, vn)) return;
+        if (!consume(1, rc, jc, vc)) return;
+
+        Dest D;
+        D.xo[0] = wrapi(gx - 1, nx);
+        D.xo[1] = gx;
+        D.xo[2] = wrapi(gx + 1, nx);
+        D.yo[0] = wrapi(gy - 1, ny);
+        D.yo[1] = gy;
+        D.yo[2] = wrapi(gy + 1, ny);
+        D.nb = 0;
+
+        for (int z = za; z < zb; ++z) {
+            if (!consume(z - za + 2, rn, jn, vn)) return;
+            if (valid) {
+                float F[2][3];
+                sc_force<HX, HY>(sp + ((z - 1) & 3) * (2 * HY * HX), sp + (z & 3) * (2 * HY * HX),
+                                 sp + ((z + 1) & 3) * (2 * HY * HX), ty, tx, gk, Gax, Gdi, F);
+                D.zo[0] = (long long)(z - 1) * plane;
+                D.zo[1] = (long long)z * plane;
+                D.zo[2] = (long long)(z + 1) * plane;
+                D.bot = z - 1 == 0;
+                D.top = z + 1 == nz - 1;
+                collide_store<S, false, kTauOne>(rc, jc, vc, F, tau, itau, ref, dst, L, gx, gy, D);
+            }
+#pragma unroll
+            for (int a = 0; a < 2; ++a) {
+                rc[a] = rn[a];
+#pragma unroll
+                for (int d = 0; d < 3; ++d) jc[a][d] = jn[a][d];
+                if constexpr (!kTauOne) {
+#pragma unroll
+                    for (int k = 0; k < Q; ++k) vc[a][k] = vn[a][k];
+                }
+            }
+        }
+        g += np;
+    }
+}
+
+template <class S, int TY, int NS, bool T1>
+static cudaError_t tma_launch_one(const CUtensorMap& m, const StepArgs<S>& A, cudaStream_t st)
+{
+    const size_t smem = TmaGeom<S, TY>::smem(NS);
+    const int items = A.tiles_x * A.tiles_y * A.nseg;
+    step_tma_kernel<S, TY, NS, T1><<<items, 32 * TY, smem, st>>>(m, A);
+    return cudaGetLastError();
+}
+
+template <class S, int TY, int NS, bool T1>
+static cudaError_t tma_prepare_one()
+{
+    return cudaFuncSetAttribute(step_tma_kernel<S, TY, NS, T1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)TmaGeom<S, TY>::smem(NS));
+}
+
+template <class S, int TY, int NS, bool T1>
+static int tma_occ_one()
+{
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, step_tma_kernel<S, TY, NS, T1>, 32 * TY,
+                                                      TmaGeom<S, TY>::smem(NS)) != cudaSuccess)
+        return 1;
+    return n;
+}
+
+// Dispatch over the built (tile height, stages, tau == 1) combinations.
+// op 0: launch; op 1: set the shared-memory attribute; op 2: occupancy.
+template <class S>
+static long long tma_dispatch(int op, int ty, int ns, bool t1, const CUtensorMap* m, const StepArgs<S>* A,
+                              cudaStream_t st)
+{
+#define LBSC_TMA_CASE(TY_, NS_)                                                                       \
+    if (ty == TY_ && ns == NS_) {                                                                     \
+        if (op == 0) return t1 ? tma_launch_one<S, TY_, NS_, true>(*m, *A, st)                        \
+                               : tma_launch_one<S, TY_, NS_, false>(*m, *A, st);                      \
+        if (op == 1) {                                                                                \
+            cudaError_t e = tma_prepare_one<S, TY_, NS_, true>();                                     \
+            return e != cudaSuccess ? e : tma_prepare_one<S, TY_, NS_, false>();                      \
+        }                                                                                             \
+        return t1 ? tma_occ_one<S, TY_, NS_, true>() : tma_occ_one<S, TY_, NS_, false>();             \
+    }
+    LBSC_TMA_CASE(4, 2)
+    LBSC_TMA_CASE(4, 3)
+    LBSC_TMA_CASE(8, 2)
+    LBSC_TMA_CASE(8, 3)
+    if constexpr (sizeof(S) == 2) {
+        LBSC_TMA_CASE(16, 2)
+    }
+#undef LBSC_TMA_CASE
+    return op == 2 ? 0 : (long long)cudaErrorInvalidValue;
+}
+
+}  // namespace lbsc

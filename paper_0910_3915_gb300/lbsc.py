@@ -29,6 +29,8 @@ LB_ERR_UNSUPPORTED = -6
 LB_F32, LB_F16, LB_BF16 = 0, 1, 2
 PRECISIONS = {"f32": LB_F32, "f16": LB_F16, "bf16": LB_BF16}
 LB_WEIGHTS_UNIT, LB_WEIGHTS_W36 = 0, 1
+LB_STEP_AUTO, LB_STEP_LDG, LB_STEP_TMA = 0, 1, 2
+STEP_VARIANTS = {"auto": LB_STEP_AUTO, "ldg": LB_STEP_LDG, "tma": LB_STEP_TMA}
 
 
 class LBError(RuntimeError):
@@ -90,6 +92,7 @@ SIGNATURES = [
     ("lb_get_populations", _I, [_VP, _DP]),
     ("lb_set_populations", _I, [_VP, _DP]),
     ("lb_set_schedule", _I, [_VP, _I, _I]),
+    ("lb_set_step_variant", _I, [_VP, _I, _I]),
     ("lb_last_error", ctypes.c_char_p, [_VP]),
     ("lb_free", None, [_VP]),
 ]
@@ -193,6 +196,10 @@ class Lattice:
 
     def set_schedule(self, tile_y: int = 8, z_segments: int = 0) -> "Lattice":
         _check(load().lb_set_schedule(self._ctx, tile_y, z_segments), self._ctx)
+        return self
+
+    def set_step_variant(self, variant: str = "auto", stages: int = 0) -> "Lattice":
+        _check(load().lb_set_step_variant(self._ctx, STEP_VARIANTS[variant], int(stages)), self._ctx)
         return self
 
     # ------------------------------------------------------------ stepping

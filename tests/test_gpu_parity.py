@@ -105,7 +105,8 @@ def test_fully_periodic_one_step_from_random_populations(lbsc):
     st.n[:] = n0
     st.step(1)
     n1 = lat.populations()
-    assert np.max(np.abs(n1 - st.n) / np.abs(st.n)) < 1e-6
+    # far from equilibrium (|u| up to 0.3): FP32 rounding of the cubic polynomial
+    assert np.max(np.abs(n1 - st.n) / np.abs(st.n)) < 5e-6
 
 
 def test_fully_periodic_droplet_and_momentum(lbsc):
@@ -125,20 +126,40 @@ def test_fully_periodic_droplet_and_momentum(lbsc):
     assert np.abs(g[3][2:5] - p0).max() < 1e-6 * mass
 
 
-def test_schedules_are_bitwise_identical(lbsc):
-    """Tile height and z segmentation change only the work split, never a value."""
+@pytest.mark.parametrize("precision", ["f32", "f16", "bf16"])
+def test_schedules_are_bitwise_identical(lbsc, precision):
+    """Kernel variant (TMA-staged or load-from-global), stages, tile height and
+    z segmentation change only the work split, never a value."""
     nx, ny, nz = 37, 23, 21
     rr, rb = W.droplet_fields(nx, ny, nz, 7.0, seed=1)
     ref = None
-    for ty, seg in [(8, 1), (4, 3), (16, 2), (8, 5)]:
-        lat = lbsc.Lattice(rr, rb).set_schedule(ty, seg).set_params(**CONTACT, eta_wall_b=0.05)
+    configs = [("ldg", 0, 8, 1), ("tma", 2, 4, 3), ("tma", 3, 8, 2), ("tma", 2, 8, 5), ("ldg", 0, 16, 2),
+               ("auto", 0, 4, 0), ("tma", 3, 4, 1)]
+    if precision != "f32":
+        configs.append(("tma", 2, 16, 2))
+    for variant, stages, ty, seg in configs:
+        lat = lbsc.Lattice(rr, rb, precision).set_step_variant(variant, stages).set_schedule(ty, seg)
+        lat.set_params(**CONTACT, eta_wall_b=0.05, eta_wall_r=-0.05)
         lat.step(20)
-        out = lat.moments()[:2]
+        out = lat.populations()
         lat.close()
         if ref is None:
             ref = out
         else:
-            assert np.array_equal(out[0], ref[0]) and np.array_equal(out[1], ref[1])
+            fl = (W.wall_mask(nx, ny, nz) == 0)[None, None]
+            assert np.array_equal(np.where(fl, out, 0), np.where(fl, ref, 0)), (variant, stages, ty, seg)
+
+
+def test_ldg_variant_parity(lbsc):
+    """The load-from-global kernel on the planar-wall geometry against the oracle."""
+    nx, ny, nz = 45, 27, 19
+    rr, rb = W.droplet_fields(nx, ny, nz, 9.0, seed=4)
+    prm = dict(CONTACT, eta_wall_r=-0.03, eta_wall_b=0.03)
+    lat = lbsc.Lattice(rr, rb).set_step_variant("ldg").set_params(**prm)
+    lat.step(100)
+    g = lat.moments()
+    o = oracle.State(rr, rb, W.wall_mask(nx, ny, nz), oracle.Params(**prm)).step(100).moments()
+    assert rel_err(g, o, W.wall_mask(nx, ny, nz)) <= 1e-5
 
 
 def test_graph_replay_matches_eager(lbsc):
@@ -178,7 +199,8 @@ def test_mass_conservation_fp64_sums(lbsc):
     m0 = lat.conservation()[:2]
     lat.step(1000)
     m1 = lat.conservation()[:2]
-    assert np.all(np.abs(m1 - m0) / m0 < 1e-5)
+    # the rest population carries each node's mass remainder: FP32 rounding only, no bias
+    assert np.all(np.abs(m1 - m0) / m0 < 1e-6)
     ref = oracle.State(rr, rb, W.wall_mask(nx, ny, nz), oracle.Params(**CONTACT)).moments()[3]
     assert np.allclose(m0, ref[:2], rtol=1e-6)
 
