@@ -75,16 +75,18 @@ static size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
 static size_t elem_size_of(int prec) { return prec == LB_F32 ? 4 : 2; }
 
-// rows of nx nodes with 16 bytes of ghost images on each side, one ghost row
-// above and below each plane
+// rows of nx nodes behind 128 bytes of left padding (x = 0 starts a line; the
+// ghost column x = -1 is its last element), at least one ghost column on the
+// right, pitch a multiple of 128 bytes; one ghost row above and below each plane
 static Layout make_layout(int nx, int ny, int nz, int prec)
 {
     Layout L;
+    const int line = (int)(128 / elem_size_of(prec));
     L.nx = nx;
     L.ny = ny;
     L.nz = nz;
-    L.gx = (int)(16 / elem_size_of(prec));
-    L.px = (nx + 2 * L.gx + 31) / 32 * 32;
+    L.gx = line;
+    L.px = (L.gx + nx + 1 + line - 1) / line * line;
     L.plane = (long long)L.px * (ny + 2);
     L.slot = (L.plane * nz + 127) / 128 * 128;
     return L;

@@ -73,11 +73,12 @@ struct Codec<__nv_bfloat16> {
 // Lattice storage: 2*19 population planes of `slot` elements each, slot
 // index a*19 + k. Inside a slot, node (x, y, z) sits at
 //   z*plane + (y + 1)*px + (x + gx),
-// i.e. every row carries gx ghost elements on each side (16 bytes) and every
-// plane one ghost row on each side. Ghost column x = -1 mirrors x = nx-1,
-// x = nx mirrors x = 0, and likewise for rows y = -1 and y = ny; every
-// writer keeps the images current, so a tile plus its one-node ring is a
-// contiguous, 16-byte aligned box even on the periodic edges.
+// with gx = 128 bytes of row padding on the left (so x = 0 starts a 128-byte
+// line) and at least one element on the right, and one ghost row above and
+// below each plane. Ghost column x = -1 mirrors x = nx-1, x = nx mirrors
+// x = 0, and likewise rows y = -1 and y = ny; every writer keeps the images
+// current, so a tile plus its one-node ring is one box even on the periodic
+// edges.
 struct Layout {
     int nx, ny, nz, px, gx;
     long long plane, slot;
@@ -87,14 +88,12 @@ struct Layout {
     }
 };
 
-// Store v for node (x, y) of the plane at zoff into slot base p, with the
-// ghost images of edge nodes.
+// Write the ghost images (only) of node (x, y) of the plane at zoff.
 template <class S>
-__device__ __forceinline__ void put(S* __restrict__ p, const Layout& L, int x, int y, long long zoff, float v)
+__device__ __forceinline__ void put_ghosts(S* __restrict__ p, const Layout& L, int x, int y, long long zoff, float v)
 {
     const long long row = zoff + (long long)(y + 1) * L.px + L.gx;
     const bool xl = x == L.nx - 1, xr = x == 0;
-    Codec<S>::store(p + row + x, v);
     if (xl) Codec<S>::store(p + row - 1, v);
     if (xr) Codec<S>::store(p + row + L.nx, v);
     if (y == L.ny - 1) {
@@ -109,6 +108,21 @@ __device__ __forceinline__ void put(S* __restrict__ p, const Layout& L, int x, i
         if (xl) Codec<S>::store(p + g - 1, v);
         if (xr) Codec<S>::store(p + g + L.nx, v);
     }
+}
+
+// 1 if node (x, y) has a ghost image
+__host__ __device__ __forceinline__ bool has_ghost(const Layout& L, int x, int y)
+{
+    return x == 0 || x == L.nx - 1 || y == 0 || y == L.ny - 1;
+}
+
+// Store v for node (x, y) of the plane at zoff into slot base p, with the
+// ghost images of edge nodes.
+template <class S>
+__device__ __forceinline__ void put(S* __restrict__ p, const Layout& L, int x, int y, long long zoff, float v)
+{
+    Codec<S>::store(p + zoff + (long long)(y + 1) * L.px + L.gx + x, v);
+    if (has_ghost(L, x, y)) put_ghosts<S>(p, L, x, y, zoff, v);
 }
 
 // Parameters as the kernels use them.
@@ -137,7 +151,7 @@ constexpr uint32_t kSelfSolid = 1u << 31;
 
 __host__ __device__ __forceinline__ int wrapi(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
 
-// ghost columns per row side: 16 bytes
+// elements in 16 bytes: the ring column a TMA box carries on each side of a tile
 template <class S>
 __host__ __device__ constexpr int ghost_x() { return 16 / (int)sizeof(S); }
 

@@ -126,13 +126,7 @@ __global__ void __launch_bounds__(32 * TY) step_kernel(const StepArgs<S> A)
         fill(za, rc, jc, vc);
 
         Dest D;
-        D.xo[0] = wrapi(gx - 1, nx);
-        D.xo[1] = gx;
-        D.xo[2] = wrapi(gx + 1, nx);
-        D.yo[0] = wrapi(gy - 1, ny);
-        D.yo[1] = gy;
-        D.yo[2] = wrapi(gy + 1, ny);
-        D.nb = 0;
+        D.set_column(L, valid ? gx : 0, valid ? gy : 0);
 
         for (int z = za; z < zb; ++z) {
             fill(z + 1, rn, jn, vn);

@@ -84,9 +84,37 @@ __device__ __forceinline__ void sc_force(const float* s0, const float* s1, const
 // z, z+1, and which links end on a wall.
 struct Dest {
     int xo[3], yo[3];  // x-1, x, x+1 and y-1, y, y+1, wrapped
+    long long ro[3];   // row offsets of y-1, y, y+1 (incl. the left padding)
     long long zo[3];   // plane offsets of z-1, z, z+1
+    uint32_t gmask;    // bit (dx+1) + 3 (dy+1): that neighbour column/row has ghost images
     bool bot, top;     // planar walls: solid plane below / above
     uint32_t nb;       // general geometry: bit k = link k ends on a solid node
+
+    // per-thread part that stays fixed while the thread marches in z
+    __device__ __forceinline__ void set_column(const Layout& L, int x, int y)
+    {
+        xo[0] = wrapi(x - 1, L.nx);
+        xo[1] = x;
+        xo[2] = wrapi(x + 1, L.nx);
+        yo[0] = wrapi(y - 1, L.ny);
+        yo[1] = y;
+        yo[2] = wrapi(y + 1, L.ny);
+        gmask = 0;
+#pragma unroll
+        for (int dy = 0; dy < 3; ++dy) {
+            ro[dy] = (long long)(yo[dy] + 1) * L.px + L.gx;
+#pragma unroll
+            for (int dx = 0; dx < 3; ++dx)
+                if (has_ghost(L, xo[dx], yo[dy])) gmask |= 1u << (dx + 3 * dy);
+        }
+        nb = 0;
+    }
+    template <class S>
+    __device__ __forceinline__ void store(S* __restrict__ p, const Layout& L, int dx, int dy, int dz, float v) const
+    {
+        Codec<S>::store(p + zo[dz + 1] + ro[dy + 1] + xo[dx + 1], v);
+        if ((gmask >> ((dx + 1) + 3 * (dy + 1))) & 1u) put_ghosts<S>(p, L, xo[dx + 1], yo[dy + 1], zo[dz + 1], v);
+    }
 };
 
 // BGK with the force-shifted cubic equilibrium and the push with mid-grid
@@ -143,13 +171,13 @@ __device__ __forceinline__ void collide_store(const float (&rc)[2], const float 
             bool wall;
             if constexpr (kGeneral) wall = (D.nb >> k) & 1u;
             else wall = (cz(k) < 0 && D.bot) || (cz(k) > 0 && D.top);
-            if (wall) put<S>(dbase + (long long)opp(k) * L.slot, L, x, y, D.zo[1], s);
-            else put<S>(dbase + (long long)k * L.slot, L, D.xo[cx(k) + 1], D.yo[cy(k) + 1], D.zo[cz(k) + 1], s);
+            if (wall) D.store<S>(dbase + (long long)opp(k) * L.slot, L, 0, 0, 0, s);
+            else D.store<S>(dbase + (long long)k * L.slot, L, cx(k), cy(k), cz(k), s);
         }
         float s0;
         if constexpr (Codec<S>::kDeviation) s0 = 3.0f * (dref - (sax * (1.0f / 18.0f) + sdi * (1.0f / 36.0f)));
         else s0 = r - sum;
-        put<S>(dbase, L, x, y, D.zo[1], s0);
+        D.store<S>(dbase, L, 0, 0, 0, s0);
     }
 }
 

@@ -69,7 +69,8 @@ __device__ __forceinline__ void tma_load_5d(void* dst, const CUtensorMap* map, u
 }
 
 // Geometry of one stage: the box [a][k][row][col] of 2 x 19 x (TY+2) x BX
-// elements; column c holds x = x0 - GX + c, row r holds y = y0 - 1 + r.
+// elements; column c holds x = x0 - GX + c (16 bytes of columns left of the
+// tile, so the box starts on a 16-byte boundary), row r holds y = y0 - 1 + r.
 template <class S, int TY>
 struct TmaGeom {
     static constexpr int TX = 32, HX = TX + 2, HY = TY + 2;
@@ -151,7 +152,7 @@ __global__ void __launch_bounds__(32 * TY) step_tma_kernel(const __grid_constant
             } else {
                 fence_proxy_async();
                 mbar_expect_tx(b, G::STAGE_BYTES);
-                tma_load_5d(stages + (size_t)(gi % NS) * G::STAGE_ELEMS, &tmap, b, x0, y0, zp, 0, 0);
+                tma_load_5d(stages + (size_t)(gi % NS) * G::STAGE_ELEMS, &tmap, b, x0 + L.gx - GX, y0, zp, 0, 0);
             }
         };
 
@@ -219,13 +220,7 @@ __global__ void __launch_bounds__(32 * TY) step_tma_kernel(const __grid_constant
         if (!consume(1, rc, jc, vc)) return;
 
         Dest D;
-        D.xo[0] = wrapi(gx - 1, nx);
-        D.xo[1] = gx;
-        D.xo[2] = wrapi(gx + 1, nx);
-        D.yo[0] = wrapi(gy - 1, ny);
-        D.yo[1] = gy;
-        D.yo[2] = wrapi(gy + 1, ny);
-        D.nb = 0;
+        D.set_column(L, valid ? gx : 0, valid ? gy : 0);
 
         for (int z = za; z < zb; ++z) {
             if (!consume(z - za + 2, rn, jn, vn)) return;
