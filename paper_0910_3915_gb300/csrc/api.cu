@@ -46,6 +46,7 @@ struct lb_ctx {
     CUtensorMap tmap[2][3];                  // per buffer, per tile height 4/8/16
     bool tmap_ok[2][3] = {{false, false, false}, {false, false, false}};
     int* dev_err = nullptr;                  // device status word of the step kernels
+    bool ghost_ok = true;                    // ghost images of the current buffer are current
     static constexpr int kGraphSteps = 32;
     std::string err;
 };
@@ -275,10 +276,29 @@ static StepArgs<S> step_args(lb_ctx* c, int src)
 }
 
 template <class S>
+static cudaError_t refresh_ghosts(lb_ctx* c, int buf, cudaStream_t st)
+{
+    return launch_ghosts<S>(c->L, (S*)c->f[buf], c->zlo, c->zhi, st);
+}
+
+static cudaError_t refresh_ghosts_any(lb_ctx* c, int buf, cudaStream_t st)
+{
+    switch (c->prec) {
+    case LB_F32: return refresh_ghosts<float>(c, buf, st);
+    case LB_F16: return refresh_ghosts<__half>(c, buf, st);
+    default: return refresh_ghosts<__nv_bfloat16>(c, buf, st);
+    }
+}
+
+// one TMA-staged step, then the ghost images of its output
+template <class S>
 static cudaError_t launch_tma(lb_ctx* c, int parity, int ns, cudaStream_t st)
 {
     const StepArgs<S> A = step_args<S>(c, parity);
-    return (cudaError_t)tma_step<S>(0, c->tile_y, ns, tau_one(c), &c->tmap[parity][tile_index(c->tile_y)], &A, st);
+    cudaError_t e =
+        (cudaError_t)tma_step<S>(0, c->tile_y, ns, tau_one(c), &c->tmap[parity][tile_index(c->tile_y)], &A, st);
+    if (e != cudaSuccess) return e;
+    return refresh_ghosts<S>(c, 1 - parity, st);
 }
 
 static cudaError_t launch_steps(lb_ctx* c, int n, int& parity, cudaStream_t st)
@@ -544,6 +564,11 @@ int lb_step(lb_ctx* c, int nsteps)
     if (!c || nsteps < 0) return fail(c, LB_ERR_ARG, "lb_step: bad argument");
     const int G = lb_ctx::kGraphSteps;
     int n = nsteps;
+    const int ns = tma_stages(c);
+    if (ns && !c->ghost_ok && n > 0) {  // the TMA path reads the source's ghost images
+        LB_CUDA(c, refresh_ghosts_any(c, c->cur, c->stream));
+        c->ghost_ok = true;
+    }
     if (n >= G) {
         int& par = c->cur;
         if (!c->graph[par]) {
@@ -569,6 +594,7 @@ int lb_step(lb_ctx* c, int nsteps)
     if (e != cudaSuccess) return cuda_fail(c, e, "lb_step: launch");
     c->cur = par;
     c->steps += nsteps;
+    if (nsteps > 0) c->ghost_ok = ns != 0;  // only the TMA path leaves the images current
     return LB_OK;
 }
 
@@ -792,6 +818,7 @@ int lb_load(lb_ctx* c, const void* host, size_t bytes)
     LB_CUDA(c, cudaMemcpyAsync(c->f[c->cur], (const char*)host + sizeof(h), pb, cudaMemcpyHostToDevice, c->stream));
     LB_CUDA(c, cudaStreamSynchronize(c->stream));
     c->steps = h.steps;
+    c->ghost_ok = false;
     return LB_OK;
 }
 

@@ -244,6 +244,47 @@ __global__ void __launch_bounds__(kRedThreads) angle_kernel(FieldArgs F, Scratch
     block_reduce<kAngleVals>(acc, 1u, part);
 }
 
+// ---------------------------------------------------------------- ghost images
+// Refresh the ghost columns x = -1, nx and rows y = -1, ny (corners
+// included) of planes [z0, z1) from the real nodes they mirror.
+template <class S>
+__global__ void ghost_kernel(Layout L, S* __restrict__ f, int z0, int z1)
+{
+    const int per_plane = 2 * L.ny + 2 * (L.nx + 2);
+    const long long total = (long long)2 * Q * (z1 - z0) * per_plane;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+        const int item = (int)(i % per_plane);
+        const long long rest = i / per_plane;
+        const int z = z0 + (int)(rest % (z1 - z0));
+        const int ak = (int)(rest / (z1 - z0));
+        S* p = f + (long long)ak * L.slot;
+        int sx, sy, gx, gy;  // source node, ghost position
+        if (item < 2 * L.ny) {
+            sy = gy = item >> 1;
+            gx = (item & 1) ? L.nx : -1;
+            sx = (item & 1) ? 0 : L.nx - 1;
+        } else {
+            const int r = item - 2 * L.ny;
+            gx = (r >> 1) - 1;  // -1 .. nx
+            sx = wrapi(gx, L.nx);
+            gy = (r & 1) ? L.ny : -1;
+            sy = (r & 1) ? 0 : L.ny - 1;
+        }
+        p[L.off(gx, gy, z)] = p[L.off(sx, sy, z)];
+    }
+}
+
+template <class S>
+cudaError_t launch_ghosts(const Layout& L, S* f, int z0, int z1, cudaStream_t st)
+{
+    if (z1 <= z0) return cudaSuccess;
+    const long long total = (long long)2 * Q * (z1 - z0) * (2 * L.ny + 2 * (L.nx + 2));
+    long long b = (total + 255) / 256;
+    if (b > 4096) b = 4096;
+    ghost_kernel<S><<<(int)b, 256, 0, st>>>(L, f, z0, z1);
+    return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------- population copies
 template <class S>
 __global__ void get_pop_kernel(FieldArgs F, const S* __restrict__ f, double* __restrict__ out)
@@ -335,7 +376,8 @@ cudaError_t launch_set_pop(const FieldArgs& F, S* f, const double* in, cudaStrea
     template cudaError_t launch_conservation<S>(const FieldArgs&, const S*, double*, double*, cudaStream_t); \
     template cudaError_t launch_fields<S>(const FieldArgs&, const S*, const Scratch&, bool, cudaStream_t); \
     template cudaError_t launch_get_pop<S>(const FieldArgs&, const S*, double*, cudaStream_t);       \
-    template cudaError_t launch_set_pop<S>(const FieldArgs&, S*, const double*, cudaStream_t);
+    template cudaError_t launch_set_pop<S>(const FieldArgs&, S*, const double*, cudaStream_t);   \
+    template cudaError_t launch_ghosts<S>(const Layout&, S*, int, int, cudaStream_t);
 LBSC_INST(float)
 LBSC_INST(__half)
 LBSC_INST(__nv_bfloat16)

@@ -76,9 +76,10 @@ struct Codec<__nv_bfloat16> {
 // with gx = 128 bytes of row padding on the left (so x = 0 starts a 128-byte
 // line) and at least one element on the right, and one ghost row above and
 // below each plane. Ghost column x = -1 mirrors x = nx-1, x = nx mirrors
-// x = 0, and likewise rows y = -1 and y = ny; every writer keeps the images
-// current, so a tile plus its one-node ring is one box even on the periodic
-// edges.
+// x = 0, and likewise rows y = -1 and y = ny, so a tile plus its one-node
+// ring is one box even on the periodic edges. The step kernels write real
+// nodes only; the images are refreshed by a separate pass where a reader
+// needs them (the TMA-staged step).
 struct Layout {
     int nx, ny, nz, px, gx;
     long long plane, slot;

@@ -82,11 +82,12 @@ __device__ __forceinline__ void sc_force(const float* s0, const float* s1, const
 
 // Where the node's populations go: neighbours (wrapped), the planes of z-1,
 // z, z+1, and which links end on a wall.
+// Ghost images are not written here: the TMA path refreshes them in a
+// separate pass (ghost_kernel) after each step.
 struct Dest {
     int xo[3], yo[3];  // x-1, x, x+1 and y-1, y, y+1, wrapped
     long long ro[3];   // row offsets of y-1, y, y+1 (incl. the left padding)
     long long zo[3];   // plane offsets of z-1, z, z+1
-    uint32_t gmask;    // bit (dx+1) + 3 (dy+1): that neighbour column/row has ghost images
     bool bot, top;     // planar walls: solid plane below / above
     uint32_t nb;       // general geometry: bit k = link k ends on a solid node
 
@@ -99,21 +100,14 @@ struct Dest {
         yo[0] = wrapi(y - 1, L.ny);
         yo[1] = y;
         yo[2] = wrapi(y + 1, L.ny);
-        gmask = 0;
 #pragma unroll
-        for (int dy = 0; dy < 3; ++dy) {
-            ro[dy] = (long long)(yo[dy] + 1) * L.px + L.gx;
-#pragma unroll
-            for (int dx = 0; dx < 3; ++dx)
-                if (has_ghost(L, xo[dx], yo[dy])) gmask |= 1u << (dx + 3 * dy);
-        }
+        for (int dy = 0; dy < 3; ++dy) ro[dy] = (long long)(yo[dy] + 1) * L.px + L.gx;
         nb = 0;
     }
     template <class S>
-    __device__ __forceinline__ void store(S* __restrict__ p, const Layout& L, int dx, int dy, int dz, float v) const
+    __device__ __forceinline__ void store(S* __restrict__ p, const Layout&, int dx, int dy, int dz, float v) const
     {
         Codec<S>::store(p + zo[dz + 1] + ro[dy + 1] + xo[dx + 1], v);
-        if ((gmask >> ((dx + 1) + 3 * (dy + 1))) & 1u) put_ghosts<S>(p, L, xo[dx + 1], yo[dy + 1], zo[dz + 1], v);
     }
 };
 
