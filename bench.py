@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="single")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--schedule", default=None,
+                    help="fixed step schedule variant:stages:tile_y:z_segments (e.g. ldg:0:4:16); skips tuning")
     return ap.parse_args()
 
 
@@ -197,7 +199,11 @@ def run_ours(args):
 
     lat = lbsc.Lattice(rr, rb, prec).set_params(**prm)
     schedule = None
-    if not args.no_tune:
+    if args.schedule:
+        v, ns, ty, seg = args.schedule.split(":")
+        schedule = (v, int(ns), int(ty), int(seg))
+        tune.apply(lat, schedule)
+    elif not args.no_tune:
         schedule, _ = tune.tune(lat)
     lat.step(Wm)
     lat.sync()
