@@ -52,7 +52,7 @@ extern "C" {
 #define LB_BF16 2  /* BF16 deviations, as above */
 
 /* step kernel variants (lb_set_step_variant) */
-#define LB_STEP_AUTO 0  /* TMA-staged kernel for planar walls, load-from-global otherwise */
+#define LB_STEP_AUTO 0  /* the load-from-global kernel (measured the faster one on GB300) */
 #define LB_STEP_LDG 1   /* every plane loaded from global memory by the compute threads */
 #define LB_STEP_TMA 2   /* planes staged into shared memory by TMA (planar walls only) */
 
@@ -92,7 +92,9 @@ typedef struct {
 } lb_droplet;
 
 /* Create a context on the current CUDA device.
- * nx, ny, nz >= 1 (nz >= 3 with the default walls); precision LB_F32/LB_F16/LB_BF16.
+ * nx, ny, nz >= 1 (nz >= 3 with the default walls), and one population plane
+ * set (padded rows times ny+2 rows times nz) below 2^31 elements, i.e. up to
+ * about 1.9e9 nodes; precision LB_F32/LB_F16/LB_BF16.
  * rho_r, rho_b: host arrays (nx*ny*nz doubles) of initial densities; populations
  * start at rest equilibrium n_k = zeta_k rho (Eq. Equil at u = 0). Values on
  * solid nodes are ignored. For 16-bit storage the deviation reference rho_ref

@@ -110,7 +110,13 @@ static Plan make_plan(const Layout& L, int prec)
     return p;
 }
 
-static bool dims_ok(int nx, int ny, int nz) { return nx >= 1 && ny >= 1 && nz >= 1 && (long long)nx * ny * nz <= (1LL << 34); }
+// the kernels address a node inside a population slot with a 32-bit offset
+static bool dims_ok(int nx, int ny, int nz)
+{
+    if (nx < 1 || ny < 1 || nz < 1) return false;
+    const long long px = ((long long)nx + 64 + 1 + 63) / 64 * 64;
+    return px * ((long long)ny + 2) * nz < (1LL << 31) - 256;
+}
 
 static FieldArgs field_args(const lb_ctx* c)
 {
@@ -203,7 +209,7 @@ static cudaError_t tma_prepare(lb_ctx* c)
 // stages used by the TMA kernel for the current schedule, 0 if not available
 static int tma_stages(lb_ctx* c)
 {
-    if (c->general || c->variant == LB_STEP_LDG) return 0;
+    if (c->general || c->variant != LB_STEP_TMA) return 0;  // AUTO: load-from-global (measured faster)
     const int want[2] = {c->stages ? c->stages : 3, c->stages ? c->stages : 2};
     for (int ns : want) {
         // occupancy 0: the pair is not built for this precision (or does not fit)

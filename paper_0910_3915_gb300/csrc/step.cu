@@ -3,22 +3,18 @@
 //
 // Design: populations are double-buffered (read src, write dst), structure of
 // arrays, one 32-node row segment per warp. A CTA owns a tile of 32 x TY
-// columns and a range of z planes and marches upward in z. At each plane it
-// loads the next plane's populations, reduces them to rho, j and psi, and
-// keeps psi for planes z-1..z+2 (tile plus a one-node ring) in shared memory;
-// the ring nodes' psi comes from their populations in src, which no CTA
-// writes during the step. psi never travels through HBM.
+// columns and a range of z planes and marches upward in z. For plane z it
+// collides, with psi of planes z-1..z+1 (tile plus a one-node ring) held in a
+// four-plane shared-memory ring; the ring nodes' psi comes from their
+// populations in src, which no CTA writes during the step, so psi never
+// travels through HBM. Loads run two planes ahead of the collision: the raw
+// populations of plane z+2 are requested into registers before plane z is
+// collided and reduced to rho, j and psi one iteration later, so memory
+// latency overlaps the arithmetic of the plane below.
 #include "lb_fields.cuh"
 #include "step_common.cuh"
 
 namespace lbsc {
-
-template <class S>
-__device__ __forceinline__ void load_comp(const S* __restrict__ p, long long slot, float (&v)[Q])
-{
-#pragma unroll
-    for (int k = 0; k < Q; ++k) v[k] = Codec<S>::load(p + k * slot);
-}
 
 template <class S, int TY, bool kGeneral, bool kTauOne>
 __global__ void __launch_bounds__(32 * TY) step_kernel(const StepArgs<S> A)
@@ -30,7 +26,8 @@ __global__ void __launch_bounds__(32 * TY) step_kernel(const StepArgs<S> A)
 
     const Layout L = A.L;
     const int nx = L.nx, ny = L.ny, nz = L.nz, px = L.px;
-    const long long plane = L.plane, slot = L.slot;
+    const int plane = (int)L.plane;
+    const long long slot = L.slot;
     const S* __restrict__ src = A.src;
     S* __restrict__ dst = A.dst;
     const uint32_t* __restrict__ nbmask = A.nbmask;
@@ -52,15 +49,16 @@ __global__ void __launch_bounds__(32 * TY) step_kernel(const StepArgs<S> A)
         const int gx = x0 + tx, gy = y0 + ty;
         const bool valid = gx < nx && gy < ny;
         const int ox = gx % nx, oy = gy % ny;  // ragged tiles: wrapped copy of a real column
-        const long long own = (long long)(oy + 1) * px + ox + L.gx;
+        const int own = (oy + 1) * px + ox + L.gx;
 
         // this thread's ring items: smem position, plane offset of the node, component
-        int it_sm[NIT], it_a[NIT];
-        long long it_off[NIT];
+        int it_sm[NIT], it_a[NIT], it_off[NIT];
 #pragma unroll
         for (int i = 0; i < NIT; ++i) {
             const int it = tid + i * NT;
             it_a[i] = -1;
+            it_sm[i] = 0;
+            it_off[i] = 0;
             if (it < 2 * RING) {
                 const int a = it >= RING, r = it - a * RING;
                 int ix, iy;
@@ -71,33 +69,54 @@ __global__ void __launch_bounds__(32 * TY) step_kernel(const StepArgs<S> A)
                 const int hx = ((x0 - 1 + ix) % nx + nx) % nx, hy = ((y0 - 1 + iy) % ny + ny) % ny;
                 it_a[i] = a;
                 it_sm[i] = iy * HX + ix;
-                it_off[i] = (long long)(hy + 1) * px + hx + L.gx;
+                it_off[i] = (hy + 1) * px + hx + L.gx;
             }
         }
 
-        // psi of plane zp (tile + ring) into its slot; own moments returned.
-        // Own populations stay in v when the collision needs them (tau != 1).
-        auto fill = [&](int zp, float (&rho)[2], float (&j)[2][3], float (&v)[2][Q]) {
+        // raw populations of the plane in flight (own node, ring items) and
+        // whether each node is solid
+        float ro_[2][Q], ri_[NIT][Q];
+        bool so_ = false, si_[NIT];
+
+        // request plane zp into the raw registers
+        auto issue = [&](int zp) {
             const int zw = kGeneral ? wrapi(zp, nz) : zp;
-            const long long zoff = (long long)zw * plane;
+            const int zoff = zw * plane;
+            if constexpr (kGeneral) so_ = (__ldg(nbmask + zoff + own) & kSelfSolid) != 0;
+            else so_ = (zp == 0 || zp == nz - 1);
+            if (!so_) {
+#pragma unroll
+                for (int a = 0; a < 2; ++a)
+#pragma unroll
+                    for (int k = 0; k < Q; ++k) ro_[a][k] = Codec<S>::load(src + (a * Q + k) * slot + (zoff + own));
+            }
+#pragma unroll
+            for (int i = 0; i < NIT; ++i) {
+                if (it_a[i] < 0) continue;
+                if constexpr (kGeneral) si_[i] = (__ldg(nbmask + zoff + it_off[i]) & kSelfSolid) != 0;
+                else si_[i] = so_;
+                if (!si_[i]) {
+#pragma unroll
+                    for (int k = 0; k < Q; ++k)
+                        ri_[i][k] = Codec<S>::load(src + (it_a[i] * Q + k) * slot + (zoff + it_off[i]));
+                }
+            }
+        };
+        // reduce the raw registers of plane zp: psi into its ring slot, own moments out
+        auto reduce = [&](int zp, float (&rho)[2], float (&j)[2][3], float (&v)[2][Q]) {
             float* spl = &sp[zp & 3][0][0][0];
-            bool solid;
-            if constexpr (kGeneral) solid = (__ldg(nbmask + zoff + own) & kSelfSolid) != 0;
-            else solid = (zp == 0 || zp == nz - 1);
 #pragma unroll
             for (int a = 0; a < 2; ++a) {
                 float ps = eta[a];
                 rho[a] = 0.f;
                 j[a][0] = j[a][1] = j[a][2] = 0.f;
-                if (!solid) {
-                    float w[Q];
-                    load_comp<S>(src + (long long)a * Q * slot + zoff + own, slot, w);
-                    rho[a] = rho_of<S>(w, ref[a]);
-                    mom_of<S>(w, j[a]);
+                if (!so_) {
+                    rho[a] = rho_of<S>(ro_[a], ref[a]);
+                    mom_of<S>(ro_[a], j[a]);
                     ps = psi_of(rho[a]);
                     if constexpr (!kTauOne) {
 #pragma unroll
-                        for (int k = 0; k < Q; ++k) v[a][k] = w[k];
+                        for (int k = 0; k < Q; ++k) v[a][k] = ro_[a][k];
                     }
                 }
                 spl[(a * HY + ty + 1) * HX + tx + 1] = ps;
@@ -106,36 +125,31 @@ __global__ void __launch_bounds__(32 * TY) step_kernel(const StepArgs<S> A)
             for (int i = 0; i < NIT; ++i) {
                 if (it_a[i] < 0) continue;
                 const int a = it_a[i];
-                bool hsolid;
-                if constexpr (kGeneral) hsolid = (__ldg(nbmask + zoff + it_off[i]) & kSelfSolid) != 0;
-                else hsolid = solid;
-                float ps = eta[a];
-                if (!hsolid) {
-                    float w[Q];
-                    load_comp<S>(src + (long long)a * Q * slot + zoff + it_off[i], slot, w);
-                    ps = psi_of(rho_of<S>(w, ref[a]));
-                }
-                spl[a * HY * HX + it_sm[i]] = ps;
+                spl[a * HY * HX + it_sm[i]] = si_[i] ? eta[a] : psi_of(rho_of<S>(ri_[i], ref[a]));
             }
         };
 
         float rc[2], jc[2][3], vc[2][Q];
         float rn[2], jn[2][3], vn[2][Q];
         __syncthreads();  // the previous item's readers are done with the ring
-        fill(za - 1, rn, jn, vn);
-        fill(za, rc, jc, vc);
+        issue(za - 1);
+        reduce(za - 1, rn, jn, vn);
+        issue(za);
+        reduce(za, rc, jc, vc);
+        issue(za + 1);
 
         Dest D;
         D.set_column(L, valid ? gx : 0, valid ? gy : 0);
 
         for (int z = za; z < zb; ++z) {
-            fill(z + 1, rn, jn, vn);
+            reduce(z + 1, rn, jn, vn);
+            if (z + 2 <= zb) issue(z + 2);
             __syncthreads();
 
             bool self_solid = false;
             if constexpr (kGeneral) {
                 if (valid) {
-                    D.nb = __ldg(nbmask + (long long)z * plane + own);
+                    D.nb = __ldg(nbmask + z * plane + own);
                     self_solid = (D.nb & kSelfSolid) != 0;
                 }
             }
@@ -144,13 +158,13 @@ __global__ void __launch_bounds__(32 * TY) step_kernel(const StepArgs<S> A)
                 sc_force<HX, HY>(&sp[(z - 1) & 3][0][0][0], &sp[z & 3][0][0][0], &sp[(z + 1) & 3][0][0][0], ty, tx,
                                  gk, Gax, Gdi, F);
                 if constexpr (kGeneral) {
-                    D.zo[0] = (long long)wrapi(z - 1, nz) * plane;
-                    D.zo[2] = (long long)wrapi(z + 1, nz) * plane;
+                    D.zo[0] = wrapi(z - 1, nz) * plane;
+                    D.zo[2] = wrapi(z + 1, nz) * plane;
                 } else {
-                    D.zo[0] = (long long)(z - 1) * plane;
-                    D.zo[2] = (long long)(z + 1) * plane;
+                    D.zo[0] = (z - 1) * plane;
+                    D.zo[2] = (z + 1) * plane;
                 }
-                D.zo[1] = (long long)z * plane;
+                D.zo[1] = z * plane;
                 D.bot = !kGeneral && z - 1 == 0;
                 D.top = !kGeneral && z + 1 == nz - 1;
                 collide_store<S, kGeneral, kTauOne>(rc, jc, vc, F, tau, itau, ref, dst, L, gx, gy, D);

@@ -83,11 +83,12 @@ __device__ __forceinline__ void sc_force(const float* s0, const float* s1, const
 // Where the node's populations go: neighbours (wrapped), the planes of z-1,
 // z, z+1, and which links end on a wall.
 // Ghost images are not written here: the TMA path refreshes them in a
-// separate pass (ghost_kernel) after each step.
+// separate pass (ghost_kernel) after each step. Addresses are a warp-uniform
+// slot base plus a 32-bit per-thread offset.
 struct Dest {
     int xo[3], yo[3];  // x-1, x, x+1 and y-1, y, y+1, wrapped
-    long long ro[3];   // row offsets of y-1, y, y+1 (incl. the left padding)
-    long long zo[3];   // plane offsets of z-1, z, z+1
+    int ro[3];         // row offsets of y-1, y, y+1 (incl. the left padding)
+    int zo[3];         // plane offsets of z-1, z, z+1 (offsets stay below 2^31: slot < 2^31)
     bool bot, top;     // planar walls: solid plane below / above
     uint32_t nb;       // general geometry: bit k = link k ends on a solid node
 
@@ -101,7 +102,7 @@ struct Dest {
         yo[1] = y;
         yo[2] = wrapi(y + 1, L.ny);
 #pragma unroll
-        for (int dy = 0; dy < 3; ++dy) ro[dy] = (long long)(yo[dy] + 1) * L.px + L.gx;
+        for (int dy = 0; dy < 3; ++dy) ro[dy] = (yo[dy] + 1) * L.px + L.gx;
         nb = 0;
     }
     template <class S>

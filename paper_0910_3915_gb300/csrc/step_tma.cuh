@@ -228,9 +228,9 @@ __global__ void __launch_bounds__(32 * TY) step_tma_kernel(const __grid_constant
                 float F[2][3];
                 sc_force<HX, HY>(sp + ((z - 1) & 3) * (2 * HY * HX), sp + (z & 3) * (2 * HY * HX),
                                  sp + ((z + 1) & 3) * (2 * HY * HX), ty, tx, gk, Gax, Gdi, F);
-                D.zo[0] = (long long)(z - 1) * plane;
-                D.zo[1] = (long long)z * plane;
-                D.zo[2] = (long long)(z + 1) * plane;
+                D.zo[0] = (int)((z - 1) * plane);
+                D.zo[1] = (int)(z * plane);
+                D.zo[2] = (int)((z + 1) * plane);
                 D.bot = z - 1 == 0;
                 D.top = z + 1 == nz - 1;
                 collide_store<S, false, kTauOne>(rc, jc, vc, F, tau, itau, ref, dst, L, gx, gy, D);
