@@ -85,10 +85,11 @@ __global__ void __launch_bounds__(32 * TY) step_kernel(const StepArgs<S> A)
             if constexpr (kGeneral) so_ = (__ldg(nbmask + zoff + own) & kSelfSolid) != 0;
             else so_ = (zp == 0 || zp == nz - 1);
             if (!so_) {
+                const S* p = src + (zoff + own);  // per-thread node pointer, uniform slot offsets
 #pragma unroll
                 for (int a = 0; a < 2; ++a)
 #pragma unroll
-                    for (int k = 0; k < Q; ++k) ro_[a][k] = Codec<S>::load(src + (a * Q + k) * slot + (zoff + own));
+                    for (int k = 0; k < Q; ++k) ro_[a][k] = Codec<S>::load(p + (long long)(a * Q + k) * slot);
             }
 #pragma unroll
             for (int i = 0; i < NIT; ++i) {
@@ -96,9 +97,9 @@ __global__ void __launch_bounds__(32 * TY) step_kernel(const StepArgs<S> A)
                 if constexpr (kGeneral) si_[i] = (__ldg(nbmask + zoff + it_off[i]) & kSelfSolid) != 0;
                 else si_[i] = so_;
                 if (!si_[i]) {
+                    const S* p = src + (it_a[i] * Q * slot + zoff + it_off[i]);
 #pragma unroll
-                    for (int k = 0; k < Q; ++k)
-                        ri_[i][k] = Codec<S>::load(src + (it_a[i] * Q + k) * slot + (zoff + it_off[i]));
+                    for (int k = 0; k < Q; ++k) ri_[i][k] = Codec<S>::load(p + (long long)k * slot);
                 }
             }
         };

@@ -119,60 +119,83 @@ struct Dest {
 // remainder of the node's mass, which Eq. Equil and BGK leave unchanged, so
 // that rounded lattice weights (1/3 + 6/18 + 12/36 != 1 in FP32) and 16-bit
 // rounding of the stored values do not bias the mass.
+// Loop order: velocity k outer, component inner, so each destination address
+// is formed once and both components' slots are reached by a uniform offset.
 template <class S, bool kGeneral, bool kTauOne>
 __device__ __forceinline__ void collide_store(const float (&rc)[2], const float (&jc)[2][3], const float (&vc)[2][Q],
                                               const float (&F)[2][3], const float (&tau)[2], const float (&itau)[2],
                                               const float (&ref)[2], S* __restrict__ dst, const Layout& L, int x, int y,
                                               const Dest& D)
 {
+    (void)x;
+    (void)y;
     // common velocity u' = sum_a j^a/tau^a / sum_a rho^a/tau^a
     const float den = rc[0] * itau[0] + rc[1] * itau[1];
-    const float iden = den > 0.f ? 1.0f / den : 0.f;
+    const float iden = den > 0.f ? __frcp_rn(den) : 0.f;
     float up[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) up[d] = (jc[0][d] * itau[0] + jc[1][d] * itau[1]) * iden;
 
+    // per component: equilibrium velocity u' + tau F / rho and the polynomial
+    // coefficients of Eq. Equil with c_s^2 = 1/3:
+    // n^eq_k = zeta_k rho [1 + P_k],  P = cu (3 - 4.5 u^2 + 4.5 cu (1 + cu)) - 1.5 u^2
+    float u[2][3], A0[2], B0[2], w1[2], w2[2], base[2];
 #pragma unroll
     for (int a = 0; a < 2; ++a) {
         const float r = rc[a];
-        float u[3];
-        const float sh = r > 1e-12f ? tau[a] / r : 0.f;  // shift tau F / rho
+        const float sh = r > 1e-12f ? tau[a] * __frcp_rn(r) : 0.f;  // shift tau F / rho
 #pragma unroll
-        for (int d = 0; d < 3; ++d) u[d] = up[d] + sh * F[a][d];
-        const float usq = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
-        // Eq. Equil with c_s^2 = 1/3:
-        // n^eq_k = zeta_k rho [1 + 3 cu + 4.5 cu^2 - 1.5 u^2 + 4.5 cu^3 - 4.5 u^2 cu]
-        const float A0 = 3.0f - 4.5f * usq, B0 = -1.5f * usq;
-        const float dref = r - ref[a];
-        S* dbase = dst + (long long)a * Q * L.slot;
-        float sum = 0.f, sax = 0.f, sdi = 0.f;
+        for (int d = 0; d < 3; ++d) u[a][d] = fmaf(sh, F[a][d], up[d]);
+        const float usq = u[a][0] * u[a][0] + u[a][1] * u[a][1] + u[a][2] * u[a][2];
+        A0[a] = fmaf(-4.5f, usq, 3.0f);
+        B0[a] = -1.5f * usq;
+        if constexpr (Codec<S>::kDeviation) {
+            w1[a] = w2[a] = r;          // e* = (rho - rho_ref) + rho P
+            base[a] = r - ref[a];
+        } else {
+            w1[a] = r * (1.0f / 18.0f);  // n* = zeta rho + zeta rho P
+            w2[a] = r * (1.0f / 36.0f);
+            base[a] = 0.f;
+        }
+    }
+    const long long slot = L.slot;
+    const int self = D.zo[1] + D.ro[1] + D.xo[1];
+    float sum[2] = {0.f, 0.f}, sax[2] = {0.f, 0.f}, sdi[2] = {0.f, 0.f};
 #pragma unroll
-        for (int k = 1; k < Q; ++k) {
-            const float cu = (cx(k) ? cx(k) * u[0] : 0.f) + (cy(k) ? cy(k) * u[1] : 0.f) + (cz(k) ? cz(k) * u[2] : 0.f);
-            const float P = cu * (A0 + 4.5f * cu * (1.0f + cu)) + B0;
-            float q;  // equilibrium in storage form
-            if constexpr (Codec<S>::kDeviation) q = dref + r * P;
-            else q = zeta(k) * r * (1.0f + P);
+    for (int k = 1; k < Q; ++k) {
+        bool wall;
+        if constexpr (kGeneral) wall = (D.nb >> k) & 1u;
+        else wall = (cz(k) < 0 && D.bot) || (cz(k) > 0 && D.top);
+        // destination: the neighbour x + c_k, or slot kbar of this node (bounce-back)
+        S* q = dst + (wall ? self : D.zo[cz(k) + 1] + D.ro[cy(k) + 1] + D.xo[cx(k) + 1]);
+        const long long so = (long long)(wall ? opp(k) : k) * slot;
+#pragma unroll
+        for (int a = 0; a < 2; ++a) {
+            const float cu = (cx(k) ? cx(k) * u[a][0] : 0.f) + (cy(k) ? cy(k) * u[a][1] : 0.f) +
+                             (cz(k) ? cz(k) * u[a][2] : 0.f);
+            const float P = fmaf(cu, fmaf(cu, fmaf(4.5f, cu, 4.5f), A0[a]), B0[a]);
+            const float w = is_axis(k) ? w1[a] : w2[a];
+            const float qk = fmaf(w, P, Codec<S>::kDeviation ? base[a] : w);  // equilibrium, storage form
             float s;
-            if constexpr (kTauOne) s = q;
-            else s = vc[a][k] + (q - vc[a][k]) * itau[a];
+            if constexpr (kTauOne) s = qk;
+            else s = fmaf(qk - vc[a][k], itau[a], vc[a][k]);
             if constexpr (Codec<S>::kDeviation) {
                 const float sr = Codec<S>::round(s);
-                if (is_axis(k)) sax += sr;
-                else sdi += sr;
+                if (is_axis(k)) sax[a] += sr;
+                else sdi[a] += sr;
             } else {
-                sum += s;
+                sum[a] += s;
             }
-            bool wall;
-            if constexpr (kGeneral) wall = (D.nb >> k) & 1u;
-            else wall = (cz(k) < 0 && D.bot) || (cz(k) > 0 && D.top);
-            if (wall) D.store<S>(dbase + (long long)opp(k) * L.slot, L, 0, 0, 0, s);
-            else D.store<S>(dbase + (long long)k * L.slot, L, cx(k), cy(k), cz(k), s);
+            Codec<S>::store(q + so + (long long)a * Q * slot, s);
         }
+    }
+    S* q0 = dst + self;
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {
         float s0;
-        if constexpr (Codec<S>::kDeviation) s0 = 3.0f * (dref - (sax * (1.0f / 18.0f) + sdi * (1.0f / 36.0f)));
-        else s0 = r - sum;
-        D.store<S>(dbase, L, 0, 0, 0, s0);
+        if constexpr (Codec<S>::kDeviation) s0 = 3.0f * (base[a] - (sax[a] * (1.0f / 18.0f) + sdi[a] * (1.0f / 36.0f)));
+        else s0 = rc[a] - sum[a];
+        Codec<S>::store(q0 + (long long)a * Q * slot, s0);
     }
 }
 
