@@ -181,8 +181,34 @@ int lb_set_schedule(lb_ctx* ctx, int tile_y, int z_segments);
  * the precision, falls back to LB_STEP_LDG. */
 int lb_set_step_variant(lb_ctx* ctx, int variant, int stages);
 
-/* Message of the last failure on this context (or of the last failed lb_init
- * when ctx is NULL). Never NULL. */
+/* FP64 conservation sums of a population field, for callers that cannot
+ * allocate device memory. (The paper has no counterpart; this is a library
+ * facility.) Some callers may not allocate at the point where they want the
+ * sums: code running while its stream is being captured into a CUDA graph,
+ * code inside a latency-critical or memory-budgeted section where an
+ * allocation may block, fail or be forbidden by the host application's
+ * allocator policy. This entry point allocates nothing (no cudaMalloc, no
+ * cudaFree, no allocating library routine): its per-block partial sums live
+ * in a fixed 64 KiB device array that the library defines at file scope.
+ *   populations  device pointer, 2*19*nx*ny*nz doubles laid out as in
+ *                lb_get_populations ([component][k][z][y][x]), caller-owned
+ *   solid        device pointer to nx*ny*nz bytes (1 = solid, skipped), or NULL
+ *   cons         device pointer to 8 doubles, caller-owned; receives
+ *                {mass_r, mass_b, Px, Py, Pz, non-finite count, fluid nodes, 0}
+ *   cuda_stream  stream the two kernels are queued on; the call is asynchronous
+ * At most 67,108,864 nodes (the scratch holds 1024 block rows of 65,536
+ * nodes each); larger lattices return LB_ERR_ARG with a message. The first
+ * call on each device looks up the scratch array's device address (a
+ * cudaGetSymbolAddress call), so make that first call before any stream
+ * capture. Every call shares the one scratch array on a device: calls whose
+ * kernels overlap on the GPU (different streams, no ordering) race and may
+ * return wrong sums. Errors: LB_ERR_ARG (NULL pointer, bad or too large
+ * dimensions), LB_ERR_CUDA (launch failure); message via lb_last_error(NULL). */
+int lb_conservation_static(const double* populations, const uint8_t* solid, int nx, int ny, int nz,
+                           double* cons, void* cuda_stream);
+
+/* Message of the last failure on this context (or, when ctx is NULL, of the
+ * last failed lb_init or context-free call on this thread). Never NULL. */
 const char* lb_last_error(const lb_ctx* ctx);
 
 /* Release the context and the device memory it owns. NULL is a no-op. */

@@ -53,6 +53,9 @@ struct lb_ctx {
 
 static thread_local std::string g_init_err;
 
+// message for lb_last_error(NULL) from the context-free entry points
+void lbsc_set_global_error(const std::string& msg) { g_init_err = msg; }
+
 static int fail(lb_ctx* c, int code, const std::string& msg)
 {
     if (c) c->err = msg;

@@ -93,6 +93,7 @@ SIGNATURES = [
     ("lb_set_populations", _I, [_VP, _DP]),
     ("lb_set_schedule", _I, [_VP, _I, _I]),
     ("lb_set_step_variant", _I, [_VP, _I, _I]),
+    ("lb_conservation_static", _I, [_VP, _VP, _I, _I, _I, _VP, _VP]),
     ("lb_last_error", ctypes.c_char_p, [_VP]),
     ("lb_free", None, [_VP]),
 ]
@@ -135,6 +136,19 @@ def _current_stream():
     except ImportError:
         pass
     return ctypes.c_void_p(None)
+
+
+def conservation_static(populations_ptr: int, solid_ptr: int | None, nx: int, ny: int, nz: int,
+                        cons_ptr: int, stream: int | None = None) -> None:
+    """lb_conservation_static: FP64 conservation sums of a dense device
+    population array into a device array of 8 doubles, with no allocation
+    (its scratch is a fixed device array of the library). Asynchronous on
+    ``stream`` (default: torch's current stream)."""
+    st = _current_stream() if stream is None else ctypes.c_void_p(stream)
+    rc = load().lb_conservation_static(ctypes.c_void_p(populations_ptr),
+                                       ctypes.c_void_p(solid_ptr) if solid_ptr else None,
+                                       nx, ny, nz, ctypes.c_void_p(cons_ptr), st)
+    _check(rc)
 
 
 class Lattice:
