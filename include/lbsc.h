@@ -181,6 +181,52 @@ int lb_set_schedule(lb_ctx* ctx, int tile_y, int z_segments);
  * the precision, falls back to LB_STEP_LDG. */
 int lb_set_step_variant(lb_ctx* ctx, int variant, int stages);
 
+/* ------------------------------------------------------------ batches
+ * Many independent droplet lattices, each with its own size and parameters,
+ * advanced together: one persistent kernel launch per time step walks a work
+ * list of (lattice, tile column, z range) items, and runs of 32 steps are
+ * replayed as a captured CUDA graph. This is the paper's kind of parameter
+ * sweep (Sec. 4: theta against system size and wall parameter) done in one
+ * launch per step instead of one run per parameter set. Every box uses the
+ * default walls (solid layers z = 0 and z = nz - 1). */
+typedef struct lb_batch lb_batch;
+
+/* Create a batch of nbox lattices on the current device. dims: 3*nbox ints
+ * (nx, ny, nz per box, nz >= 3). rho_r, rho_b: the boxes' initial densities
+ * concatenated in box order (each nx*ny*nz doubles, x fastest). params: nbox
+ * parameter sets. All boxes share one precision and one stream. */
+int lb_batch_create(lb_batch** out, int nbox, const int* dims, const double* rho_r, const double* rho_b,
+                    const lb_params* params, int precision, void* cuda_stream);
+
+/* Replace the parameters of box i. */
+int lb_batch_set_params(lb_batch* b, int i, const lb_params* params);
+
+/* Work split: tile height (4, 8, 16), z planes per work item, CTAs per SM of
+ * the persistent grid (0 = as many as fit). Results do not depend on it. */
+int lb_batch_set_schedule(lb_batch* b, int tile_y, int planes_per_item, int ctas_per_sm);
+
+/* Advance every box by nsteps (asynchronous). LB_ERR_STATE if a box was
+ * stepped on its own in between. */
+int lb_batch_step(lb_batch* b, int nsteps);
+
+/* The context of box i, borrowed: valid until lb_batch_free, usable with
+ * lb_moments, lb_contact_angle, lb_save and the other readers. Do not step
+ * it or free it on its own. */
+int lb_batch_box(lb_batch* b, int i, lb_ctx** out);
+
+/* Conservation sums (as lb_conservation) of every box: 8*nbox doubles. */
+int lb_batch_conservation(lb_batch* b, double* cons);
+
+/* Contact angle (as lb_contact_angle) of every box: nbox records. */
+int lb_batch_contact_angles(lb_batch* b, double offset, lb_droplet* out);
+
+/* Message of the last failure on this batch (NULL: of the last failed
+ * lb_batch_create on this thread). Never NULL. */
+const char* lb_batch_last_error(const lb_batch* b);
+
+/* Release the batch, its boxes and their device memory. NULL is a no-op. */
+void lb_batch_free(lb_batch* b);
+
 /* FP64 conservation sums of a population field, for callers that cannot
  * allocate device memory. (The paper has no counterpart; this is a library
  * facility.) Some callers may not allocate at the point where they want the

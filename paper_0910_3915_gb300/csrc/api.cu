@@ -903,3 +903,268 @@ void lb_free(lb_ctx* c)
 }
 
 }  // extern "C"
+
+// ====================================================================== batch
+// Many independent lattices (their own sizes and parameters) advanced by one
+// persistent kernel launch per step over a shared work list. Each box is a
+// full context living in a slice of one device allocation, so every per-box
+// readback (moments, contact angle, checkpoints) is the single-lattice code.
+
+struct lb_batch {
+    int nbox = 0, prec = LB_F32;
+    cudaStream_t stream = nullptr, cap = nullptr;
+    std::vector<lb_ctx*> box;
+    char* mem = nullptr;
+    void* dargs = nullptr;  // StepArgs<S>[2*nbox]: box i read from buffer parity p at 2*i + p
+    int4* ditems = nullptr; // (box, tile column, first plane, end plane)
+    int nitems = 0;
+    int tile_y = 8, seg_planes = 32, ctas_per_sm = 0, grid = 0;
+    bool tau1 = true;
+    int cur = 0;
+    long long steps = 0;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    std::string err;
+};
+
+static int bfail(lb_batch* b, int code, const std::string& msg)
+{
+    if (b) b->err = msg;
+    else g_init_err = msg;
+    return code;
+}
+
+#define LB_BCUDA(b, call)                                                                           \
+    do {                                                                                            \
+        cudaError_t e_ = (call);                                                                    \
+        if (e_ != cudaSuccess) return bfail(b, LB_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+static void batch_drop_graphs(lb_batch* b)
+{
+    for (int i = 0; i < 2; ++i)
+        if (b->graph[i]) {
+            cudaGraphExecDestroy(b->graph[i]);
+            b->graph[i] = nullptr;
+        }
+}
+
+template <class S>
+static int batch_build_typed(lb_batch* b)
+{
+    std::vector<StepArgs<S>> args(2 * (size_t)b->nbox);
+    std::vector<int4> items;
+    b->tau1 = true;
+    for (int i = 0; i < b->nbox; ++i) {
+        lb_ctx* c = b->box[i];
+        c->tile_y = b->tile_y;
+        b->tau1 = b->tau1 && tau_one(c);
+        for (int p = 0; p < 2; ++p) args[2 * i + p] = step_args<S>(c, p);
+        const int tx = (c->nx + 31) / 32, ty = (c->ny + b->tile_y - 1) / b->tile_y;
+        const int nzf = c->zhi - c->zlo;
+        int nseg = (nzf + b->seg_planes / 2) / b->seg_planes;
+        nseg = nseg < 1 ? 1 : (nseg > nzf ? nzf : nseg);
+        for (int s = 0; s < nseg; ++s) {
+            const int za = c->zlo + (int)((long long)s * nzf / nseg), zb = c->zlo + (int)((long long)(s + 1) * nzf / nseg);
+            if (za >= zb) continue;
+            for (int col = 0; col < tx * ty; ++col) items.push_back(make_int4(i, col, za, zb));
+        }
+    }
+    if (b->dargs) cudaFree(b->dargs);
+    if (b->ditems) cudaFree(b->ditems);
+    b->dargs = nullptr;
+    b->ditems = nullptr;
+    LB_BCUDA(b, cudaMalloc(&b->dargs, args.size() * sizeof(StepArgs<S>)));
+    LB_BCUDA(b, cudaMalloc((void**)&b->ditems, items.size() * sizeof(int4)));
+    LB_BCUDA(b, cudaMemcpy(b->dargs, args.data(), args.size() * sizeof(StepArgs<S>), cudaMemcpyHostToDevice));
+    LB_BCUDA(b, cudaMemcpy(b->ditems, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice));
+    b->nitems = (int)items.size();
+    const int occ = b->ctas_per_sm > 0 ? b->ctas_per_sm : batch_occupancy<S>(b->tile_y, b->tau1);
+    b->grid = b->box[0]->nsm * occ;
+    return LB_OK;
+}
+
+static int batch_build(lb_batch* b)
+{
+    batch_drop_graphs(b);
+    switch (b->prec) {
+    case LB_F32: return batch_build_typed<float>(b);
+    case LB_F16: return batch_build_typed<__half>(b);
+    default: return batch_build_typed<__nv_bfloat16>(b);
+    }
+}
+
+static cudaError_t batch_launch(lb_batch* b, int parity, cudaStream_t st)
+{
+    switch (b->prec) {
+    case LB_F32:
+        return launch_batch_step<float>((const StepArgs<float>*)b->dargs, b->ditems, b->nitems, parity, b->tile_y,
+                                        b->tau1, b->grid, st);
+    case LB_F16:
+        return launch_batch_step<__half>((const StepArgs<__half>*)b->dargs, b->ditems, b->nitems, parity, b->tile_y,
+                                         b->tau1, b->grid, st);
+    default:
+        return launch_batch_step<__nv_bfloat16>((const StepArgs<__nv_bfloat16>*)b->dargs, b->ditems, b->nitems, parity,
+                                                b->tile_y, b->tau1, b->grid, st);
+    }
+}
+
+extern "C" {
+
+int lb_batch_create(lb_batch** out, int nbox, const int* dims, const double* rho_r, const double* rho_b,
+                    const lb_params* params, int precision, void* cuda_stream)
+{
+    if (!out) return bfail(nullptr, LB_ERR_ARG, "lb_batch_create: out is NULL");
+    *out = nullptr;
+    if (nbox < 1 || !dims || !rho_r || !rho_b || !params) return bfail(nullptr, LB_ERR_ARG, "lb_batch_create: bad argument");
+    if (precision != LB_F32 && precision != LB_F16 && precision != LB_BF16)
+        return bfail(nullptr, LB_ERR_ARG, "lb_batch_create: unknown precision");
+    std::vector<size_t> off(nbox);
+    size_t total = 0;
+    for (int i = 0; i < nbox; ++i) {
+        const int nx = dims[3 * i], ny = dims[3 * i + 1], nz = dims[3 * i + 2];
+        if (!dims_ok(nx, ny, nz) || nz < 3) return bfail(nullptr, LB_ERR_ARG, "lb_batch_create: bad box dimensions");
+        off[i] = total;
+        total += align256(make_plan(make_layout(nx, ny, nz, precision), precision).total);
+    }
+    lb_batch* b = new (std::nothrow) lb_batch();
+    if (!b) return bfail(nullptr, LB_ERR_CUDA, "lb_batch_create: out of host memory");
+    b->nbox = nbox;
+    b->prec = precision;
+    b->stream = (cudaStream_t)cuda_stream;
+    auto bail = [&](int code) {
+        lb_batch_free(b);
+        return code;
+    };
+    cudaError_t e = cudaMalloc((void**)&b->mem, total);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        g_init_err = std::string("lb_batch_create: ") + cudaGetErrorString(e);
+        return bail(LB_ERR_CUDA);
+    }
+    size_t node_off = 0;
+    for (int i = 0; i < nbox; ++i) {
+        const int nx = dims[3 * i], ny = dims[3 * i + 1], nz = dims[3 * i + 2];
+        lb_ctx* c = nullptr;
+        const int rc = init_common(&c, nx, ny, nz, precision, rho_r + node_off, rho_b + node_off, cuda_stream,
+                                   b->mem + off[i], make_plan(make_layout(nx, ny, nz, precision), precision).total);
+        if (rc != LB_OK) return bail(rc);
+        b->box.push_back(c);
+        if (lb_set_params(c, &params[i]) != LB_OK) {
+            g_init_err = "lb_batch_create: box " + std::to_string(i) + ": " + c->err;
+            return bail(LB_ERR_ARG);
+        }
+        node_off += (size_t)nx * ny * nz;
+    }
+    const int rc = batch_build(b);
+    if (rc != LB_OK) {
+        g_init_err = b->err;
+        return bail(rc);
+    }
+    *out = b;
+    return LB_OK;
+}
+
+int lb_batch_set_params(lb_batch* b, int i, const lb_params* params)
+{
+    if (!b || i < 0 || i >= b->nbox) return bfail(b, LB_ERR_ARG, "lb_batch_set_params: bad argument");
+    const int rc = lb_set_params(b->box[i], params);
+    if (rc != LB_OK) return bfail(b, rc, b->box[i]->err);
+    return batch_build(b);
+}
+
+int lb_batch_set_schedule(lb_batch* b, int tile_y, int planes_per_item, int ctas_per_sm)
+{
+    if (!b || (tile_y != 4 && tile_y != 8 && tile_y != 16) || planes_per_item < 1 || ctas_per_sm < 0)
+        return bfail(b, LB_ERR_ARG, "lb_batch_set_schedule: tile_y 4/8/16, planes_per_item >= 1, ctas_per_sm >= 0");
+    b->tile_y = tile_y;
+    b->seg_planes = planes_per_item;
+    b->ctas_per_sm = ctas_per_sm;
+    return batch_build(b);
+}
+
+int lb_batch_step(lb_batch* b, int nsteps)
+{
+    if (!b || nsteps < 0) return bfail(b, LB_ERR_ARG, "lb_batch_step: bad argument");
+    for (lb_ctx* c : b->box)
+        if (c->cur != b->cur) return bfail(b, LB_ERR_STATE, "lb_batch_step: a box was stepped on its own");
+    const int G = lb_ctx::kGraphSteps;
+    int n = nsteps;
+    if (n >= G) {
+        const int par = b->cur;
+        if (!b->graph[par]) {
+            cudaGraph_t g = nullptr;
+            LB_BCUDA(b, cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
+            cudaError_t e = cudaSuccess;
+            for (int i = 0; i < G && e == cudaSuccess; ++i) e = batch_launch(b, (par + i) & 1, b->cap);
+            cudaError_t e2 = cudaStreamEndCapture(b->cap, &g);
+            if (e != cudaSuccess) return bfail(b, LB_ERR_CUDA, std::string("lb_batch_step: capture: ") + cudaGetErrorString(e));
+            if (e2 != cudaSuccess) return bfail(b, LB_ERR_CUDA, std::string("lb_batch_step: end capture: ") + cudaGetErrorString(e2));
+            e = cudaGraphInstantiate(&b->graph[par], g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) return bfail(b, LB_ERR_CUDA, std::string("lb_batch_step: instantiate: ") + cudaGetErrorString(e));
+        }
+        while (n >= G) {
+            LB_BCUDA(b, cudaGraphLaunch(b->graph[par], b->stream));
+            n -= G;
+        }
+    }
+    for (int i = 0; i < n; ++i) {
+        LB_BCUDA(b, batch_launch(b, b->cur, b->stream));
+        b->cur ^= 1;
+    }
+    b->steps += nsteps;
+    for (lb_ctx* c : b->box) {
+        c->cur = b->cur;
+        c->steps += nsteps;
+        if (nsteps > 0) c->ghost_ok = false;
+    }
+    return LB_OK;
+}
+
+int lb_batch_box(lb_batch* b, int i, lb_ctx** out)
+{
+    if (!b || !out || i < 0 || i >= b->nbox) return bfail(b, LB_ERR_ARG, "lb_batch_box: bad argument");
+    *out = b->box[i];
+    return LB_OK;
+}
+
+int lb_batch_conservation(lb_batch* b, double* cons)
+{
+    if (!b || !cons) return bfail(b, LB_ERR_ARG, "lb_batch_conservation: NULL argument");
+    for (int i = 0; i < b->nbox; ++i) {
+        const int rc = lb_conservation(b->box[i], cons + 8 * (size_t)i);
+        if (rc != LB_OK) return bfail(b, rc, "box " + std::to_string(i) + ": " + b->box[i]->err);
+    }
+    return LB_OK;
+}
+
+int lb_batch_contact_angles(lb_batch* b, double offset, lb_droplet* out)
+{
+    if (!b || !out) return bfail(b, LB_ERR_ARG, "lb_batch_contact_angles: NULL argument");
+    for (int i = 0; i < b->nbox; ++i) {
+        const int rc = lb_contact_angle(b->box[i], offset, &out[i]);
+        if (rc != LB_OK) return bfail(b, rc, "box " + std::to_string(i) + ": " + b->box[i]->err);
+    }
+    return LB_OK;
+}
+
+const char* lb_batch_last_error(const lb_batch* b)
+{
+    if (!b) return g_init_err.c_str();
+    return b->err.c_str();
+}
+
+void lb_batch_free(lb_batch* b)
+{
+    if (!b) return;
+    if (b->stream || b->mem) cudaStreamSynchronize(b->stream);
+    batch_drop_graphs(b);
+    for (lb_ctx* c : b->box) lb_free(c);
+    if (b->dargs) cudaFree(b->dargs);
+    if (b->ditems) cudaFree(b->ditems);
+    if (b->mem) cudaFree(b->mem);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    delete b;
+}
+
+}  // extern "C"

@@ -36,6 +36,11 @@ template <class S>
 long long tma_step(int op, int tile_y, int stages, bool tau_one, const CUtensorMap* map, const StepArgs<S>* args,
                    cudaStream_t stream);
 template <class S>
+cudaError_t launch_batch_step(const StepArgs<S>* args, const int4* items, int nitems, int parity, int tile_y,
+                              bool tau_one, int grid, cudaStream_t st);
+template <class S>
+int batch_occupancy(int tile_y, bool tau_one);
+template <class S>
 cudaError_t launch_ghosts(const Layout& L, S* f, int z0, int z1, cudaStream_t st);
 template <class S>
 cudaError_t launch_init(const FieldArgs& F, S* f, const double* rr, const double* rb, cudaStream_t st);

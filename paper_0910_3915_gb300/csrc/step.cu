@@ -16,13 +16,15 @@
 
 namespace lbsc {
 
+// One work item: tile column `col` of the lattice A, fluid planes [za, zb).
+// sp: the CTA's psi ring, [4][2][TY+2][34] floats.
 template <class S, int TY, bool kGeneral, bool kTauOne>
-__global__ void __launch_bounds__(32 * TY) step_kernel(const StepArgs<S> A)
+__device__ __forceinline__ void step_item(const StepArgs<S>& A, int col, int za, int zb,
+                                          float (&sp)[4][2][TY + 2][34])
 {
     constexpr int TX = 32, NT = TX * TY, HX = TX + 2, HY = TY + 2;
     constexpr int RING = 2 * HX + 2 * TY;          // ring nodes around the tile
     constexpr int NIT = (2 * RING + NT - 1) / NT;  // ring items (node, component) per thread
-    __shared__ float sp[4][2][HY][HX];             // psi of 4 planes, slot = z & 3
 
     const Layout L = A.L;
     const int nx = L.nx, ny = L.ny, nz = L.nz, px = L.px;
@@ -37,151 +39,173 @@ __global__ void __launch_bounds__(32 * TY) step_kernel(const StepArgs<S> A)
     const float itau[2] = {A.P.itau[0], A.P.itau[1]};
     const float gk = A.P.gk, Gax = A.P.Gax, Gdi = A.P.Gdi;
     const int tid = threadIdx.x, tx = tid % TX, ty = tid / TX;
+
+    const int x0 = (col % A.tiles_x) * TX, y0 = (col / A.tiles_x) * TY;
+    const int gx = x0 + tx, gy = y0 + ty;
+    const bool valid = gx < nx && gy < ny;
+    const int ox = gx % nx, oy = gy % ny;  // ragged tiles: wrapped copy of a real column
+    const int own = (oy + 1) * px + ox + L.gx;
+
+    // this thread's ring items: smem position, plane offset of the node, component
+    int it_sm[NIT], it_a[NIT], it_off[NIT];
+#pragma unroll
+    for (int i = 0; i < NIT; ++i) {
+        const int it = tid + i * NT;
+        it_a[i] = -1;
+        it_sm[i] = 0;
+        it_off[i] = 0;
+        if (it < 2 * RING) {
+            const int a = it >= RING, r = it - a * RING;
+            int ix, iy;
+            if (r < HX) { ix = r; iy = 0; }
+            else if (r < 2 * HX) { ix = r - HX; iy = HY - 1; }
+            else if (r < 2 * HX + TY) { ix = 0; iy = r - 2 * HX + 1; }
+            else { ix = HX - 1; iy = r - 2 * HX - TY + 1; }
+            const int hx = ((x0 - 1 + ix) % nx + nx) % nx, hy = ((y0 - 1 + iy) % ny + ny) % ny;
+            it_a[i] = a;
+            it_sm[i] = iy * HX + ix;
+            it_off[i] = (hy + 1) * px + hx + L.gx;
+        }
+    }
+
+    // raw populations of the plane in flight (own node, ring items) and
+    // whether each node is solid
+    float ro_[2][Q], ri_[NIT][Q];
+    bool so_ = false, si_[NIT];
+
+    // request plane zp into the raw registers
+    auto issue = [&](int zp) {
+        const int zw = kGeneral ? wrapi(zp, nz) : zp;
+        const int zoff = zw * plane;
+        if constexpr (kGeneral) so_ = (__ldg(nbmask + zoff + own) & kSelfSolid) != 0;
+        else so_ = (zp == 0 || zp == nz - 1);
+        if (!so_) {
+            const S* p = src + (zoff + own);  // per-thread node pointer, uniform slot offsets
+#pragma unroll
+            for (int a = 0; a < 2; ++a)
+#pragma unroll
+                for (int k = 0; k < Q; ++k) ro_[a][k] = Codec<S>::load(p + (long long)(a * Q + k) * slot);
+        }
+#pragma unroll
+        for (int i = 0; i < NIT; ++i) {
+            if (it_a[i] < 0) continue;
+            if constexpr (kGeneral) si_[i] = (__ldg(nbmask + zoff + it_off[i]) & kSelfSolid) != 0;
+            else si_[i] = so_;
+            if (!si_[i]) {
+                const S* p = src + (it_a[i] * Q * slot + zoff + it_off[i]);
+#pragma unroll
+                for (int k = 0; k < Q; ++k) ri_[i][k] = Codec<S>::load(p + (long long)k * slot);
+            }
+        }
+    };
+    // reduce the raw registers of plane zp: psi into its ring slot, own moments out
+    auto reduce = [&](int zp, float (&rho)[2], float (&j)[2][3], float (&v)[2][Q]) {
+        float* spl = &sp[zp & 3][0][0][0];
+#pragma unroll
+        for (int a = 0; a < 2; ++a) {
+            float ps = eta[a];
+            rho[a] = 0.f;
+            j[a][0] = j[a][1] = j[a][2] = 0.f;
+            if (!so_) {
+                rho[a] = rho_of<S>(ro_[a], ref[a]);
+                mom_of<S>(ro_[a], j[a]);
+                ps = psi_of(rho[a]);
+                if constexpr (!kTauOne) {
+#pragma unroll
+                    for (int k = 0; k < Q; ++k) v[a][k] = ro_[a][k];
+                }
+            }
+            spl[(a * HY + ty + 1) * HX + tx + 1] = ps;
+        }
+#pragma unroll
+        for (int i = 0; i < NIT; ++i) {
+            if (it_a[i] < 0) continue;
+            const int a = it_a[i];
+            spl[a * HY * HX + it_sm[i]] = si_[i] ? eta[a] : psi_of(rho_of<S>(ri_[i], ref[a]));
+        }
+    };
+
+    float rc[2], jc[2][3], vc[2][Q];
+    float rn[2], jn[2][3], vn[2][Q];
+    __syncthreads();  // the previous item's readers are done with the ring
+    issue(za - 1);
+    reduce(za - 1, rn, jn, vn);
+    issue(za);
+    reduce(za, rc, jc, vc);
+    issue(za + 1);
+
+    Dest D;
+    D.set_column(L, valid ? gx : 0, valid ? gy : 0);
+
+    for (int z = za; z < zb; ++z) {
+        reduce(z + 1, rn, jn, vn);
+        if (z + 2 <= zb) issue(z + 2);
+        __syncthreads();
+
+        bool self_solid = false;
+        if constexpr (kGeneral) {
+            if (valid) {
+                D.nb = __ldg(nbmask + z * plane + own);
+                self_solid = (D.nb & kSelfSolid) != 0;
+            }
+        }
+        if (valid && !self_solid) {
+            float F[2][3];
+            sc_force<HX, HY>(&sp[(z - 1) & 3][0][0][0], &sp[z & 3][0][0][0], &sp[(z + 1) & 3][0][0][0], ty, tx,
+                             gk, Gax, Gdi, F);
+            if constexpr (kGeneral) {
+                D.zo[0] = wrapi(z - 1, nz) * plane;
+                D.zo[2] = wrapi(z + 1, nz) * plane;
+            } else {
+                D.zo[0] = (z - 1) * plane;
+                D.zo[2] = (z + 1) * plane;
+            }
+            D.zo[1] = z * plane;
+            D.bot = !kGeneral && z - 1 == 0;
+            D.top = !kGeneral && z + 1 == nz - 1;
+            collide_store<S, kGeneral, kTauOne>(rc, jc, vc, F, tau, itau, ref, dst, L, gx, gy, D);
+        }
+        // rotate: next plane becomes current
+#pragma unroll
+        for (int a = 0; a < 2; ++a) {
+            rc[a] = rn[a];
+#pragma unroll
+            for (int d = 0; d < 3; ++d) jc[a][d] = jn[a][d];
+            if constexpr (!kTauOne) {
+#pragma unroll
+                for (int k = 0; k < Q; ++k) vc[a][k] = vn[a][k];
+            }
+        }
+    }
+}
+
+template <class S, int TY, bool kGeneral, bool kTauOne>
+__global__ void __launch_bounds__(32 * TY) step_kernel(const StepArgs<S> A)
+{
+    __shared__ float sp[4][2][TY + 2][34];  // psi of 4 planes, slot = z & 3
     const int ncol = A.tiles_x * A.tiles_y;
     const int nzf = A.zhi - A.zlo;
-
     for (int item = blockIdx.x; item < ncol * A.nseg; item += gridDim.x) {
         const int col = item % ncol, seg = item / ncol;
         const int za = A.zlo + (int)((long long)seg * nzf / A.nseg);
         const int zb = A.zlo + (int)((long long)(seg + 1) * nzf / A.nseg);
         if (za >= zb) continue;
-        const int x0 = (col % A.tiles_x) * TX, y0 = (col / A.tiles_x) * TY;
-        const int gx = x0 + tx, gy = y0 + ty;
-        const bool valid = gx < nx && gy < ny;
-        const int ox = gx % nx, oy = gy % ny;  // ragged tiles: wrapped copy of a real column
-        const int own = (oy + 1) * px + ox + L.gx;
+        step_item<S, TY, kGeneral, kTauOne>(A, col, za, zb, sp);
+    }
+}
 
-        // this thread's ring items: smem position, plane offset of the node, component
-        int it_sm[NIT], it_a[NIT], it_off[NIT];
-#pragma unroll
-        for (int i = 0; i < NIT; ++i) {
-            const int it = tid + i * NT;
-            it_a[i] = -1;
-            it_sm[i] = 0;
-            it_off[i] = 0;
-            if (it < 2 * RING) {
-                const int a = it >= RING, r = it - a * RING;
-                int ix, iy;
-                if (r < HX) { ix = r; iy = 0; }
-                else if (r < 2 * HX) { ix = r - HX; iy = HY - 1; }
-                else if (r < 2 * HX + TY) { ix = 0; iy = r - 2 * HX + 1; }
-                else { ix = HX - 1; iy = r - 2 * HX - TY + 1; }
-                const int hx = ((x0 - 1 + ix) % nx + nx) % nx, hy = ((y0 - 1 + iy) % ny + ny) % ny;
-                it_a[i] = a;
-                it_sm[i] = iy * HX + ix;
-                it_off[i] = (hy + 1) * px + hx + L.gx;
-            }
-        }
-
-        // raw populations of the plane in flight (own node, ring items) and
-        // whether each node is solid
-        float ro_[2][Q], ri_[NIT][Q];
-        bool so_ = false, si_[NIT];
-
-        // request plane zp into the raw registers
-        auto issue = [&](int zp) {
-            const int zw = kGeneral ? wrapi(zp, nz) : zp;
-            const int zoff = zw * plane;
-            if constexpr (kGeneral) so_ = (__ldg(nbmask + zoff + own) & kSelfSolid) != 0;
-            else so_ = (zp == 0 || zp == nz - 1);
-            if (!so_) {
-                const S* p = src + (zoff + own);  // per-thread node pointer, uniform slot offsets
-#pragma unroll
-                for (int a = 0; a < 2; ++a)
-#pragma unroll
-                    for (int k = 0; k < Q; ++k) ro_[a][k] = Codec<S>::load(p + (long long)(a * Q + k) * slot);
-            }
-#pragma unroll
-            for (int i = 0; i < NIT; ++i) {
-                if (it_a[i] < 0) continue;
-                if constexpr (kGeneral) si_[i] = (__ldg(nbmask + zoff + it_off[i]) & kSelfSolid) != 0;
-                else si_[i] = so_;
-                if (!si_[i]) {
-                    const S* p = src + (it_a[i] * Q * slot + zoff + it_off[i]);
-#pragma unroll
-                    for (int k = 0; k < Q; ++k) ri_[i][k] = Codec<S>::load(p + (long long)k * slot);
-                }
-            }
-        };
-        // reduce the raw registers of plane zp: psi into its ring slot, own moments out
-        auto reduce = [&](int zp, float (&rho)[2], float (&j)[2][3], float (&v)[2][Q]) {
-            float* spl = &sp[zp & 3][0][0][0];
-#pragma unroll
-            for (int a = 0; a < 2; ++a) {
-                float ps = eta[a];
-                rho[a] = 0.f;
-                j[a][0] = j[a][1] = j[a][2] = 0.f;
-                if (!so_) {
-                    rho[a] = rho_of<S>(ro_[a], ref[a]);
-                    mom_of<S>(ro_[a], j[a]);
-                    ps = psi_of(rho[a]);
-                    if constexpr (!kTauOne) {
-#pragma unroll
-                        for (int k = 0; k < Q; ++k) v[a][k] = ro_[a][k];
-                    }
-                }
-                spl[(a * HY + ty + 1) * HX + tx + 1] = ps;
-            }
-#pragma unroll
-            for (int i = 0; i < NIT; ++i) {
-                if (it_a[i] < 0) continue;
-                const int a = it_a[i];
-                spl[a * HY * HX + it_sm[i]] = si_[i] ? eta[a] : psi_of(rho_of<S>(ri_[i], ref[a]));
-            }
-        };
-
-        float rc[2], jc[2][3], vc[2][Q];
-        float rn[2], jn[2][3], vn[2][Q];
-        __syncthreads();  // the previous item's readers are done with the ring
-        issue(za - 1);
-        reduce(za - 1, rn, jn, vn);
-        issue(za);
-        reduce(za, rc, jc, vc);
-        issue(za + 1);
-
-        Dest D;
-        D.set_column(L, valid ? gx : 0, valid ? gy : 0);
-
-        for (int z = za; z < zb; ++z) {
-            reduce(z + 1, rn, jn, vn);
-            if (z + 2 <= zb) issue(z + 2);
-            __syncthreads();
-
-            bool self_solid = false;
-            if constexpr (kGeneral) {
-                if (valid) {
-                    D.nb = __ldg(nbmask + z * plane + own);
-                    self_solid = (D.nb & kSelfSolid) != 0;
-                }
-            }
-            if (valid && !self_solid) {
-                float F[2][3];
-                sc_force<HX, HY>(&sp[(z - 1) & 3][0][0][0], &sp[z & 3][0][0][0], &sp[(z + 1) & 3][0][0][0], ty, tx,
-                                 gk, Gax, Gdi, F);
-                if constexpr (kGeneral) {
-                    D.zo[0] = wrapi(z - 1, nz) * plane;
-                    D.zo[2] = wrapi(z + 1, nz) * plane;
-                } else {
-                    D.zo[0] = (z - 1) * plane;
-                    D.zo[2] = (z + 1) * plane;
-                }
-                D.zo[1] = z * plane;
-                D.bot = !kGeneral && z - 1 == 0;
-                D.top = !kGeneral && z + 1 == nz - 1;
-                collide_store<S, kGeneral, kTauOne>(rc, jc, vc, F, tau, itau, ref, dst, L, gx, gy, D);
-            }
-            // rotate: next plane becomes current
-#pragma unroll
-            for (int a = 0; a < 2; ++a) {
-                rc[a] = rn[a];
-#pragma unroll
-                for (int d = 0; d < 3; ++d) jc[a][d] = jn[a][d];
-                if constexpr (!kTauOne) {
-#pragma unroll
-                    for (int k = 0; k < Q; ++k) vc[a][k] = vn[a][k];
-                }
-            }
-        }
+// Batched step: a persistent grid walks a work list of (box, tile column,
+// first plane, end plane) items over many lattices with their own sizes and
+// parameters; args[2*box + parity] describes box `box` for this step.
+template <class S, int TY, bool kTauOne>
+__global__ void __launch_bounds__(32 * TY)
+    batch_step_kernel(const StepArgs<S>* __restrict__ args, const int4* __restrict__ items, int nitems, int parity)
+{
+    __shared__ float sp[4][2][TY + 2][34];
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const int4 w = items[it];
+        const StepArgs<S> A = args[2 * w.x + parity];
+        step_item<S, TY, false, kTauOne>(A, w.y, w.z, w.w, sp);
     }
 }
 
@@ -244,6 +268,56 @@ int step_occupancy(int precision, int tile_y, bool general, bool tau_one)
     default: return occ_s<__nv_bfloat16>(tile_y, general, tau_one);
     }
 }
+
+template <class S, int TY>
+static cudaError_t batch_ty(const StepArgs<S>* args, const int4* items, int nitems, int parity, bool tau_one,
+                            int grid, cudaStream_t st)
+{
+    if (tau_one) batch_step_kernel<S, TY, true><<<grid, 32 * TY, 0, st>>>(args, items, nitems, parity);
+    else batch_step_kernel<S, TY, false><<<grid, 32 * TY, 0, st>>>(args, items, nitems, parity);
+    return cudaGetLastError();
+}
+
+template <class S>
+cudaError_t launch_batch_step(const StepArgs<S>* args, const int4* items, int nitems, int parity, int tile_y,
+                              bool tau_one, int grid, cudaStream_t st)
+{
+    switch (tile_y) {
+    case 4: return batch_ty<S, 4>(args, items, nitems, parity, tau_one, grid, st);
+    case 8: return batch_ty<S, 8>(args, items, nitems, parity, tau_one, grid, st);
+    case 16: return batch_ty<S, 16>(args, items, nitems, parity, tau_one, grid, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+// resident CTAs per SM of the batched kernel
+template <class S>
+int batch_occupancy(int tile_y, bool tau_one)
+{
+    int n = 0;
+    cudaError_t e = cudaErrorInvalidValue;
+    switch (tile_y) {
+    case 4:
+        e = tau_one ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_step_kernel<S, 4, true>, 128, 0)
+                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_step_kernel<S, 4, false>, 128, 0);
+        break;
+    case 8:
+        e = tau_one ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_step_kernel<S, 8, true>, 256, 0)
+                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_step_kernel<S, 8, false>, 256, 0);
+        break;
+    default:
+        e = tau_one ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_step_kernel<S, 16, true>, 512, 0)
+                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_step_kernel<S, 16, false>, 512, 0);
+    }
+    return e == cudaSuccess && n > 0 ? n : 1;
+}
+
+#define LBSC_BATCH_INST(S)                                                                                     \
+    template cudaError_t launch_batch_step<S>(const StepArgs<S>*, const int4*, int, int, int, bool, int, cudaStream_t); \
+    template int batch_occupancy<S>(int, bool);
+LBSC_BATCH_INST(float)
+LBSC_BATCH_INST(__half)
+LBSC_BATCH_INST(__nv_bfloat16)
 
 template cudaError_t launch_step<float>(const StepArgs<float>&, int, bool, bool, cudaStream_t);
 template cudaError_t launch_step<__half>(const StepArgs<__half>&, int, bool, bool, cudaStream_t);

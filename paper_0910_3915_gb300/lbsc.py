@@ -93,6 +93,15 @@ SIGNATURES = [
     ("lb_set_populations", _I, [_VP, _DP]),
     ("lb_set_schedule", _I, [_VP, _I, _I]),
     ("lb_set_step_variant", _I, [_VP, _I, _I]),
+    ("lb_batch_create", _I, [ctypes.POINTER(_VP), _I, ctypes.POINTER(_I), _DP, _DP, ctypes.POINTER(lb_params), _I, _VP]),
+    ("lb_batch_set_params", _I, [_VP, _I, ctypes.POINTER(lb_params)]),
+    ("lb_batch_set_schedule", _I, [_VP, _I, _I, _I]),
+    ("lb_batch_step", _I, [_VP, _I]),
+    ("lb_batch_box", _I, [_VP, _I, ctypes.POINTER(_VP)]),
+    ("lb_batch_conservation", _I, [_VP, _DP]),
+    ("lb_batch_contact_angles", _I, [_VP, ctypes.c_double, ctypes.POINTER(lb_droplet)]),
+    ("lb_batch_last_error", ctypes.c_char_p, [_VP]),
+    ("lb_batch_free", None, [_VP]),
     ("lb_conservation_static", _I, [_VP, _VP, _I, _I, _I, _VP, _VP]),
     ("lb_last_error", ctypes.c_char_p, [_VP]),
     ("lb_free", None, [_VP]),
@@ -287,3 +296,99 @@ class Lattice:
 
     def __exit__(self, *exc):
         self.close()
+
+
+def _bcheck(rc: int, b=None):
+    if rc != LB_OK:
+        msg = load().lb_batch_last_error(b)
+        raise LBError(rc, msg.decode() if msg else "")
+
+
+class _BoxView(Lattice):
+    """A borrowed box context of a Batch: readers only (moments, contact angle, save)."""
+
+    def __init__(self, ctx, shape, precision, batch):
+        self.nz, self.ny, self.nx = shape
+        self.precision = precision
+        self._ctx = ctx
+        self._buf = None
+        self._params = Params()
+        self._batch = batch
+
+    def step(self, n: int = 1):
+        raise LBError(LB_ERR_STATE, "a batch box is stepped through its Batch")
+
+    def close(self):
+        self._ctx = ctypes.c_void_p()  # owned by the batch
+
+
+class Batch:
+    """Many independent droplet lattices advanced together (lb_batch_*).
+
+    fields: list of (rho_r, rho_b) pairs, each (nz, ny, nx); params: list of Params."""
+
+    def __init__(self, fields, params, precision: str = "f32", stream=None):
+        lib = load()
+        self.n = len(fields)
+        if self.n != len(params) or self.n == 0:
+            raise ValueError("one Params per box")
+        dims = []
+        rr_all, rb_all = [], []
+        self.shapes = []
+        for rr, rb in fields:
+            rr, rb = _f64(rr), _f64(rb)
+            nz, ny, nx = rr.shape
+            dims += [nx, ny, nz]
+            self.shapes.append((nz, ny, nx))
+            rr_all.append(rr.ravel())
+            rb_all.append(rb.ravel())
+        d = (ctypes.c_int * len(dims))(*dims)
+        rr = np.ascontiguousarray(np.concatenate(rr_all))
+        rb = np.ascontiguousarray(np.concatenate(rb_all))
+        pa = (lb_params * self.n)(*[p.c() for p in params])
+        st = _current_stream() if stream is None else ctypes.c_void_p(stream)
+        b = ctypes.c_void_p()
+        _bcheck(lib.lb_batch_create(ctypes.byref(b), self.n, d, _dp(rr), _dp(rb), pa, PRECISIONS[precision], st))
+        self._b = b
+        self.precision = precision
+        self.params = list(params)
+
+    def set_schedule(self, tile_y: int = 8, planes_per_item: int = 32, ctas_per_sm: int = 0) -> "Batch":
+        _bcheck(load().lb_batch_set_schedule(self._b, tile_y, planes_per_item, ctas_per_sm), self._b)
+        return self
+
+    def set_params(self, i: int, params: Params) -> "Batch":
+        cp = params.c()
+        _bcheck(load().lb_batch_set_params(self._b, i, ctypes.byref(cp)), self._b)
+        self.params[i] = params
+        return self
+
+    def step(self, n: int = 1) -> "Batch":
+        _bcheck(load().lb_batch_step(self._b, int(n)), self._b)
+        return self
+
+    def box(self, i: int) -> Lattice:
+        c = ctypes.c_void_p()
+        _bcheck(load().lb_batch_box(self._b, i, ctypes.byref(c)), self._b)
+        return _BoxView(c, self.shapes[i], self.precision, self)
+
+    def conservation(self) -> np.ndarray:
+        out = np.empty((self.n, 8))
+        _bcheck(load().lb_batch_conservation(self._b, _dp(out)), self._b)
+        return out
+
+    def contact_angles(self, offset: float = 5.0) -> list:
+        recs = (lb_droplet * self.n)()
+        _bcheck(load().lb_batch_contact_angles(self._b, float(offset), recs), self._b)
+        return [{f: getattr(r, f) for f, _ in lb_droplet._fields_} for r in recs]
+
+    def close(self):
+        if getattr(self, "_b", None) is not None and self._b.value:
+            load().lb_batch_free(self._b)
+            self._b = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -25,6 +25,21 @@ def declared_functions():
     return sorted(set(re.findall(r"^\s*(?:int|void|const char\*)\s+(lb_\w+)\s*\(", text, flags=re.M)))
 
 
+def test_batch_argument_errors_before_cuda(lib):
+    from paper_0910_3915_gb300 import lbsc
+    b = ctypes.c_void_p()
+    dims = (ctypes.c_int * 3)(8, 8, 2)  # nz < 3: no room for the walls
+    rr = np.ones(128)
+    dp = rr.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    prm = (lbsc.lb_params * 1)(lbsc.Params().c())
+    assert lib.lb_batch_create(ctypes.byref(b), 1, dims, dp, dp, prm, lbsc.LB_F32, None) == lbsc.LB_ERR_ARG
+    assert lib.lb_batch_create(ctypes.byref(b), 0, dims, dp, dp, prm, lbsc.LB_F32, None) == lbsc.LB_ERR_ARG
+    assert b.value is None
+    assert b"dimensions" in lib.lb_batch_last_error(None) or b"argument" in lib.lb_batch_last_error(None)
+    assert lib.lb_batch_step(None, 1) == lbsc.LB_ERR_ARG
+    lib.lb_batch_free(None)
+
+
 def test_header_declares_the_boundary():
     names = declared_functions()
     for required in ("lb_init", "lb_set_geometry", "lb_set_params", "lb_step", "lb_moments",
