@@ -181,6 +181,32 @@ int lb_set_schedule(lb_ctx* ctx, int tile_y, int z_segments);
  * the precision, falls back to LB_STEP_LDG. */
 int lb_set_step_variant(lb_ctx* ctx, int variant, int stages);
 
+/* ------------------------------------------------------------ adjoint
+ * Observables of the final densities (phi = rho_r - rho_b, sigma the logistic
+ * function, eps = 0.05, sums over fluid nodes, heights above the wall plane):
+ *   LB_OBS_COM       sum (z - 1/2) rho_r / sum rho_r
+ *   LB_OBS_COM_SOFT  sum (z - 1/2) sigma(phi/eps) / sum sigma(phi/eps)  (droplet centre height)
+ *   LB_OBS_WETTED    sum over the first fluid layer of sigma(phi/eps)    (wetted area) */
+#define LB_OBS_COM 0
+#define LB_OBS_COM_SOFT 1
+#define LB_OBS_WETTED 2
+
+/* Advance nsteps time steps (the context ends at step nsteps, as after
+ * lb_step) and return J = observable of the final state and the exact
+ * gradient of J with respect to the wall pseudo-densities,
+ * dJ_deta[0] = dJ/d eta_wall_r, dJ_deta[1] = dJ/d eta_wall_b, computed by the
+ * discrete adjoint of the step (Sec. 2: the reverse of streaming with
+ * bounce-back, BGK with Eq. Equil, the velocity shift and Eq. SCforce with
+ * the wall as a species). States are checkpointed every ckpt_every steps
+ * and recomputed one segment at a time (device memory: nsteps/ckpt_every + 1
+ * + ckpt_every states). Planar walls only (LB_ERR_UNSUPPORTED otherwise).
+ * The paper calibrates the wall parameter by repeated runs; the gradient
+ * replaces that search. J may be NULL. */
+int lb_step_backward(lb_ctx* ctx, int nsteps, int ckpt_every, int observable, double* dJ_deta, double* J);
+
+/* The observable of the current state (no stepping). */
+int lb_observable(lb_ctx* ctx, int observable, double* J);
+
 /* ------------------------------------------------------------ batches
  * Many independent droplet lattices, each with its own size and parameters,
  * advanced together: one persistent kernel launch per time step walks a work

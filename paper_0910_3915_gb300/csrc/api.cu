@@ -15,6 +15,7 @@ using namespace lbsc;
 
 namespace lbsc {
 int step_occupancy(int precision, int tile_y, bool general, bool tau_one);
+
 }
 
 struct lb_ctx {
@@ -1168,3 +1169,167 @@ void lb_batch_free(lb_batch* b)
 }
 
 }  // extern "C"
+
+// ====================================================================== adjoint
+
+namespace {
+// device allocations of one lb_step_backward call, released on every path
+struct AdjScratch {
+    std::vector<void*> ptrs;
+    ~AdjScratch()
+    {
+        for (void* p : ptrs) cudaFree(p);
+    }
+    cudaError_t alloc(void** p, size_t bytes)
+    {
+        cudaError_t e = cudaMalloc(p, bytes);
+        if (e == cudaSuccess) ptrs.push_back(*p);
+        return e;
+    }
+};
+}  // namespace
+
+template <class S>
+static cudaError_t adj_step_into(lb_ctx* c, const void* src, void* dst, cudaStream_t st)
+{
+    StepArgs<S> A = step_args<S>(c, 0);
+    A.src = (const S*)src;
+    A.dst = (S*)dst;
+    return launch_step<S>(A, c->tile_y, c->general, tau_one(c), st);
+}
+
+template <class S>
+static cudaError_t adj_forward_of(lb_ctx* c, const void* f, const AdjFields& A, cudaStream_t st)
+{
+    return launch_adj_forward<S>(c->L, c->kp, (const S*)f, A, st);
+}
+
+extern "C" int lb_step_backward(lb_ctx* c, int nsteps, int ckpt_every, int observable, double* dJ_deta, double* J)
+{
+    if (!c || nsteps < 0 || ckpt_every < 1 || observable < 0 || observable > 2 || !dJ_deta)
+        return fail(c, LB_ERR_ARG, "lb_step_backward: bad argument");
+    if (c->general) return fail(c, LB_ERR_UNSUPPORTED, "lb_step_backward: planar walls only");
+    cudaStream_t st = c->stream;
+    const long long N = (long long)c->nx * c->ny * c->nz;
+    const size_t sb = payload_bytes(c);
+    const int nseg = (nsteps + ckpt_every - 1) / ckpt_every;
+    const int slen = nsteps < ckpt_every ? (nsteps > 0 ? nsteps : 1) : ckpt_every;
+    AdjScratch M;
+    char* ck = nullptr;
+    char* store = nullptr;
+    float* lam = nullptr;
+    float* aux = nullptr;
+    double* dsc = nullptr;
+    if (nseg > 0) LB_CUDA(c, M.alloc((void**)&ck, sb * (size_t)nseg));
+    LB_CUDA(c, M.alloc((void**)&store, sb * (size_t)(slen + 1)));
+    LB_CUDA(c, M.alloc((void**)&lam, sizeof(float) * 2 * 2 * Q * (size_t)N));
+    LB_CUDA(c, M.alloc((void**)&aux, sizeof(float) * 26 * (size_t)N));
+    LB_CUDA(c, M.alloc((void**)&dsc, sizeof(double) * (2 * kAdjBlocks + 8)));
+    double* part = dsc;
+    double* acc = dsc + 2 * kAdjBlocks;
+    double* sums = acc + 2;
+    AdjFields A;
+    {
+        float* q = aux;
+        for (int a = 0; a < 2; ++a) A.rho[a] = q, q += N;
+        for (int a = 0; a < 2; ++a) A.psi[a] = q, q += N;
+        for (int a = 0; a < 2; ++a)
+            for (int d = 0; d < 3; ++d) A.j[a][d] = q, q += N;
+        for (int a = 0; a < 2; ++a) A.rhob[a] = q, q += N;
+        for (int a = 0; a < 2; ++a)
+            for (int d = 0; d < 3; ++d) A.jb[a][d] = q, q += N;
+        for (int a = 0; a < 2; ++a)
+            for (int d = 0; d < 3; ++d) A.V[a][d] = q, q += N;
+        for (int a = 0; a < 2; ++a) A.psib[a] = q, q += N;
+    }
+    AdjArgs G;
+    G.nx = c->nx;
+    G.ny = c->ny;
+    G.nz = c->nz;
+    G.gk = c->kp.gk;
+    for (int k = 0; k < Q; ++k) G.G[k] = k == 0 ? 0.f : (is_axis(k) ? c->kp.Gax : c->kp.Gdi);
+    for (int a = 0; a < 2; ++a) {
+        G.tau[a] = c->kp.tau[a];
+        G.omega[a] = c->kp.itau[a];
+        G.eta[a] = c->kp.eta[a];
+    }
+    auto fwd = [&](const void* f) -> cudaError_t {
+        switch (c->prec) {
+        case LB_F32: return adj_forward_of<float>(c, f, A, st);
+        case LB_F16: return adj_forward_of<__half>(c, f, A, st);
+        default: return adj_forward_of<__nv_bfloat16>(c, f, A, st);
+        }
+    };
+    auto step_into = [&](const void* src, void* dst) -> cudaError_t {
+        switch (c->prec) {
+        case LB_F32: return adj_step_into<float>(c, src, dst, st);
+        case LB_F16: return adj_step_into<__half>(c, src, dst, st);
+        default: return adj_step_into<__nv_bfloat16>(c, src, dst, st);
+        }
+    };
+
+    // forward: a checkpoint at the start of every segment
+    for (int s = 0; s < nseg; ++s) {
+        LB_CUDA(c, cudaMemcpyAsync(ck + sb * (size_t)s, c->f[c->cur], sb, cudaMemcpyDeviceToDevice, st));
+        const int len = nsteps - s * ckpt_every < ckpt_every ? nsteps - s * ckpt_every : ckpt_every;
+        const int rc = lb_step(c, len);
+        if (rc != LB_OK) return rc;
+    }
+    // observable of the final state and lambda(T) = dJ/dn(T)
+    const double eps = 0.05;
+    float* lam_next = lam;
+    float* lam_cur = lam + 2 * Q * (size_t)N;
+    LB_CUDA(c, fwd(c->f[c->cur]));
+    LB_CUDA(c, launch_observable(c->nx, c->ny, c->nz, observable, eps, A.rho[0], A.rho[1], part, sums, lam_next, st));
+    LB_CUDA(c, cudaMemsetAsync(acc, 0, 2 * sizeof(double), st));
+    // backward, segment by segment: recompute the segment's states, then sweep them in reverse
+    for (int s = nseg - 1; s >= 0; --s) {
+        const int t0 = s * ckpt_every;
+        const int len = nsteps - t0 < ckpt_every ? nsteps - t0 : ckpt_every;
+        LB_CUDA(c, cudaMemcpyAsync(store, ck + sb * (size_t)s, sb, cudaMemcpyDeviceToDevice, st));
+        for (int i = 0; i < len; ++i) LB_CUDA(c, step_into(store + sb * (size_t)i, store + sb * (size_t)(i + 1)));
+        for (int i = len - 1; i >= 0; --i) {
+            LB_CUDA(c, fwd(store + sb * (size_t)i));
+            LB_CUDA(c, launch_adj_backstep(G, A, lam_next, lam_cur, part, acc, st));
+            std::swap(lam_next, lam_cur);
+        }
+    }
+    double h[3] = {0, 0, 0};
+    LB_CUDA(c, cudaMemcpyAsync(h, acc, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    LB_CUDA(c, cudaMemcpyAsync(h + 2, sums + 2, sizeof(double), cudaMemcpyDeviceToHost, st));
+    LB_CUDA(c, cudaStreamSynchronize(st));
+    dJ_deta[0] = h[0];
+    dJ_deta[1] = h[1];
+    if (J) *J = h[2];
+    return check_device_status(c);
+}
+
+extern "C" int lb_observable(lb_ctx* c, int observable, double* J)
+{
+    if (!c || !J || observable < 0 || observable > 2) return fail(c, LB_ERR_ARG, "lb_observable: bad argument");
+    if (c->general) return fail(c, LB_ERR_UNSUPPORTED, "lb_observable: planar walls only");
+    const long long N = (long long)c->nx * c->ny * c->nz;
+    AdjScratch M;
+    float* aux = nullptr;
+    double* dsc = nullptr;
+    LB_CUDA(c, M.alloc((void**)&aux, sizeof(float) * 10 * (size_t)N));
+    LB_CUDA(c, M.alloc((void**)&dsc, sizeof(double) * (2 * kAdjBlocks + 8)));
+    AdjFields A{};
+    float* q = aux;
+    for (int a = 0; a < 2; ++a) A.rho[a] = q, q += N;
+    for (int a = 0; a < 2; ++a) A.psi[a] = q, q += N;
+    for (int a = 0; a < 2; ++a)
+        for (int d = 0; d < 3; ++d) A.j[a][d] = q, q += N;
+    cudaError_t e;
+    switch (c->prec) {
+    case LB_F32: e = adj_forward_of<float>(c, c->f[c->cur], A, c->stream); break;
+    case LB_F16: e = adj_forward_of<__half>(c, c->f[c->cur], A, c->stream); break;
+    default: e = adj_forward_of<__nv_bfloat16>(c, c->f[c->cur], A, c->stream); break;
+    }
+    LB_CUDA(c, e);
+    LB_CUDA(c, launch_observable(c->nx, c->ny, c->nz, observable, 0.05, A.rho[0], A.rho[1], dsc,
+                                 dsc + 2 * kAdjBlocks, nullptr, c->stream));
+    LB_CUDA(c, cudaMemcpyAsync(J, dsc + 2 * kAdjBlocks + 2, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    LB_CUDA(c, cudaStreamSynchronize(c->stream));
+    return LB_OK;
+}

@@ -27,6 +27,30 @@ struct Scratch {
     float* u[3];
 };
 
+// Dense FP32 fields of the adjoint (index x + nx*(y + ny*z)).
+struct AdjFields {
+    float* rho[2];   // forward: densities
+    float* psi[2];   // forward: psi (wall pseudo-density on solid nodes)
+    float* j[2][3];  // forward: momenta
+    float* rhob[2];  // adjoint of rho before the psi term
+    float* jb[2][3]; // adjoint of j
+    float* V[2][3];  // adjoint of the neighbour sum S^a: -g kappa psi^a Fbar^a
+    float* psib[2];  // adjoint of psi^a from the node's own force
+};
+struct AdjArgs {
+    int nx, ny, nz;
+    float gk, G[Q];  // G[k]: neighbour weight of link k (G[0] unused)
+    float tau[2], omega[2];
+    float eta[2];
+};
+constexpr int kAdjBlocks = 512;
+template <class S>
+cudaError_t launch_adj_forward(const Layout& L, const KParams& P, const S* f, const AdjFields& A, cudaStream_t st);
+cudaError_t launch_adj_backstep(const AdjArgs& G, const AdjFields& A, const float* lam_next, float* lam_cur,
+                                double* part, double* acc, cudaStream_t st);
+cudaError_t launch_observable(int nx, int ny, int nz, int obs, double eps, const float* rr, const float* rb,
+                              double* part, double* sums, float* lam, cudaStream_t st);
+
 template <class S>
 cudaError_t launch_step(const StepArgs<S>& A, int tile_y, bool general, bool tau_one, cudaStream_t st);
 // TMA-staged step for planar walls: op 0 launches (returns a cudaError_t),

@@ -30,6 +30,8 @@ LB_F32, LB_F16, LB_BF16 = 0, 1, 2
 PRECISIONS = {"f32": LB_F32, "f16": LB_F16, "bf16": LB_BF16}
 LB_WEIGHTS_UNIT, LB_WEIGHTS_W36 = 0, 1
 LB_STEP_AUTO, LB_STEP_LDG, LB_STEP_TMA = 0, 1, 2
+LB_OBS_COM, LB_OBS_COM_SOFT, LB_OBS_WETTED = 0, 1, 2
+OBSERVABLES = {"com": LB_OBS_COM, "com_soft": LB_OBS_COM_SOFT, "wetted": LB_OBS_WETTED}
 STEP_VARIANTS = {"auto": LB_STEP_AUTO, "ldg": LB_STEP_LDG, "tma": LB_STEP_TMA}
 
 
@@ -93,6 +95,8 @@ SIGNATURES = [
     ("lb_set_populations", _I, [_VP, _DP]),
     ("lb_set_schedule", _I, [_VP, _I, _I]),
     ("lb_set_step_variant", _I, [_VP, _I, _I]),
+    ("lb_step_backward", _I, [_VP, _I, _I, _I, _DP, _DP]),
+    ("lb_observable", _I, [_VP, _I, _DP]),
     ("lb_batch_create", _I, [ctypes.POINTER(_VP), _I, ctypes.POINTER(_I), _DP, _DP, ctypes.POINTER(lb_params), _I, _VP]),
     ("lb_batch_set_params", _I, [_VP, _I, ctypes.POINTER(lb_params)]),
     ("lb_batch_set_schedule", _I, [_VP, _I, _I, _I]),
@@ -267,6 +271,20 @@ class Lattice:
         _check(load().lb_set_populations(self._ctx, _dp(a)), self._ctx)
         return self
 
+    # ------------------------------------------------------------ adjoint
+    def step_backward(self, nsteps: int, ckpt_every: int = 100, observable: str = "com_soft"):
+        """Advance nsteps; return (J, dJ/d(eta_wall_r, eta_wall_b)) by the discrete adjoint."""
+        g = np.zeros(2)
+        J = ctypes.c_double()
+        _check(load().lb_step_backward(self._ctx, int(nsteps), int(ckpt_every), OBSERVABLES[observable],
+                                       _dp(g), ctypes.byref(J)), self._ctx)
+        return J.value, g
+
+    def observable(self, observable: str = "com_soft") -> float:
+        J = ctypes.c_double()
+        _check(load().lb_observable(self._ctx, OBSERVABLES[observable], ctypes.byref(J)), self._ctx)
+        return J.value
+
     # ------------------------------------------------------------ checkpoints
     def save(self) -> bytes:
         nb = ctypes.c_size_t()
@@ -392,3 +410,29 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def wall_gradient(lattice: Lattice, initial_state: bytes, base: Params, nsteps: int, ckpt_every: int = 100,
+                  observable: str = "com_soft"):
+    """Torch autograd Function over the signed wall parameter w, (eta_r, eta_b) = (-w, +w).
+
+    Returns a function f(w_tensor) -> J_tensor whose backward uses the adjoint
+    gradient dJ/dw = dJ/deta_b - dJ/deta_r. Each call restarts from
+    ``initial_state`` (a checkpoint from Lattice.save())."""
+    import torch
+
+    class LBStepFn(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, w):
+            wv = float(w.detach().cpu())
+            lattice.load(initial_state)
+            lattice.set_params(Params(**{**base.__dict__, "eta_wall_r": -wv, "eta_wall_b": wv}))
+            J, g = lattice.step_backward(nsteps, ckpt_every, observable)
+            ctx.dJdw = g[1] - g[0]
+            return torch.tensor(J, dtype=torch.float64)
+
+        @staticmethod
+        def backward(ctx, grad):
+            return grad * ctx.dJdw
+
+    return LBStepFn.apply
