@@ -20,6 +20,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -39,6 +40,8 @@ WORKLOADS = {
     "small": dict(dims=(32, 32, 32), radius=8.0, precision="f32", w=0.05),
     # 64 cubic boxes, edges from {48, 64, 80, 96}, R = 0.3 edge, per-box g_br and wall value
     "sweep": dict(boxes=64, seed=3, precision="f32"),
+    # adjoint calibration: 64^3, R = 16, 2000 steps, checkpoints every 100
+    "adjoint": dict(dims=(64, 64, 64), radius=16.0, precision="f32", steps=2000, ckpt=100),
 }
 BYTES_PER_LU = {"f32": 304, "f16": 152, "bf16": 152}
 CONS_EVERY = 1000
@@ -399,12 +402,115 @@ def run_sweep(args):
     print(json.dumps(line), flush=True)
 
 
+def cap_centroid_height(volume: float, theta_deg: float) -> float:
+    """Height above its base of the centroid of a spherical cap of the given
+    volume and contact angle: V = pi R^3 (1 - c)^2 (2 + c) / 3, h = R (1 - c),
+    centroid 3 (2R - h)^2 / (4 (3R - h)) from the sphere centre, c = cos theta."""
+    c = math.cos(math.radians(theta_deg))
+    R = (3.0 * volume / (math.pi * (1 - c) ** 2 * (2 + c))) ** (1.0 / 3.0)
+    h = R * (1 - c)
+    return 3.0 * (2 * R - h) ** 2 / (4.0 * (3 * R - h)) - (R - h)
+
+
+def run_adjoint(args):
+    """Adjoint throughput, a check against FP64 oracle finite differences, and
+    calibration of the wall parameter to target contact angles."""
+    import numpy as np
+    import torch
+
+    import oracle
+    from paper_0910_3915_gb300 import lbsc
+    from paper_0910_3915_gb300 import workloads as W
+
+    torch.cuda.set_device(0)
+    wl = WORKLOADS["adjoint"]
+    nx, ny, nz = wl["dims"]
+    T, ck = wl["steps"], wl["ckpt"]
+    nf = nx * ny * (nz - 2)
+    rr, rb = W.droplet_fields(nx, ny, nz, wl["radius"], seed=0)
+    lat = lbsc.Lattice(rr, rb, wl["precision"]).set_params(**CONTACT)
+    s0 = lat.save()
+    lat.step_backward(10, ck)  # warm-up
+    lat.load(s0)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    J0, g0 = lat.step_backward(T, ck)
+    adj_s = time.perf_counter() - t
+    lat.load(s0)
+    t = time.perf_counter()
+    lat.step(T)
+    lat.sync()
+    fwd_s = time.perf_counter() - t
+
+    # FP64 oracle central differences (h = 1e-4) of the same observable, 200 steps
+    Tc, h = 200, 1e-4
+    lat.load(s0)
+    Jc, gc = lat.step_backward(Tc, ck)
+
+    def oJ(prm):
+        st = oracle.State(rr, rb, W.wall_mask(nx, ny, nz), oracle.Params(**prm)).step(Tc)
+        r, b, _, _ = st.moments()
+        w = 1.0 / (1.0 + np.exp(-(r - b) / 0.05))
+        zz = np.arange(nz)[:, None, None] - 0.5 + 0 * r
+        return float((zz * w)[1:-1].sum() / w[1:-1].sum())
+
+    fd = []
+    for comp in ("eta_wall_r", "eta_wall_b"):
+        jp = oJ(dict(CONTACT, **{comp: h}))
+        jm = oJ(dict(CONTACT, **{comp: -h}))
+        fd.append((jp - jm) / (2 * h))
+    fd_err = float(np.max(np.abs(np.array(gc) - fd)) / np.max(np.abs(fd)))
+
+    # calibration: Newton steps on J(w) = J*(theta*) with dJ/dw from the adjoint
+    lat.load(s0)
+    lat.step(T)
+    r, b, _, _ = lat.moments()
+    vol = float((1.0 / (1.0 + np.exp(-(r - b) / 0.05)))[1:-1].sum())
+    calib = []
+    for target in (60.0, 90.0, 120.0):
+        Jt = cap_centroid_height(vol, target)
+        w, hist = 0.0, []
+        for _ in range(6):
+            lat.load(s0)
+            lat.set_params(**CONTACT, eta_wall_r=-w, eta_wall_b=w)
+            J, g = lat.step_backward(T, ck)
+            dJdw = g[1] - g[0]
+            hist.append((round(w, 5), round(J, 4)))
+            if abs(J - Jt) < 1e-3 or dJdw == 0:
+                break
+            w = float(np.clip(w - (J - Jt) / dJdw, -0.15, 0.15))
+        lat.load(s0)
+        lat.set_params(**CONTACT, eta_wall_r=-w, eta_wall_b=w)
+        lat.step(T)
+        ca = lat.contact_angle(5.0)
+        calib.append({"theta_target": target, "J_target": round(Jt, 4), "w": round(w, 5),
+                      "theta_measured": round(ca["theta_deg"], 2) if ca["ok"] else None,
+                      "theta_fit": round(ca["theta_fit_deg"], 2), "iterations": hist})
+    lat.close()
+    line = {
+        "metric": METRIC, "value": round(nf * T / adj_s / 1e6, 1), "unit": "MLUPS",
+        "n_gpus": 1, "steps": T, "warmup": 1, "ms_per_step": round(adj_s / T * 1e3, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": wl["precision"], "data": "synthetic",
+        "config": {"workload": f"adjoint calibration: droplet {nx}^3 R={wl['radius']:g}, {T} steps, checkpoint every {ck}",
+                   "observable": "soft droplet centre height, sigma(phi/0.05) weights"},
+        "adjoint_seconds": round(adj_s, 3), "forward_seconds": round(fwd_s, 3),
+        "adjoint_over_forward": round(adj_s / fwd_s, 2),
+        "gradient": [float(g0[0]), float(g0[1])], "J": J0,
+        "fd_check": {"steps": Tc, "h": h, "adjoint": [float(gc[0]), float(gc[1])], "oracle_fd": fd,
+                     "max_rel_err": fd_err},
+        "calibration": calib,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "sweep":
         run_sweep(args)
+    elif args.workload == "adjoint":
+        run_adjoint(args)
     else:
         run_ours(args)
 
