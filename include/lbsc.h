@@ -176,9 +176,6 @@ int lb_set_schedule(lb_ctx* ctx, int tile_y, int z_segments);
 
 /* Choose the step kernel: LB_STEP_AUTO, LB_STEP_LDG or LB_STEP_TMA, and for
  * the TMA kernel the number of shared-memory stages (2 or 3; 0 = automatic).
- * For LB_STEP_LDG a non-zero `stages` instead caps registers so that this
- * many CTAs reside per SM (3 with tile height 8, 5 with 4, 2 with 16; planar
- * walls and tau = 1; other values fall back to the uncapped kernel).
  * Every variant computes bit-identical results. LB_STEP_TMA with a
  * non-planar geometry, or a (tile height, stages) pair that is not built for
  * the precision, falls back to LB_STEP_LDG. */

@@ -331,20 +331,6 @@ static cudaError_t launch_steps(lb_ctx* c, int n, int& parity, cudaStream_t st)
             parity ^= 1;
             continue;
         }
-        // the load-from-global kernel with a register cap: 'stages' names the resident CTAs per SM
-        const bool capped = c->variant == LB_STEP_LDG && c->stages > 0 && !c->general && t1;
-        if (capped) {
-            switch (c->prec) {
-            case LB_F32: e = launch_step_capped<float>(step_args<float>(c, parity), c->tile_y, c->stages, st); break;
-            case LB_F16: e = launch_step_capped<__half>(step_args<__half>(c, parity), c->tile_y, c->stages, st); break;
-            default:
-                e = launch_step_capped<__nv_bfloat16>(step_args<__nv_bfloat16>(c, parity), c->tile_y, c->stages, st);
-                break;
-            }
-            if (e != cudaSuccess) return e;
-            parity ^= 1;
-            continue;
-        }
         switch (c->prec) {
         case LB_F32: e = launch_step<float>(step_args<float>(c, parity), c->tile_y, c->general, t1, st); break;
         case LB_F16: e = launch_step<__half>(step_args<__half>(c, parity), c->tile_y, c->general, t1, st); break;
@@ -564,7 +550,7 @@ int lb_set_params(lb_ctx* c, const lb_params* p)
 int lb_set_step_variant(lb_ctx* c, int variant, int stages)
 {
     if (!c) return fail(c, LB_ERR_ARG, "lb_set_step_variant: NULL context");
-    if (variant < LB_STEP_AUTO || variant > LB_STEP_TMA || stages < 0 || stages > 5)
+    if (variant < LB_STEP_AUTO || variant > LB_STEP_TMA || (stages != 0 && stages != 2 && stages != 3))
         return fail(c, LB_ERR_ARG, "lb_set_step_variant: unknown variant or stages");
     drop_graphs(c);
     c->variant = variant;

@@ -60,8 +60,6 @@ template <class S>
 long long tma_step(int op, int tile_y, int stages, bool tau_one, const CUtensorMap* map, const StepArgs<S>* args,
                    cudaStream_t stream);
 template <class S>
-cudaError_t launch_step_capped(const StepArgs<S>& A, int tile_y, int occ, cudaStream_t st);
-template <class S>
 cudaError_t launch_batch_step(const StepArgs<S>* args, const int4* items, int nitems, int parity, int tile_y,
                               bool tau_one, int grid, cudaStream_t st);
 template <class S>

@@ -179,8 +179,8 @@ __device__ __forceinline__ void step_item(const StepArgs<S>& A, int col, int za,
     }
 }
 
-template <class S, int TY, bool kGeneral, bool kTauOne, int MINB = 1>
-__global__ void __launch_bounds__(32 * TY, MINB) step_kernel(const StepArgs<S> A)
+template <class S, int TY, bool kGeneral, bool kTauOne>
+__global__ void __launch_bounds__(32 * TY) step_kernel(const StepArgs<S> A)
 {
     __shared__ float sp[4][2][TY + 2][34];  // psi of 4 planes, slot = z & 3
     const int ncol = A.tiles_x * A.tiles_y;
@@ -209,26 +209,13 @@ __global__ void __launch_bounds__(32 * TY)
     }
 }
 
-template <class S, int TY, bool G, bool T1, int MINB = 1>
+template <class S, int TY, bool G, bool T1>
 static cudaError_t launch_one(const StepArgs<S>& A, cudaStream_t st)
 {
     const int items = A.tiles_x * A.tiles_y * A.nseg;
-    step_kernel<S, TY, G, T1, MINB><<<items, 32 * TY, 0, st>>>(A);
+    step_kernel<S, TY, G, T1><<<items, 32 * TY, 0, st>>>(A);
     return cudaGetLastError();
 }
-
-// planar walls, tau = 1, with a register cap that lets `occ` CTAs reside per SM
-template <class S>
-cudaError_t launch_step_capped(const StepArgs<S>& A, int tile_y, int occ, cudaStream_t st)
-{
-    if (tile_y == 8 && occ == 3) return launch_one<S, 8, false, true, 3>(A, st);
-    if (tile_y == 4 && occ == 5) return launch_one<S, 4, false, true, 5>(A, st);
-    if (tile_y == 16 && occ == 2) return launch_one<S, 16, false, true, 2>(A, st);
-    return cudaErrorInvalidValue;
-}
-template cudaError_t launch_step_capped<float>(const StepArgs<float>&, int, int, cudaStream_t);
-template cudaError_t launch_step_capped<__half>(const StepArgs<__half>&, int, int, cudaStream_t);
-template cudaError_t launch_step_capped<__nv_bfloat16>(const StepArgs<__nv_bfloat16>&, int, int, cudaStream_t);
 
 template <class S, int TY>
 static cudaError_t launch_ty(const StepArgs<S>& A, bool general, bool tau_one, cudaStream_t st)

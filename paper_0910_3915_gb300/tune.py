@@ -28,9 +28,6 @@ def candidates(nz_fluid: int, precision: str, segments=SEGMENTS):
         out += [("tma", ns, ty, s) for s in segments if nz_fluid // s >= 4]
     for ty in LDG_TILES:
         out += [("ldg", 0, ty, s) for s in segments if nz_fluid // s >= 4]
-    # register-capped load kernel (resident CTAs per SM in the stages field)
-    for ty, occ in ((8, 3), (4, 5), (16, 2)):
-        out += [("ldg", occ, ty, s) for s in segments if nz_fluid // s >= 4]
     return out
 
 
