@@ -134,6 +134,14 @@ int lb_step(lb_ctx* ctx, int nsteps);
 /* Wait for the stream and report a device-side failure, if any. */
 int lb_sync(lb_ctx* ctx);
 
+/* Failure-detection self-test (a library facility; the paper has no
+ * counterpart). Runs the bounded device-side wait used by the TMA-staged step
+ * on an mbarrier that nothing completes, with spin_limit try_wait rounds
+ * (1 .. 2^20). The wait gives up, the kernel records the failure in the
+ * context's device status word and returns without faulting. Returns
+ * LB_ERR_BARRIER_TIMEOUT (the expected outcome); the context stays usable. */
+int lb_selftest_bounded_wait(lb_ctx* ctx, unsigned spin_limit);
+
 /* Read densities and conservation sums (Sec. 2, moments). Any output may be NULL.
  * rho_r, rho_b: nx*ny*nz doubles. u: 3*nx*ny*nz doubles (component-major),
  * the barycentric velocity (sum_a j^a + F/2)/sum_a rho^a with F the total

@@ -547,6 +547,14 @@ int lb_set_params(lb_ctx* c, const lb_params* p)
     return LB_OK;
 }
 
+int lb_selftest_bounded_wait(lb_ctx* c, unsigned spin_limit)
+{
+    if (!c || spin_limit < 1 || spin_limit > (1u << 20))
+        return fail(c, LB_ERR_ARG, "lb_selftest_bounded_wait: spin_limit in [1, 2^20]");
+    LB_CUDA(c, launch_wait_probe(c->dev_err, spin_limit, c->stream));
+    return lb_sync(c);
+}
+
 int lb_set_step_variant(lb_ctx* c, int variant, int stages)
 {
     if (!c) return fail(c, LB_ERR_ARG, "lb_set_step_variant: NULL context");

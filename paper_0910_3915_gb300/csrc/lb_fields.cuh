@@ -64,6 +64,8 @@ cudaError_t launch_batch_step(const StepArgs<S>* args, const int4* items, int ni
                               bool tau_one, int grid, cudaStream_t st);
 template <class S>
 int batch_occupancy(int tile_y, bool tau_one);
+// bounded-wait self-test: a wait nothing satisfies, limit try_wait rounds
+cudaError_t launch_wait_probe(int* err, unsigned limit, cudaStream_t st);
 template <class S>
 cudaError_t launch_ghosts(const Layout& L, S* f, int z0, int z1, cudaStream_t st);
 template <class S>

@@ -307,3 +307,20 @@ def test_full_size_sampled_nodes(lbsc, precision, dims, radius, tol):
         got = n7[:, :, z, y, x]
         worst = max(worst, float(np.max(np.abs(got - ref)) / np.max(np.abs(ref))))
     assert worst <= tol, worst
+
+
+def test_bounded_wait_reports_timeout_and_context_survives(lbsc):
+    """Failure detection without a GPU fault: a device wait that nothing
+    satisfies gives up after its limit, the status word surfaces as
+    LB_ERR_BARRIER_TIMEOUT, and the context keeps working."""
+    import ctypes
+    nx, ny, nz = 32, 16, 10
+    rr, rb = W.droplet_fields(nx, ny, nz, 4.0, seed=1)
+    lat = lbsc.Lattice(rr, rb).set_params(**CONTACT)
+    lib = lbsc.load()
+    assert lib.lb_selftest_bounded_wait(lat._ctx, 2000) == lbsc.LB_ERR_BARRIER_TIMEOUT
+    assert b"gave up" in lib.lb_last_error(lat._ctx)
+    lat.step(10)
+    cons = lat.conservation()  # the status word was cleared: no error now
+    assert cons[7] == 10 and cons[5] == 0
+    lat.close()
