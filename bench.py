@@ -40,6 +40,9 @@ WORKLOADS = {
     "small": dict(dims=(32, 32, 32), radius=8.0, precision="f32", w=0.05),
     # 64 cubic boxes, edges from {48, 64, 80, 96}, R = 0.3 edge, per-box g_br and wall value
     "sweep": dict(boxes=64, seed=3, precision="f32"),
+    # 11 wall values in [-0.1, 0.1] on the 128^3 droplet, 20000 steps, as one batch
+    "angles": dict(dims=(128, 128, 128), radius=30.0, precision="f32", steps=20000,
+                   w=[round(-0.1 + 0.02 * i, 3) for i in range(11)]),
     # adjoint calibration: 64^3, R = 16, 2000 steps, checkpoints every 100
     "adjoint": dict(dims=(64, 64, 64), radius=16.0, precision="f32", steps=2000, ckpt=100),
 }
@@ -318,6 +321,8 @@ def run_ours(args):
     }
     m0 = float(rr[1:-1].sum()), float(rb[1:-1].sum())
     line["mass_rel_drift"] = [float(cons[0] / m0[0] - 1), float(cons[1] / m0[1] - 1)]
+    if args.workload.startswith("precision") and ws == 1:
+        line["accuracy"] = precision_accuracy(prec, 10000)
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
@@ -503,6 +508,123 @@ def run_adjoint(args):
     print(json.dumps(line), flush=True)
 
 
+def bulk_densities(rr, rb):
+    """Bulk r density inside the drop and outside (medians over the cores of each phase)."""
+    import numpy as np
+    phi = (rr - rb)[1:-1]
+    r = rr[1:-1]
+    inside = r[phi > 0.8 * phi.max()]
+    outside = r[phi < 0.8 * phi.min()]
+    return float(np.median(inside)), float(np.median(outside))
+
+
+def run_angles(args):
+    """Contact angle against the wall parameter on the 128^3 droplet (Sec. 4, Fig. 4 right):
+    geometric theta, sphere-fit theta, the half-max |phi| interfaces as error bars, and
+    Huang's closed-form estimate (Eq. huangSigmaLG) for comparison."""
+    import torch
+
+    from paper_0910_3915_gb300 import lbsc
+    from paper_0910_3915_gb300 import workloads as W
+
+    torch.cuda.set_device(0)
+    wl = WORKLOADS["angles"]
+    nx, ny, nz = wl["dims"]
+    T = args.steps if args.steps != 20000 else wl["steps"]
+    ws = wl["w"]
+    fields = [W.droplet_fields(nx, ny, nz, wl["radius"], seed=0) for _ in ws]
+    params = [lbsc.Params(**CONTACT, eta_wall_r=W.wall_split(w)[0], eta_wall_b=W.wall_split(w)[1]) for w in ws]
+    batch = lbsc.Batch(fields, params, wl["precision"])
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    batch.step(64)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    batch.step(T - 64)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    nf = nx * ny * (nz - 2) * len(ws)
+    rows = []
+    for i, w in enumerate(ws):
+        box = batch.box(i)
+        rr, rb, _, cons = box.moments()
+        phi = rr - rb
+        a0 = box.contact_angle(5.0)
+        hi = box.contact_angle(5.0, level=0.5 * float(phi[1:-1].max()))
+        lo = box.contact_angle(5.0, level=0.5 * float(phi[1:-1].min()))
+        r_in, r_out = bulk_densities(rr, rb)
+        # Huang: cos theta = (G_ads,r - G_ads,b) / (g (rho_in - rho_out) / 2) with G_ads = g eta, read so that
+        # a wall repelling r (w > 0) gives theta > 90: cos theta = -(2 w) / ((rho_in - rho_out) / 2)
+        c = -(2.0 * w) / ((r_in - r_out) / 2.0)
+        th_h = math.degrees(math.acos(max(-1.0, min(1.0, c))))
+        rows.append({"w": w, "theta": round(a0["theta_deg"], 2) if a0["ok"] else None,
+                     "theta_fit": round(a0["theta_fit_deg"], 2),
+                     "theta_halfmax": [round(hi["theta_deg"], 2) if hi["ok"] else None,
+                                       round(lo["theta_deg"], 2) if lo["ok"] else None],
+                     "huang": round(th_h, 2), "rho_in": round(r_in, 4), "rho_out": round(r_out, 4),
+                     "h": round(a0["h"], 2), "b": round(a0["b"], 2)})
+    batch.close()
+    line = {
+        "metric": METRIC, "value": round(nf * (T - 64) / (ms * 1e-3) / 1e6, 1), "unit": "MLUPS", "n_gpus": 1,
+        "steps": T, "warmup": 64, "ms_per_step": round(ms / (T - 64), 5), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": wl["precision"], "data": "synthetic",
+        "config": {"workload": f"theta vs wall parameter: {len(ws)} droplets {nx}^3 R={wl['radius']:g}, {T} steps, one batch"},
+        "angles": rows,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def precision_accuracy(prec: str, steps: int):
+    """16-bit storage against FP32 on the full lattice, and against the FP64 oracle on the
+    64x64x32 copy (same set-up scaled by 1/4)."""
+    import numpy as np
+
+    import oracle
+    from paper_0910_3915_gb300 import lbsc
+    from paper_0910_3915_gb300 import workloads as W
+
+    out = {}
+    er, eb = W.wall_split(0.05)
+    prm = dict(CONTACT, eta_wall_r=er, eta_wall_b=eb)
+    # full size: 16-bit vs FP32
+    nx, ny, nz = 256, 256, 128
+    rr, rb = W.droplet_fields(nx, ny, nz, 60.0, seed=0)
+    res = {}
+    for p in ("f32", prec):
+        lat = lbsc.Lattice(rr, rb, p).set_params(**prm)
+        m0 = lat.conservation()[:2]
+        lat.step(steps)
+        r, b, _, cons = lat.moments()
+        res[p] = (r, b, lat.contact_angle(5.0), cons[:2] / m0 - 1.0)
+        lat.close()
+    fl = np.s_[1:-1]
+    rel = max(float(np.max(np.abs(res[prec][k][fl] - res["f32"][k][fl]) / np.abs(res["f32"][k][fl]))) for k in (0, 1))
+    rms = max(float(np.sqrt(np.mean(((res[prec][k][fl] - res["f32"][k][fl]) / res["f32"][k][fl]) ** 2))) for k in (0, 1))
+    out["vs_fp32_256x256x128"] = {"steps": steps, "max_rel_density_err": rel, "rms_rel_density_err": rms,
+                                  "theta_fp32": res["f32"][2]["theta_deg"], "theta": res[prec][2]["theta_deg"],
+                                  "theta_err_deg": abs(res[prec][2]["theta_deg"] - res["f32"][2]["theta_deg"]),
+                                  "mass_drift": [float(v) for v in res[prec][3]],
+                                  "mass_drift_fp32": [float(v) for v in res["f32"][3]]}
+    # 64x64x32 copy against the FP64 oracle
+    nx, ny, nz, S = 64, 64, 32, 1000
+    rr, rb = W.droplet_fields(nx, ny, nz, 15.0, seed=0)
+    st = oracle.State(rr, rb, W.wall_mask(nx, ny, nz), oracle.Params(**prm)).step(S)
+    orr, orb, _, _ = st.moments()
+    oca = oracle.contact_angle(orr, orb, st.solid, 3.0)
+    for p in ("f32", prec):
+        lat = lbsc.Lattice(rr, rb, p).set_params(**prm)
+        lat.step(S)
+        r, b, _, _ = lat.moments()
+        ca = lat.contact_angle(3.0)
+        lat.close()
+        e = max(float(np.max(np.abs((r, b)[k][fl] - (orr, orb)[k][fl]) / np.abs((orr, orb)[k][fl]))) for k in (0, 1))
+        out[f"vs_oracle_64x64x32_{p}"] = {"steps": S, "max_rel_density_err": e, "theta": ca["theta_deg"],
+                                          "theta_oracle": oca["theta_deg"],
+                                          "theta_err_deg": abs(ca["theta_deg"] - oca["theta_deg"])}
+    return out
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -511,6 +633,8 @@ def main():
         run_sweep(args)
     elif args.workload == "adjoint":
         run_adjoint(args)
+    elif args.workload == "angles":
+        run_angles(args)
     else:
         run_ours(args)
 

@@ -162,6 +162,11 @@ int lb_conservation(lb_ctx* ctx, double cons[8]);
  * when no cap is found. */
 int lb_contact_angle(lb_ctx* ctx, double offset, lb_droplet* out);
 
+/* As lb_contact_angle with the interface at phi = level instead of phi = 0.
+ * Fig. 4 of the paper draws its error bars from the interface at half the
+ * maximum |phi|: level = +max(phi)/2 and level = min(phi)/2. */
+int lb_contact_angle_at(lb_ctx* ctx, double offset, double level, lb_droplet* out);
+
 /* Checkpoint: bytes of the state, and copies to / from a host buffer of that
  * size. The state is the population array plus the step counter; params and
  * geometry are not part of it. */

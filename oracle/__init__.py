@@ -94,6 +94,9 @@ def lib():
         _lib.lbo_moments.argtypes = [ctypes.POINTER(_Params), i, i, i, u8, d, d, d, d, d]
         _lib.lbo_contact_angle.argtypes = [i, i, i, u8, d, d, ctypes.c_double, ctypes.POINTER(_Droplet)]
         _lib.lbo_contact_angle.restype = ctypes.c_int
+        _lib.lbo_contact_angle_level.argtypes = [i, i, i, u8, d, d, ctypes.c_double, ctypes.c_double,
+                                                 ctypes.POINTER(_Droplet)]
+        _lib.lbo_contact_angle_level.restype = ctypes.c_int
         _lib.lbo_pressure_tensor.argtypes = [ctypes.POINTER(_Params), i, i, i, u8, d, d]
     return _lib
 
@@ -179,11 +182,13 @@ class State:
         return contact_angle(rr, rb, self.solid, offset)
 
 
-def contact_angle(rho_r: np.ndarray, rho_b: np.ndarray, solid: np.ndarray, offset: float = 5.0) -> dict:
+def contact_angle(rho_r: np.ndarray, rho_b: np.ndarray, solid: np.ndarray, offset: float = 5.0,
+                  level: float = 0.0) -> dict:
     nz, ny, nx = rho_r.shape
     out = _Droplet()
     rr = np.ascontiguousarray(rho_r, dtype=np.float64)
     rb = np.ascontiguousarray(rho_b, dtype=np.float64)
     s = np.ascontiguousarray(solid, dtype=np.uint8)
-    lib().lbo_contact_angle(nx, ny, nz, _u8(s), _dp(rr), _dp(rb), float(offset), ctypes.byref(out))
+    lib().lbo_contact_angle_level(nx, ny, nz, _u8(s), _dp(rr), _dp(rb), float(offset), float(level),
+                                  ctypes.byref(out))
     return {f: getattr(out, f) for f, _ in _Droplet._fields_}

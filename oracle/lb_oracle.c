@@ -362,11 +362,20 @@ int lbo_contact_angle(int nx, int ny, int nz, const uint8_t* solid,
                       const double* rho_r, const double* rho_b, double offset,
                       lbo_droplet* out)
 {
+    return lbo_contact_angle_level(nx, ny, nz, solid, rho_r, rho_b, offset, 0.0, out);
+}
+
+/* As above with the interface taken at phi = level instead of phi = 0
+ * (Fig. 4's error bars use half the maximum |phi|). */
+int lbo_contact_angle_level(int nx, int ny, int nz, const uint8_t* solid,
+                            const double* rho_r, const double* rho_b, double offset, double level,
+                            lbo_droplet* out)
+{
     memset(out, 0, sizeof(*out));
     const double zw = 0.5;
     size_t N = (size_t)nx * ny * nz;
     double* phi = (double*)malloc(sizeof(double) * N);
-    for (size_t i = 0; i < N; ++i) phi[i] = solid[i] ? 0.0 : rho_r[i] - rho_b[i];
+    for (size_t i = 0; i < N; ++i) phi[i] = solid[i] ? 0.0 : rho_r[i] - rho_b[i] - level;
 
     /* apex: highest phi = 0 crossing from phi > 0 below to phi <= 0 above */
     double top = -1e300;

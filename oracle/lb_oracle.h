@@ -82,6 +82,11 @@ int lbo_contact_angle(int nx, int ny, int nz, const uint8_t* solid,
                       const double* rho_r, const double* rho_b, double offset,
                       lbo_droplet* out);
 
+/* The same with the interface at phi = level (Fig. 4 error bars: half max |phi|). */
+int lbo_contact_angle_level(int nx, int ny, int nz, const uint8_t* solid,
+                            const double* rho_r, const double* rho_b, double offset, double level,
+                            lbo_droplet* out);
+
 /* Pressure tensor of Sec. 4.1 per node: P[(c)*N + idx], c = xx, yy, zz, xy, xz, yz. */
 void lbo_pressure_tensor(const lbo_params* p, int nx, int ny, int nz, const uint8_t* solid,
                          const double* n, double* P);

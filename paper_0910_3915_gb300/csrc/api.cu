@@ -723,13 +723,16 @@ static int solve4(double M[4][4], double v[4], double s[4])
     return 0;
 }
 
-int lb_contact_angle(lb_ctx* c, double offset, lb_droplet* out)
+int lb_contact_angle(lb_ctx* c, double offset, lb_droplet* out) { return lb_contact_angle_at(c, offset, 0.0, out); }
+
+int lb_contact_angle_at(lb_ctx* c, double offset, double level, lb_droplet* out)
 {
-    if (!c || !out || !(offset >= 0) || !std::isfinite(offset)) return fail(c, LB_ERR_ARG, "lb_contact_angle: bad argument");
+    if (!c || !out || !(offset >= 0) || !std::isfinite(offset) || !std::isfinite(level))
+        return fail(c, LB_ERR_ARG, "lb_contact_angle: bad argument");
     memset(out, 0, sizeof(*out));
     const double zw = 0.5, zref = zw + offset;
     LB_CUDA(c, dispatch_fields(c, false));
-    LB_CUDA(c, launch_angle(field_args(c), c->W, zref, c->part, c->red, c->stream));
+    LB_CUDA(c, launch_angle(field_args(c), c->W, zref, level, c->part, c->red, c->stream));
     LB_CUDA(c, cudaMemcpyAsync(c->h_red, c->red, kAngleVals * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     LB_CUDA(c, cudaStreamSynchronize(c->stream));
     const double* v = c->h_red;

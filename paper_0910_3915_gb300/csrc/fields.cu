@@ -185,7 +185,8 @@ __global__ void velocity_kernel(FieldArgs F, Scratch W)
 // Per column (x, y): top phi = 0 crossing (max), positive length of the
 // reference-plane interpolant along x, and sphere-fit sums of interface points.
 // acc = {top, area, npts, M00, M01, M02, M03, M11, M12, M13, M22, M23, M33, v0, v1, v2, v3}
-__global__ void __launch_bounds__(kRedThreads) angle_kernel(FieldArgs F, Scratch W, double zref, double* __restrict__ part)
+__global__ void __launch_bounds__(kRedThreads) angle_kernel(FieldArgs F, Scratch W, double zref, double level,
+                                                            double* __restrict__ part)
 {
     const int nx = F.L.nx, ny = F.L.ny, nz = F.L.nz;
     double acc[kAngleVals];
@@ -195,7 +196,7 @@ __global__ void __launch_bounds__(kRedThreads) angle_kernel(FieldArgs F, Scratch
     const double fz = zref - z0;
     auto phi = [&](int x, int y, int z) -> double {
         const long long i = (long long)x + (long long)nx * (y + (long long)ny * z);
-        return (double)W.rho[0][i] - (double)W.rho[1][i];
+        return (double)W.rho[0][i] - (double)W.rho[1][i] - level;
     };
     auto solid = [&](int x, int y, int z) -> bool {
         const long long off = F.L.off(x, y, z);
@@ -348,9 +349,10 @@ cudaError_t launch_fields(const FieldArgs& F, const S* f, const Scratch& W, bool
     return cudaGetLastError();
 }
 
-cudaError_t launch_angle(const FieldArgs& F, const Scratch& W, double zref, double* part, double* out, cudaStream_t st)
+cudaError_t launch_angle(const FieldArgs& F, const Scratch& W, double zref, double level, double* part, double* out,
+                         cudaStream_t st)
 {
-    angle_kernel<<<kRedBlocks, kRedThreads, 0, st>>>(F, W, zref, part);
+    angle_kernel<<<kRedBlocks, kRedThreads, 0, st>>>(F, W, zref, level, part);
     finish_kernel<kAngleVals><<<1, 32, 0, st>>>(part, kRedBlocks, 1u, out);
     return cudaGetLastError();
 }

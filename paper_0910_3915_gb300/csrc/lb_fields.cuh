@@ -74,7 +74,8 @@ template <class S>
 cudaError_t launch_conservation(const FieldArgs& F, const S* f, double* part, double* out, cudaStream_t st);
 template <class S>
 cudaError_t launch_fields(const FieldArgs& F, const S* f, const Scratch& W, bool velocity, cudaStream_t st);
-cudaError_t launch_angle(const FieldArgs& F, const Scratch& W, double zref, double* part, double* out, cudaStream_t st);
+cudaError_t launch_angle(const FieldArgs& F, const Scratch& W, double zref, double level, double* part, double* out,
+                         cudaStream_t st);
 template <class S>
 cudaError_t launch_get_pop(const FieldArgs& F, const S* f, double* out, cudaStream_t st);
 template <class S>

@@ -89,6 +89,7 @@ SIGNATURES = [
     ("lb_moments", _I, [_VP, _DP, _DP, _DP, _DP]),
     ("lb_conservation", _I, [_VP, _DP]),
     ("lb_contact_angle", _I, [_VP, ctypes.c_double, ctypes.POINTER(lb_droplet)]),
+    ("lb_contact_angle_at", _I, [_VP, ctypes.c_double, ctypes.c_double, ctypes.POINTER(lb_droplet)]),
     ("lb_state_bytes", _I, [_VP, ctypes.POINTER(ctypes.c_size_t)]),
     ("lb_save", _I, [_VP, _VP, ctypes.c_size_t]),
     ("lb_load", _I, [_VP, _VP, ctypes.c_size_t]),
@@ -255,9 +256,9 @@ class Lattice:
         _check(load().lb_conservation(self._ctx, _dp(cons)), self._ctx)
         return cons
 
-    def contact_angle(self, offset: float = 5.0) -> dict:
+    def contact_angle(self, offset: float = 5.0, level: float = 0.0) -> dict:
         d = lb_droplet()
-        _check(load().lb_contact_angle(self._ctx, float(offset), ctypes.byref(d)), self._ctx)
+        _check(load().lb_contact_angle_at(self._ctx, float(offset), float(level), ctypes.byref(d)), self._ctx)
         return {f: getattr(d, f) for f, _ in lb_droplet._fields_}
 
     def populations(self) -> np.ndarray:
