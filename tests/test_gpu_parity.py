@@ -237,6 +237,13 @@ def test_contact_angle_measurement_on_analytic_caps(lbsc):
         assert abs(g["theta_deg"] - o["theta_deg"]) < 0.01
         assert abs(g["theta_fit_deg"] - o["theta_fit_deg"]) < 0.01
         assert g["n_points"] == o["n_points"]
+        # interface at a phi level (the half-max |phi| error bars of Fig. 4)
+        lat = lbsc.Lattice(rr, rb)
+        gl = lat.contact_angle(5.0, level=0.2)
+        lat.close()
+        ol = oracle.contact_angle(rr, rb, W.wall_mask(n, n, nz), 5.0, level=0.2)
+        assert gl["ok"] == 1 and abs(gl["theta_deg"] - ol["theta_deg"]) < 0.01
+        assert abs(gl["theta_deg"] - theta) > 0.1  # a different surface
 
 
 @pytest.mark.parametrize("w", W.small_wall_params())
