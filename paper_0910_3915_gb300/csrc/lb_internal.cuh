@@ -53,9 +53,33 @@ struct Codec<float> {
     static __device__ __forceinline__ float round(float v) { return v; }
     static __device__ __forceinline__ void store(float* p, float v) { *p = v; }
 };
+// Stochastic rounding to a 16-bit format with `mant` explicit mantissa bits:
+// add a uniform dither of one unit in the last place, then round to nearest.
+// u01 in [0, 1); the result's expected value is v (no rounding bias).
+__device__ __forceinline__ float dither_ulp(float v, float u01, int mant)
+{
+    const int e = ((__float_as_int(v) >> 23) & 0xff);  // biased FP32 exponent of |v|
+    const int eu = e - mant > 1 ? e - mant : 1;        // exponent of one ulp (FP32 normal range)
+    return v + (u01 - 0.5f) * __int_as_float(eu << 23);
+}
+
+// Uniform in [0, 1) from three 32-bit keys: a multiply-xorshift hash (the
+// 32-bit finaliser of MurmurHash3) of a combined key.
+__device__ __forceinline__ float hash_u01(uint32_t node, uint32_t comp, uint32_t key)
+{
+    uint32_t h = node * 0x9E3779B1u ^ (key * 0x85EBCA77u + comp * 0xC2B2AE3Du);
+    h ^= h >> 16;
+    h *= 0x85EBCA6Bu;
+    h ^= h >> 13;
+    h *= 0xC2B2AE35u;
+    h ^= h >> 16;
+    return (float)(h >> 8) * (1.0f / 16777216.0f);
+}
+
 template <>
 struct Codec<__half> {
     static constexpr bool kDeviation = true;
+    static constexpr int kMant = 10;
     static __device__ __forceinline__ float load(const __half* p) { return __half2float(__ldg(p)); }
     static __device__ __forceinline__ float val(__half v) { return __half2float(v); }
     static __device__ __forceinline__ float round(float v) { return __half2float(__float2half_rn(v)); }
@@ -64,6 +88,7 @@ struct Codec<__half> {
 template <>
 struct Codec<__nv_bfloat16> {
     static constexpr bool kDeviation = true;
+    static constexpr int kMant = 7;
     static __device__ __forceinline__ float load(const __nv_bfloat16* p) { return __bfloat162float(__ldg(p)); }
     static __device__ __forceinline__ float val(__nv_bfloat16 v) { return __bfloat162float(v); }
     static __device__ __forceinline__ float round(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }

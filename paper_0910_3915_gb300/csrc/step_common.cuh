@@ -121,14 +121,18 @@ struct Dest {
 // rounding of the stored values do not bias the mass.
 // Loop order: velocity k outer, component inner, so each destination address
 // is formed once and both components' slots are reached by a uniform offset.
+// For 16-bit storage the rest value, which balances the node's mass, is
+// rounded stochastically: round-to-nearest of nearly equal bulk values would
+// bias the mass of every bulk node the same way, step after step. The dither
+// is a hash of the node, the component and the bits of the value itself, so
+// the rounding stays a pure function of the state (graph replays and the
+// adjoint's recompute reproduce it exactly).
 template <class S, bool kGeneral, bool kTauOne>
 __device__ __forceinline__ void collide_store(const float (&rc)[2], const float (&jc)[2][3], const float (&vc)[2][Q],
                                               const float (&F)[2][3], const float (&tau)[2], const float (&itau)[2],
                                               const float (&ref)[2], S* __restrict__ dst, const Layout& L, int x, int y,
                                               const Dest& D)
 {
-    (void)x;
-    (void)y;
     // common velocity u' = sum_a j^a/tau^a / sum_a rho^a/tau^a
     const float den = rc[0] * itau[0] + rc[1] * itau[1];
     const float iden = den > 0.f ? __frcp_rn(den) : 0.f;
@@ -193,8 +197,12 @@ __device__ __forceinline__ void collide_store(const float (&rc)[2], const float 
 #pragma unroll
     for (int a = 0; a < 2; ++a) {
         float s0;
-        if constexpr (Codec<S>::kDeviation) s0 = 3.0f * (base[a] - (sax[a] * (1.0f / 18.0f) + sdi[a] * (1.0f / 36.0f)));
-        else s0 = rc[a] - sum[a];
+        if constexpr (Codec<S>::kDeviation) {
+            s0 = 3.0f * (base[a] - (sax[a] * (1.0f / 18.0f) + sdi[a] * (1.0f / 36.0f)));
+            s0 = dither_ulp(s0, hash_u01((uint32_t)self, (uint32_t)a, __float_as_uint(s0)), Codec<S>::kMant);
+        } else {
+            s0 = rc[a] - sum[a];
+        }
         Codec<S>::store(q0 + (long long)a * Q * slot, s0);
     }
 }
