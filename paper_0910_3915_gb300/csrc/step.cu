@@ -99,15 +99,16 @@ __device__ __forceinline__ void step_item(const StepArgs<S>& A, int col, int za,
         }
     };
     // reduce the raw registers of plane zp: psi into its ring slot, own moments out
-    auto reduce = [&](int zp, float (&rho)[2], float (&j)[2][3], float (&v)[2][Q]) {
+    auto reduce = [&](int zp, float (&rho)[2], float (&j)[2][3], float (&v)[2][Q], float (&m)[2]) {
         float* spl = &sp[zp & 3][0][0][0];
 #pragma unroll
         for (int a = 0; a < 2; ++a) {
             float ps = eta[a];
             rho[a] = 0.f;
+            m[a] = 0.f;
             j[a][0] = j[a][1] = j[a][2] = 0.f;
             if (!so_) {
-                rho[a] = rho_of<S>(ro_[a], ref[a]);
+                rho[a] = rho_of<S>(ro_[a], ref[a], &m[a]);
                 mom_of<S>(ro_[a], j[a]);
                 ps = psi_of(rho[a]);
                 if constexpr (!kTauOne) {
@@ -125,20 +126,20 @@ __device__ __forceinline__ void step_item(const StepArgs<S>& A, int col, int za,
         }
     };
 
-    float rc[2], jc[2][3], vc[2][Q];
-    float rn[2], jn[2][3], vn[2][Q];
+    float rc[2], jc[2][3], vc[2][Q], mc[2];
+    float rn[2], jn[2][3], vn[2][Q], mn[2];
     __syncthreads();  // the previous item's readers are done with the ring
     issue(za - 1);
-    reduce(za - 1, rn, jn, vn);
+    reduce(za - 1, rn, jn, vn, mn);
     issue(za);
-    reduce(za, rc, jc, vc);
+    reduce(za, rc, jc, vc, mc);
     issue(za + 1);
 
     Dest D;
     D.set_column(L, valid ? gx : 0, valid ? gy : 0);
 
     for (int z = za; z < zb; ++z) {
-        reduce(z + 1, rn, jn, vn);
+        reduce(z + 1, rn, jn, vn, mn);
         if (z + 2 <= zb) issue(z + 2);
         __syncthreads();
 
@@ -163,12 +164,13 @@ __device__ __forceinline__ void step_item(const StepArgs<S>& A, int col, int za,
             D.zo[1] = z * plane;
             D.bot = !kGeneral && z - 1 == 0;
             D.top = !kGeneral && z + 1 == nz - 1;
-            collide_store<S, kGeneral, kTauOne>(rc, jc, vc, F, tau, itau, ref, dst, L, gx, gy, D);
+            collide_store<S, kGeneral, kTauOne>(rc, jc, vc, F, tau, itau, ref, dst, L, gx, gy, D, mc);
         }
         // rotate: next plane becomes current
 #pragma unroll
         for (int a = 0; a < 2; ++a) {
             rc[a] = rn[a];
+            mc[a] = mn[a];
 #pragma unroll
             for (int d = 0; d < 3; ++d) jc[a][d] = jn[a][d];
             if constexpr (!kTauOne) {

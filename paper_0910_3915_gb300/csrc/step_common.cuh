@@ -12,8 +12,13 @@ namespace lbsc {
 // rho of one component from its 19 stored values v_k: FP32 stores n_k;
 // 16-bit formats store e_k with n_k = zeta_k (rho_ref + e_k). The same routine
 // serves a tile's own nodes and its ring, so both see bit-identical rho.
+//
+// For 16-bit storage, m36 = 36 (rho - rho_ref) = 12 e_0 + 2 sum_axis e_k + sum_diag e_k
+// is also returned: the values are 16-bit numbers, so these FP32 sums are exact
+// (their bits span far less than 24), and the collision balances the node's
+// mass in this exact form rather than through the rounded rho.
 template <class S>
-__device__ __forceinline__ float rho_of(const float (&v)[Q], float ref)
+__device__ __forceinline__ float rho_of(const float (&v)[Q], float ref, float* m36 = nullptr)
 {
     if constexpr (Codec<S>::kDeviation) {
         float ax = 0.f, di = 0.f;
@@ -21,7 +26,9 @@ __device__ __forceinline__ float rho_of(const float (&v)[Q], float ref)
         for (int k = 1; k <= 6; ++k) ax += v[k];
 #pragma unroll
         for (int k = 7; k < Q; ++k) di += v[k];
-        return ref + (v[0] * (1.0f / 3.0f) + (ax * (1.0f / 18.0f) + di * (1.0f / 36.0f)));
+        const float m = fmaf(12.0f, v[0], fmaf(2.0f, ax, di));
+        if (m36) *m36 = m;
+        return ref + m * (1.0f / 36.0f);
     } else {
         float s = 0.f;
 #pragma unroll
@@ -121,8 +128,8 @@ struct Dest {
 // rounding of the stored values do not bias the mass.
 // Loop order: velocity k outer, component inner, so each destination address
 // is formed once and both components' slots are reached by a uniform offset.
-// For 16-bit storage the rest value, which balances the node's mass, is
-// rounded stochastically: round-to-nearest of nearly equal bulk values would
+// For 16-bit storage the rest value, which balances the node's mass (taken
+// exactly from m36 and the stored moving values), is rounded stochastically: round-to-nearest of nearly equal bulk values would
 // bias the mass of every bulk node the same way, step after step. The dither
 // is a hash of the node, the component and the bits of the value itself, so
 // the rounding stays a pure function of the state (graph replays and the
@@ -131,7 +138,7 @@ template <class S, bool kGeneral, bool kTauOne>
 __device__ __forceinline__ void collide_store(const float (&rc)[2], const float (&jc)[2][3], const float (&vc)[2][Q],
                                               const float (&F)[2][3], const float (&tau)[2], const float (&itau)[2],
                                               const float (&ref)[2], S* __restrict__ dst, const Layout& L, int x, int y,
-                                              const Dest& D)
+                                              const Dest& D, const float (&m36)[2])
 {
     // common velocity u' = sum_a j^a/tau^a / sum_a rho^a/tau^a
     const float den = rc[0] * itau[0] + rc[1] * itau[1];
@@ -198,7 +205,8 @@ __device__ __forceinline__ void collide_store(const float (&rc)[2], const float 
     for (int a = 0; a < 2; ++a) {
         float s0;
         if constexpr (Codec<S>::kDeviation) {
-            s0 = 3.0f * (base[a] - (sax[a] * (1.0f / 18.0f) + sdi[a] * (1.0f / 36.0f)));
+            // 12 e_0* = m36 - 2 sum_axis e_k* - sum_diag e_k*, the right side exact in FP32
+            s0 = (m36[a] - fmaf(2.0f, sax[a], sdi[a])) * (1.0f / 12.0f);
             s0 = dither_ulp(s0, hash_u01((uint32_t)self, (uint32_t)a, __float_as_uint(s0)), Codec<S>::kMant);
         } else {
             s0 = rc[a] - sum[a];

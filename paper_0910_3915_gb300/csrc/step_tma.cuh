@@ -158,7 +158,7 @@ __global__ void __launch_bounds__(32 * TY) step_tma_kernel(const __grid_constant
 
         // wait for plane i of the item, reduce it to psi (tile + ring) and own
         // moments, then refill its stage with plane i + NS
-        auto consume = [&](int i, float (&rho)[2], float (&j)[2][3], float (&v)[2][Q]) -> bool {
+        auto consume = [&](int i, float (&rho)[2], float (&j)[2][3], float (&v)[2][Q], float (&m)[2]) -> bool {
             const int zp = za - 1 + i;
             const uint32_t gi = g + i;
             const bool ok = mbar_wait(&bar[gi % NS], (gi / NS) & 1u);
@@ -170,12 +170,13 @@ __global__ void __launch_bounds__(32 * TY) step_tma_kernel(const __grid_constant
                 for (int a = 0; a < 2; ++a) {
                     float ps = eta[a];
                     rho[a] = 0.f;
+                    m[a] = 0.f;
                     j[a][0] = j[a][1] = j[a][2] = 0.f;
                     if (!solid) {
                         float w[Q];
 #pragma unroll
                         for (int k = 0; k < Q; ++k) w[k] = Codec<S>::val(st[((a * Q + k) * HY + ty + 1) * BX + tx + GX]);
-                        rho[a] = rho_of<S>(w, ref[a]);
+                        rho[a] = rho_of<S>(w, ref[a], &m[a]);
                         mom_of<S>(w, j[a]);
                         ps = psi_of(rho[a]);
                         if constexpr (!kTauOne) {
@@ -211,19 +212,19 @@ __global__ void __launch_bounds__(32 * TY) step_tma_kernel(const __grid_constant
             return true;
         };
 
-        float rc[2], jc[2][3], vc[2][Q];
-        float rn[2], jn[2][3], vn[2][Q];
+        float rc[2], jc[2][3], vc[2][Q], mc[2];
+        float rn[2], jn[2][3], vn[2][Q], mn[2];
         __syncthreads();  // the previous item's collide is done with the psi ring
         if (tid == 0)
             for (int i = 0; i < NS && i < np; ++i) issue(za - 1 + i, g + i);
-        if (!consume(0, rn, jn, vn)) return;
-        if (!consume(1, rc, jc, vc)) return;
+        if (!consume(0, rn, jn, vn, mn)) return;
+        if (!consume(1, rc, jc, vc, mc)) return;
 
         Dest D;
         D.set_column(L, valid ? gx : 0, valid ? gy : 0);
 
         for (int z = za; z < zb; ++z) {
-            if (!consume(z - za + 2, rn, jn, vn)) return;
+            if (!consume(z - za + 2, rn, jn, vn, mn)) return;
             if (valid) {
                 float F[2][3];
                 sc_force<HX, HY>(sp + ((z - 1) & 3) * (2 * HY * HX), sp + (z & 3) * (2 * HY * HX),
@@ -233,11 +234,12 @@ __global__ void __launch_bounds__(32 * TY) step_tma_kernel(const __grid_constant
                 D.zo[2] = (int)((z + 1) * plane);
                 D.bot = z - 1 == 0;
                 D.top = z + 1 == nz - 1;
-                collide_store<S, false, kTauOne>(rc, jc, vc, F, tau, itau, ref, dst, L, gx, gy, D);
+                collide_store<S, false, kTauOne>(rc, jc, vc, F, tau, itau, ref, dst, L, gx, gy, D, mc);
             }
 #pragma unroll
             for (int a = 0; a < 2; ++a) {
                 rc[a] = rn[a];
+                mc[a] = mn[a];
 #pragma unroll
                 for (int d = 0; d < 3; ++d) jc[a][d] = jn[a][d];
                 if constexpr (!kTauOne) {
