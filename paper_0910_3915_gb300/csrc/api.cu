@@ -47,6 +47,7 @@ struct lb_ctx {
     CUtensorMap tmap[2][3];                  // per buffer, per tile height 4/8/16
     bool tmap_ok[2][3] = {{false, false, false}, {false, false, false}};
     int* dev_err = nullptr;                  // device status word of the step kernels
+    uint32_t* clock = nullptr;               // device step counter {steps mod 2^32, done-ticket}
     bool ghost_ok = true;                    // ghost images of the current buffer are current
     static constexpr int kGraphSteps = 32;
     std::string err;
@@ -275,6 +276,7 @@ static StepArgs<S> step_args(lb_ctx* c, int src)
     A.dst = (S*)c->f[1 - src];
     A.nbmask = c->nbmask;
     A.err = c->dev_err;
+    A.clock = c->clock;
     A.L = c->L;
     A.P = c->kp;
     A.tiles_x = (c->nx + 31) / 32;
@@ -422,6 +424,7 @@ static int init_common(lb_ctx** out, int nx, int ny, int nz, int precision, cons
     q += p.part;
     c->red = (double*)q;
     c->dev_err = (int*)(c->red + 48);
+    c->clock = (uint32_t*)(c->red + 50);
     const long long Nn = N;
     c->W.rho[0] = sf + 0 * Nn;
     c->W.rho[1] = sf + 1 * Nn;
@@ -434,6 +437,7 @@ static int init_common(lb_ctx** out, int nx, int ny, int nz, int precision, cons
 
     if (planar_default(c) != LB_OK) return bail(LB_ERR_CUDA, c->err);
     e = cudaMemsetAsync(c->dev_err, 0, sizeof(int), c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->clock, 0, 2 * sizeof(uint32_t), c->stream);
     if (e == cudaSuccess) e = tma_prepare(c);
     if (e != cudaSuccess) return bail(LB_ERR_CUDA, std::string("lb_init: ") + cudaGetErrorString(e));
     // 16-bit deviation references: mean initial density over fluid nodes
@@ -837,6 +841,7 @@ int lb_load(lb_ctx* c, const void* host, size_t bytes)
         return fail(c, LB_ERR_ARG, "lb_load: state does not match this context");
     if (bytes < sizeof(StateHeader) + pb) return fail(c, LB_ERR_ARG, "lb_load: truncated state");
     LB_CUDA(c, cudaMemcpyAsync(c->f[c->cur], (const char*)host + sizeof(h), pb, cudaMemcpyHostToDevice, c->stream));
+    LB_CUDA(c, launch_clock_set(c->clock, (uint32_t)h.steps, c->stream));
     LB_CUDA(c, cudaStreamSynchronize(c->stream));
     c->steps = h.steps;
     c->ghost_ok = false;
@@ -928,6 +933,7 @@ struct lb_batch {
     std::vector<lb_ctx*> box;
     char* mem = nullptr;
     void* dargs = nullptr;  // StepArgs<S>[2*nbox]: box i read from buffer parity p at 2*i + p
+    uint32_t* done = nullptr; // CTAs finished in the current step (the last one advances the boxes' counters)
     int4* ditems = nullptr; // (box, tile column, first plane, end plane)
     int nitems = 0;
     int tile_y = 8, seg_planes = 32, ctas_per_sm = 0, grid = 0;
@@ -985,7 +991,10 @@ static int batch_build_typed(lb_batch* b)
     if (b->ditems) cudaFree(b->ditems);
     b->dargs = nullptr;
     b->ditems = nullptr;
-    LB_BCUDA(b, cudaMalloc(&b->dargs, args.size() * sizeof(StepArgs<S>)));
+    const size_t abytes = align256(args.size() * sizeof(StepArgs<S>));
+    LB_BCUDA(b, cudaMalloc(&b->dargs, abytes + 256));
+    b->done = (uint32_t*)((char*)b->dargs + abytes);
+    LB_BCUDA(b, cudaMemset(b->done, 0, sizeof(uint32_t)));
     LB_BCUDA(b, cudaMalloc((void**)&b->ditems, items.size() * sizeof(int4)));
     LB_BCUDA(b, cudaMemcpy(b->dargs, args.data(), args.size() * sizeof(StepArgs<S>), cudaMemcpyHostToDevice));
     LB_BCUDA(b, cudaMemcpy(b->ditems, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice));
@@ -1010,13 +1019,13 @@ static cudaError_t batch_launch(lb_batch* b, int parity, cudaStream_t st)
     switch (b->prec) {
     case LB_F32:
         return launch_batch_step<float>((const StepArgs<float>*)b->dargs, b->ditems, b->nitems, parity, b->tile_y,
-                                        b->tau1, b->grid, st);
+                                        b->tau1, b->grid, b->nbox, b->done, st);
     case LB_F16:
         return launch_batch_step<__half>((const StepArgs<__half>*)b->dargs, b->ditems, b->nitems, parity, b->tile_y,
-                                         b->tau1, b->grid, st);
+                                         b->tau1, b->grid, b->nbox, b->done, st);
     default:
         return launch_batch_step<__nv_bfloat16>((const StepArgs<__nv_bfloat16>*)b->dargs, b->ditems, b->nitems, parity,
-                                                b->tile_y, b->tau1, b->grid, st);
+                                                b->tile_y, b->tau1, b->grid, b->nbox, b->done, st);
     }
 }
 
@@ -1279,8 +1288,11 @@ extern "C" int lb_step_backward(lb_ctx* c, int nsteps, int ckpt_every, int obser
         }
     };
 
-    // forward: a checkpoint at the start of every segment
+    // forward: a checkpoint at the start of every segment (with the step count,
+    // which keys the 16-bit rounding dither, so the recompute replays it)
+    std::vector<long long> ck_steps(nseg > 0 ? nseg : 1);
     for (int s = 0; s < nseg; ++s) {
+        ck_steps[s] = c->steps;
         LB_CUDA(c, cudaMemcpyAsync(ck + sb * (size_t)s, c->f[c->cur], sb, cudaMemcpyDeviceToDevice, st));
         const int len = nsteps - s * ckpt_every < ckpt_every ? nsteps - s * ckpt_every : ckpt_every;
         const int rc = lb_step(c, len);
@@ -1298,6 +1310,7 @@ extern "C" int lb_step_backward(lb_ctx* c, int nsteps, int ckpt_every, int obser
         const int t0 = s * ckpt_every;
         const int len = nsteps - t0 < ckpt_every ? nsteps - t0 : ckpt_every;
         LB_CUDA(c, cudaMemcpyAsync(store, ck + sb * (size_t)s, sb, cudaMemcpyDeviceToDevice, st));
+        LB_CUDA(c, launch_clock_set(c->clock, (uint32_t)ck_steps[s], st));
         for (int i = 0; i < len; ++i) LB_CUDA(c, step_into(store + sb * (size_t)i, store + sb * (size_t)(i + 1)));
         for (int i = len - 1; i >= 0; --i) {
             LB_CUDA(c, fwd(store + sb * (size_t)i));
@@ -1305,6 +1318,7 @@ extern "C" int lb_step_backward(lb_ctx* c, int nsteps, int ckpt_every, int obser
             std::swap(lam_next, lam_cur);
         }
     }
+    LB_CUDA(c, launch_clock_set(c->clock, (uint32_t)c->steps, st));
     double h[3] = {0, 0, 0};
     LB_CUDA(c, cudaMemcpyAsync(h, acc, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
     LB_CUDA(c, cudaMemcpyAsync(h + 2, sums + 2, sizeof(double), cudaMemcpyDeviceToHost, st));

@@ -324,6 +324,18 @@ static int grid_for(long long n, int threads, int cap)
     return (int)(b < 1 ? 1 : (b > cap ? cap : b));
 }
 
+__global__ void clock_set_kernel(uint32_t* clk, uint32_t v)
+{
+    clk[0] = v;
+    clk[1] = 0;
+}
+
+cudaError_t launch_clock_set(uint32_t* clk, uint32_t v, cudaStream_t st)
+{
+    clock_set_kernel<<<1, 1, 0, st>>>(clk, v);
+    return cudaGetLastError();
+}
+
 template <class S>
 cudaError_t launch_init(const FieldArgs& F, S* f, const double* rr, const double* rb, cudaStream_t st)
 {

@@ -61,11 +61,13 @@ long long tma_step(int op, int tile_y, int stages, bool tau_one, const CUtensorM
                    cudaStream_t stream);
 template <class S>
 cudaError_t launch_batch_step(const StepArgs<S>* args, const int4* items, int nitems, int parity, int tile_y,
-                              bool tau_one, int grid, cudaStream_t st);
+                              bool tau_one, int grid, int nbox, uint32_t* done, cudaStream_t st);
 template <class S>
 int batch_occupancy(int tile_y, bool tau_one);
 // bounded-wait self-test: a wait nothing satisfies, limit try_wait rounds
 cudaError_t launch_wait_probe(int* err, unsigned limit, cudaStream_t st);
+// set a lattice's device step counter to v (and its done-ticket to 0)
+cudaError_t launch_clock_set(uint32_t* clk, uint32_t v, cudaStream_t st);
 template <class S>
 cudaError_t launch_ghosts(const Layout& L, S* f, int z0, int z1, cudaStream_t st);
 template <class S>

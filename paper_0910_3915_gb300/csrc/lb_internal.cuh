@@ -48,50 +48,69 @@ struct Codec;
 template <>
 struct Codec<float> {
     static constexpr bool kDeviation = false;
+    static constexpr bool kDitherMoving = false;
     static __device__ __forceinline__ float load(const float* p) { return __ldg(p); }
     static __device__ __forceinline__ float val(float v) { return v; }
-    static __device__ __forceinline__ float round(float v) { return v; }
     static __device__ __forceinline__ void store(float* p, float v) { *p = v; }
 };
-// Stochastic rounding to a 16-bit format with `mant` explicit mantissa bits:
-// add a uniform dither of one unit in the last place, then round to nearest.
-// u01 in [0, 1); the result's expected value is v (no rounding bias).
-__device__ __forceinline__ float dither_ulp(float v, float u01, int mant)
+// Random bits for stochastic rounding. A 32-bit hash per node and step (the
+// 32-bit finaliser of MurmurHash3 applied to a combined key); value j of the
+// node takes the upper half of h * M_j with the odd multiplier
+// M_j = 0x9E3779B1 (2j + 1). Multiplication by an odd number permutes the
+// 32-bit integers, so each value's bits are uniform when h is. The rest
+// value balances the node's mass against the rounded moving values, so its
+// bits come from a second, independent hash (node index with bit 31 set):
+// bits shared with the moving values would correlate with the fraction being
+// rounded and bias the mass.
+__device__ __forceinline__ uint32_t node_hash(uint32_t node, uint32_t key)
 {
-    const int e = ((__float_as_int(v) >> 23) & 0xff);  // biased FP32 exponent of |v|
-    const int eu = e - mant > 1 ? e - mant : 1;        // exponent of one ulp (FP32 normal range)
-    return v + (u01 - 0.5f) * __int_as_float(eu << 23);
-}
-
-// Uniform in [0, 1) from three 32-bit keys: a multiply-xorshift hash (the
-// 32-bit finaliser of MurmurHash3) of a combined key.
-__device__ __forceinline__ float hash_u01(uint32_t node, uint32_t comp, uint32_t key)
-{
-    uint32_t h = node * 0x9E3779B1u ^ (key * 0x85EBCA77u + comp * 0xC2B2AE3Du);
+    uint32_t h = node * 0x9E3779B1u ^ key * 0x85EBCA77u;
     h ^= h >> 16;
     h *= 0x85EBCA6Bu;
     h ^= h >> 13;
     h *= 0xC2B2AE35u;
     h ^= h >> 16;
-    return (float)(h >> 8) * (1.0f / 16777216.0f);
+    return h;
+}
+__device__ __forceinline__ uint32_t rand16(uint32_t h, int j)
+{
+    return (h * (0x9E3779B1u * (2u * (uint32_t)j + 1u))) >> 16;
 }
 
 template <>
 struct Codec<__half> {
     static constexpr bool kDeviation = true;
-    static constexpr int kMant = 10;
+    static constexpr bool kDitherMoving = false;  // 11 significant bits: only the rest value is dithered
     static __device__ __forceinline__ float load(const __half* p) { return __half2float(__ldg(p)); }
     static __device__ __forceinline__ float val(__half v) { return __half2float(v); }
-    static __device__ __forceinline__ float round(float v) { return __half2float(__float2half_rn(v)); }
+    static __device__ __forceinline__ __half rn(float v) { return __float2half_rn(v); }
+    // stochastic rounding: add a uniform dither of one unit in the last place
+    // (r16 / 2^16 - 1/2 units, the unit taken from v's binade), round to nearest
+    static __device__ __forceinline__ __half sr(float v, uint32_t r16)
+    {
+        const int e = (__float_as_int(v) >> 23) & 0xff;
+        const int eu = e - 10 > 103 ? e - 10 : 103;  // FP16 subnormals: one unit is 2^-24
+        const float u = (float)r16 * (1.0f / 65536.0f) - 0.5f;
+        return __float2half_rn(fmaf(u, __int_as_float(eu << 23), v));
+    }
     static __device__ __forceinline__ void store(__half* p, float v) { *p = __float2half_rn(v); }
 };
 template <>
 struct Codec<__nv_bfloat16> {
     static constexpr bool kDeviation = true;
-    static constexpr int kMant = 7;
+    static constexpr bool kDitherMoving = true;  // 8 significant bits: every value is dithered
     static __device__ __forceinline__ float load(const __nv_bfloat16* p) { return __bfloat162float(__ldg(p)); }
     static __device__ __forceinline__ float val(__nv_bfloat16 v) { return __bfloat162float(v); }
-    static __device__ __forceinline__ float round(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
+    static __device__ __forceinline__ __nv_bfloat16 rn(float v) { return __float2bfloat16_rn(v); }
+    // stochastic rounding: BF16 is the upper half of the FP32 word, so adding
+    // 16 uniform bits to the lower half and truncating rounds the magnitude up
+    // with probability equal to the discarded fraction
+    static __device__ __forceinline__ __nv_bfloat16 sr(float v, uint32_t r16)
+    {
+        __nv_bfloat16_raw raw;
+        raw.x = (unsigned short)((__float_as_uint(v) + r16) >> 16);
+        return __nv_bfloat16(raw);
+    }
     static __device__ __forceinline__ void store(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
 };
 
@@ -166,6 +185,7 @@ struct StepArgs {
     S* __restrict__ dst;
     const uint32_t* __restrict__ nbmask;  // general geometry: bit k = (x + c_k solid), bit 31 = x solid
     int* err;                             // device status word (bounded waits that gave up)
+    uint32_t* clock;                      // [0] step counter of the lattice, [1] CTAs done this step
     Layout L;
     KParams P;
     int tiles_x, tiles_y;
@@ -176,6 +196,23 @@ struct StepArgs {
 constexpr uint32_t kSelfSolid = 1u << 31;
 
 __host__ __device__ __forceinline__ int wrapi(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
+
+// Device-side step counter (16-bit storage: it drives the rounding dither).
+// Every CTA reads it on entry; the last CTA to finish the step advances it, so
+// the count stays right under CUDA-graph replay without any host update.
+__device__ __forceinline__ uint32_t clock_read(const uint32_t* clk) { return *(const volatile uint32_t*)clk; }
+__device__ __forceinline__ void clock_tick(uint32_t* clk)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned t = atomicAdd(&clk[1], 1u);
+        if (t == gridDim.x - 1) {
+            atomicExch(&clk[1], 0u);
+            atomicAdd(&clk[0], 1u);
+        }
+    }
+}
 
 // elements in 16 bytes: the ring column a TMA box carries on each side of a tile
 template <class S>

@@ -20,7 +20,7 @@ namespace lbsc {
 // sp: the CTA's psi ring, [4][2][TY+2][34] floats.
 template <class S, int TY, bool kGeneral, bool kTauOne>
 __device__ __forceinline__ void step_item(const StepArgs<S>& A, int col, int za, int zb,
-                                          float (&sp)[4][2][TY + 2][34])
+                                          float (&sp)[4][2][TY + 2][34], uint32_t clk)
 {
     constexpr int TX = 32, NT = TX * TY, HX = TX + 2, HY = TY + 2;
     constexpr int RING = 2 * HX + 2 * TY;          // ring nodes around the tile
@@ -164,7 +164,7 @@ __device__ __forceinline__ void step_item(const StepArgs<S>& A, int col, int za,
             D.zo[1] = z * plane;
             D.bot = !kGeneral && z - 1 == 0;
             D.top = !kGeneral && z + 1 == nz - 1;
-            collide_store<S, kGeneral, kTauOne>(rc, jc, vc, F, tau, itau, ref, dst, L, gx, gy, D, mc);
+            collide_store<S, kGeneral, kTauOne>(rc, jc, vc, F, tau, itau, ref, dst, L, gx, gy, D, mc, clk);
         }
         // rotate: next plane becomes current
 #pragma unroll
@@ -187,13 +187,16 @@ __global__ void __launch_bounds__(32 * TY) step_kernel(const StepArgs<S> A)
     __shared__ float sp[4][2][TY + 2][34];  // psi of 4 planes, slot = z & 3
     const int ncol = A.tiles_x * A.tiles_y;
     const int nzf = A.zhi - A.zlo;
+    uint32_t clk = 0;
+    if constexpr (Codec<S>::kDeviation) clk = clock_read(A.clock);
     for (int item = blockIdx.x; item < ncol * A.nseg; item += gridDim.x) {
         const int col = item % ncol, seg = item / ncol;
         const int za = A.zlo + (int)((long long)seg * nzf / A.nseg);
         const int zb = A.zlo + (int)((long long)(seg + 1) * nzf / A.nseg);
         if (za >= zb) continue;
-        step_item<S, TY, kGeneral, kTauOne>(A, col, za, zb, sp);
+        step_item<S, TY, kGeneral, kTauOne>(A, col, za, zb, sp, clk);
     }
+    if constexpr (Codec<S>::kDeviation) clock_tick(A.clock);
 }
 
 // Batched step: a persistent grid walks a work list of (box, tile column,
@@ -201,13 +204,27 @@ __global__ void __launch_bounds__(32 * TY) step_kernel(const StepArgs<S> A)
 // parameters; args[2*box + parity] describes box `box` for this step.
 template <class S, int TY, bool kTauOne>
 __global__ void __launch_bounds__(32 * TY)
-    batch_step_kernel(const StepArgs<S>* __restrict__ args, const int4* __restrict__ items, int nitems, int parity)
+    batch_step_kernel(const StepArgs<S>* __restrict__ args, const int4* __restrict__ items, int nitems, int parity,
+                      int nbox, uint32_t* done)
 {
     __shared__ float sp[4][2][TY + 2][34];
     for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
         const int4 w = items[it];
         const StepArgs<S> A = args[2 * w.x + parity];
-        step_item<S, TY, false, kTauOne>(A, w.y, w.z, w.w, sp);
+        uint32_t clk = 0;
+        if constexpr (Codec<S>::kDeviation) clk = clock_read(A.clock);
+        step_item<S, TY, false, kTauOne>(A, w.y, w.z, w.w, sp, clk);
+    }
+    if constexpr (Codec<S>::kDeviation) {
+        // the last CTA out advances every box's step counter
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            if (atomicAdd(done, 1u) == gridDim.x - 1) {
+                atomicExch(done, 0u);
+                for (int b = 0; b < nbox; ++b) atomicAdd(args[2 * b].clock, 1u);
+            }
+        }
     }
 }
 
@@ -273,21 +290,21 @@ int step_occupancy(int precision, int tile_y, bool general, bool tau_one)
 
 template <class S, int TY>
 static cudaError_t batch_ty(const StepArgs<S>* args, const int4* items, int nitems, int parity, bool tau_one,
-                            int grid, cudaStream_t st)
+                            int grid, int nbox, uint32_t* done, cudaStream_t st)
 {
-    if (tau_one) batch_step_kernel<S, TY, true><<<grid, 32 * TY, 0, st>>>(args, items, nitems, parity);
-    else batch_step_kernel<S, TY, false><<<grid, 32 * TY, 0, st>>>(args, items, nitems, parity);
+    if (tau_one) batch_step_kernel<S, TY, true><<<grid, 32 * TY, 0, st>>>(args, items, nitems, parity, nbox, done);
+    else batch_step_kernel<S, TY, false><<<grid, 32 * TY, 0, st>>>(args, items, nitems, parity, nbox, done);
     return cudaGetLastError();
 }
 
 template <class S>
 cudaError_t launch_batch_step(const StepArgs<S>* args, const int4* items, int nitems, int parity, int tile_y,
-                              bool tau_one, int grid, cudaStream_t st)
+                              bool tau_one, int grid, int nbox, uint32_t* done, cudaStream_t st)
 {
     switch (tile_y) {
-    case 4: return batch_ty<S, 4>(args, items, nitems, parity, tau_one, grid, st);
-    case 8: return batch_ty<S, 8>(args, items, nitems, parity, tau_one, grid, st);
-    case 16: return batch_ty<S, 16>(args, items, nitems, parity, tau_one, grid, st);
+    case 4: return batch_ty<S, 4>(args, items, nitems, parity, tau_one, grid, nbox, done, st);
+    case 8: return batch_ty<S, 8>(args, items, nitems, parity, tau_one, grid, nbox, done, st);
+    case 16: return batch_ty<S, 16>(args, items, nitems, parity, tau_one, grid, nbox, done, st);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -315,7 +332,8 @@ int batch_occupancy(int tile_y, bool tau_one)
 }
 
 #define LBSC_BATCH_INST(S)                                                                                     \
-    template cudaError_t launch_batch_step<S>(const StepArgs<S>*, const int4*, int, int, int, bool, int, cudaStream_t); \
+    template cudaError_t launch_batch_step<S>(const StepArgs<S>*, const int4*, int, int, int, bool, int, int, uint32_t*, \
+                                              cudaStream_t);                                                 \
     template int batch_occupancy<S>(int, bool);
 LBSC_BATCH_INST(float)
 LBSC_BATCH_INST(__half)

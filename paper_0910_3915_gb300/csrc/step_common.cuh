@@ -129,16 +129,17 @@ struct Dest {
 // Loop order: velocity k outer, component inner, so each destination address
 // is formed once and both components' slots are reached by a uniform offset.
 // For 16-bit storage the rest value, which balances the node's mass (taken
-// exactly from m36 and the stored moving values), is rounded stochastically: round-to-nearest of nearly equal bulk values would
-// bias the mass of every bulk node the same way, step after step. The dither
-// is a hash of the node, the component and the bits of the value itself, so
-// the rounding stays a pure function of the state (graph replays and the
-// adjoint's recompute reproduce it exactly).
+// exactly from m36 and the stored moving values), is rounded stochastically:
+// round-to-nearest of nearly equal bulk values would bias the mass of every
+// bulk node the same way, step after step. BF16 (8 significant bits) rounds
+// the moving values stochastically too. The random bits come from a hash of
+// the node and the lattice's step counter `clk`: fresh every step, and the
+// same again when a checkpoint is replayed.
 template <class S, bool kGeneral, bool kTauOne>
 __device__ __forceinline__ void collide_store(const float (&rc)[2], const float (&jc)[2][3], const float (&vc)[2][Q],
                                               const float (&F)[2][3], const float (&tau)[2], const float (&itau)[2],
                                               const float (&ref)[2], S* __restrict__ dst, const Layout& L, int x, int y,
-                                              const Dest& D, const float (&m36)[2])
+                                              const Dest& D, const float (&m36)[2], uint32_t clk = 0)
 {
     // common velocity u' = sum_a j^a/tau^a / sum_a rho^a/tau^a
     const float den = rc[0] * itau[0] + rc[1] * itau[1];
@@ -172,6 +173,8 @@ __device__ __forceinline__ void collide_store(const float (&rc)[2], const float 
     const long long slot = L.slot;
     const int self = D.zo[1] + D.ro[1] + D.xo[1];
     float sum[2] = {0.f, 0.f}, sax[2] = {0.f, 0.f}, sdi[2] = {0.f, 0.f};
+    uint32_t hsh = 0;
+    if constexpr (Codec<S>::kDitherMoving) hsh = node_hash((uint32_t)self, clk);
 #pragma unroll
     for (int k = 1; k < Q; ++k) {
         bool wall;
@@ -191,27 +194,34 @@ __device__ __forceinline__ void collide_store(const float (&rc)[2], const float 
             if constexpr (kTauOne) s = qk;
             else s = fmaf(qk - vc[a][k], itau[a], vc[a][k]);
             if constexpr (Codec<S>::kDeviation) {
-                const float sr = Codec<S>::round(s);
-                if (is_axis(k)) sax[a] += sr;
-                else sdi[a] += sr;
+                S h;
+                if constexpr (Codec<S>::kDitherMoving) h = Codec<S>::sr(s, rand16(hsh, a * Q + k));
+                else h = Codec<S>::rn(s);
+                if (is_axis(k)) sax[a] += Codec<S>::val(h);
+                else sdi[a] += Codec<S>::val(h);
+                q[so + (long long)a * Q * slot] = h;
             } else {
                 sum[a] += s;
+                Codec<S>::store(q + so + (long long)a * Q * slot, s);
             }
-            Codec<S>::store(q + so + (long long)a * Q * slot, s);
         }
     }
     S* q0 = dst + self;
+    uint32_t hrest = 0;
+    if constexpr (Codec<S>::kDeviation) hrest = node_hash((uint32_t)self | 0x80000000u, clk);
 #pragma unroll
     for (int a = 0; a < 2; ++a) {
-        float s0;
         if constexpr (Codec<S>::kDeviation) {
             // 12 e_0* = m36 - 2 sum_axis e_k* - sum_diag e_k*, the right side exact in FP32
-            s0 = (m36[a] - fmaf(2.0f, sax[a], sdi[a])) * (1.0f / 12.0f);
-            s0 = dither_ulp(s0, hash_u01((uint32_t)self, (uint32_t)a, __float_as_uint(s0)), Codec<S>::kMant);
+            // the residual step makes the quotient round as x/12 itself would;
+            // the rounded reciprocal alone scales every rest value by 1 + 3e-8
+            const float x0 = m36[a] - fmaf(2.0f, sax[a], sdi[a]);
+            float s0 = x0 * (1.0f / 12.0f);
+            s0 = fmaf(fmaf(-12.0f, s0, x0), 1.0f / 12.0f, s0);
+            q0[(long long)a * Q * slot] = Codec<S>::sr(s0, rand16(hrest, a));
         } else {
-            s0 = rc[a] - sum[a];
+            Codec<S>::store(q0 + (long long)a * Q * slot, rc[a] - sum[a]);
         }
-        Codec<S>::store(q0 + (long long)a * Q * slot, s0);
     }
 }
 

@@ -116,6 +116,9 @@ __global__ void __launch_bounds__(32 * TY) step_tma_kernel(const __grid_constant
     }
     __syncthreads();
     uint32_t g = 0;  // planes this CTA has issued and consumed so far
+    uint32_t clk = 0;
+    if constexpr (Codec<S>::kDeviation) clk = clock_read(A.clock);
+    bool failed = false;
 
     for (int item = blockIdx.x; item < ncol * A.nseg; item += gridDim.x) {
         const int col = item % ncol, seg = item / ncol;
@@ -217,14 +220,19 @@ __global__ void __launch_bounds__(32 * TY) step_tma_kernel(const __grid_constant
         __syncthreads();  // the previous item's collide is done with the psi ring
         if (tid == 0)
             for (int i = 0; i < NS && i < np; ++i) issue(za - 1 + i, g + i);
-        if (!consume(0, rn, jn, vn, mn)) return;
-        if (!consume(1, rc, jc, vc, mc)) return;
+        if (!consume(0, rn, jn, vn, mn) || !consume(1, rc, jc, vc, mc)) {
+            failed = true;
+            break;
+        }
 
         Dest D;
         D.set_column(L, valid ? gx : 0, valid ? gy : 0);
 
         for (int z = za; z < zb; ++z) {
-            if (!consume(z - za + 2, rn, jn, vn, mn)) return;
+            if (!consume(z - za + 2, rn, jn, vn, mn)) {
+                failed = true;
+                break;
+            }
             if (valid) {
                 float F[2][3];
                 sc_force<HX, HY>(sp + ((z - 1) & 3) * (2 * HY * HX), sp + (z & 3) * (2 * HY * HX),
@@ -234,7 +242,7 @@ __global__ void __launch_bounds__(32 * TY) step_tma_kernel(const __grid_constant
                 D.zo[2] = (int)((z + 1) * plane);
                 D.bot = z - 1 == 0;
                 D.top = z + 1 == nz - 1;
-                collide_store<S, false, kTauOne>(rc, jc, vc, F, tau, itau, ref, dst, L, gx, gy, D, mc);
+                collide_store<S, false, kTauOne>(rc, jc, vc, F, tau, itau, ref, dst, L, gx, gy, D, mc, clk);
             }
 #pragma unroll
             for (int a = 0; a < 2; ++a) {
@@ -248,8 +256,10 @@ __global__ void __launch_bounds__(32 * TY) step_tma_kernel(const __grid_constant
                 }
             }
         }
+        if (failed) break;
         g += np;
     }
+    if constexpr (Codec<S>::kDeviation) clock_tick(A.clock);
 }
 
 template <class S, int TY, int NS, bool T1>

@@ -30,7 +30,7 @@ def _boxes(n=6, edges=(24, 33, 40, 48), seed=3):
     return boxes, fields, params
 
 
-@pytest.mark.parametrize("precision", ["f32", "bf16"])
+@pytest.mark.parametrize("precision", ["f32", "f16", "bf16"])
 def test_batch_equals_individual_lattices_bitwise(lbsc, precision):
     boxes, fields, params = _boxes()
     batch = lbsc.Batch(fields, [lbsc.Params(**p) for p in params], precision)

@@ -162,11 +162,15 @@ def test_ldg_variant_parity(lbsc):
     assert rel_err(g, o, W.wall_mask(nx, ny, nz)) <= 1e-5
 
 
-def test_graph_replay_matches_eager(lbsc):
+@pytest.mark.parametrize("precision", ["f32", "f16", "bf16"])
+def test_graph_replay_matches_eager(lbsc, precision):
+    """Graph replays and single launches give the same states; for 16-bit
+    storage this also checks that the device step counter keying the rounding
+    dither advances once per step under replay."""
     nx, ny, nz = 32, 16, 12
     rr, rb = W.droplet_fields(nx, ny, nz, 5.0, seed=2)
-    a = lbsc.Lattice(rr, rb).set_params(**CONTACT)
-    b = lbsc.Lattice(rr, rb).set_params(**CONTACT)
+    a = lbsc.Lattice(rr, rb, precision).set_params(**CONTACT)
+    b = lbsc.Lattice(rr, rb, precision).set_params(**CONTACT)
     a.step(70)
     for _ in range(70):
         b.step(1)
@@ -175,10 +179,11 @@ def test_graph_replay_matches_eager(lbsc):
     assert ra[3][7] == 70 and rb_[3][7] == 70
 
 
-def test_save_load_resume_bitwise(lbsc):
+@pytest.mark.parametrize("precision", ["f32", "f16", "bf16"])
+def test_save_load_resume_bitwise(lbsc, precision):
     nx, ny, nz = 32, 32, 16
     rr, rb = W.droplet_fields(nx, ny, nz, 6.0, seed=3)
-    lat = lbsc.Lattice(rr, rb).set_params(**CONTACT, eta_wall_b=0.03, eta_wall_r=-0.03)
+    lat = lbsc.Lattice(rr, rb, precision).set_params(**CONTACT, eta_wall_b=0.03, eta_wall_r=-0.03)
     lat.step(100)
     state = lat.save()
     lat.step(100)
