@@ -58,9 +58,9 @@ struct Codec<float> {
 // node takes the upper half of h * M_j with the odd multiplier
 // M_j = 0x9E3779B1 (2j + 1). Multiplication by an odd number permutes the
 // 32-bit integers, so each value's bits are uniform when h is. The rest
-// value balances the node's mass against the rounded moving values, so its
-// bits come from a second, independent hash (node index with bit 31 set):
-// bits shared with the moving values would correlate with the fraction being
+// value balances the node's mass against the rounded moving values, so when
+// those are dithered too its bits come from a second mixing round of h: bits
+// shared with the moving values would correlate with the fraction being
 // rounded and bias the mass.
 __device__ __forceinline__ uint32_t node_hash(uint32_t node, uint32_t key)
 {

@@ -181,8 +181,15 @@ __device__ __forceinline__ void step_item(const StepArgs<S>& A, int col, int za,
     }
 }
 
+// Resident CTAs per SM the register budget is sized for (tau = 1 kernels, which
+// keep no pre-collision populations): the FP32 kernel with 8-row tiles fits 128
+// registers without spilling (two CTAs of 256 threads), 4-row tiles are held to
+// three CTAs of 128 threads (168 registers). Other variants: one CTA.
+template <class S, int TY, bool kTauOne>
+constexpr int kMinCtas = !kTauOne ? 1 : (TY == 4 ? 3 : ((sizeof(S) == 4 && TY == 8) ? 2 : 1));
+
 template <class S, int TY, bool kGeneral, bool kTauOne>
-__global__ void __launch_bounds__(32 * TY) step_kernel(const StepArgs<S> A)
+__global__ void __launch_bounds__(32 * TY, (kMinCtas<S, TY, kTauOne>)) step_kernel(const StepArgs<S> A)
 {
     __shared__ float sp[4][2][TY + 2][34];  // psi of 4 planes, slot = z & 3
     const int ncol = A.tiles_x * A.tiles_y;

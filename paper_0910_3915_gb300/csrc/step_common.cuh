@@ -208,7 +208,8 @@ __device__ __forceinline__ void collide_store(const float (&rc)[2], const float 
     }
     S* q0 = dst + self;
     uint32_t hrest = 0;
-    if constexpr (Codec<S>::kDeviation) hrest = node_hash((uint32_t)self | 0x80000000u, clk);
+    if constexpr (Codec<S>::kDitherMoving) hrest = node_hash(hsh, 0x632BE5ABu);  // a second full mixing round
+    else if constexpr (Codec<S>::kDeviation) hrest = node_hash((uint32_t)self, clk);
 #pragma unroll
     for (int a = 0; a < 2; ++a) {
         if constexpr (Codec<S>::kDeviation) {

@@ -270,6 +270,48 @@ def test_contact_angle_steady_state(lbsc, w):
     assert rel_err(gm, st.moments(), W.wall_mask(nx, ny, nz)) < 1e-3
 
 
+def _sr_mass_sigma(rho, ref, steps, mant):
+    """Standard deviation of the total mass after `steps` steps from the
+    stochastic rounding of the rest value alone (the moving values' rounding
+    is balanced exactly by it): per node and step the rounding error of
+    e_0 = rho - ref has standard deviation <= ulp/2 (mean ulp/sqrt(6)), and
+    enters the node's mass with weight zeta_0 = 1/3."""
+    e = np.abs(rho - ref)
+    e = np.where(e > 0, e, 2.0 ** -24)
+    ulp = 2.0 ** (np.floor(np.log2(e)) - mant)
+    ulp = np.maximum(ulp, 2.0 ** -24) if mant == 10 else ulp
+    return math.sqrt(steps * float(np.sum((ulp / 2 / 3) ** 2)))
+
+
+@pytest.mark.parametrize("precision", ["f16", "bf16"])
+def test_16bit_storage_contact_angle_within_one_degree(lbsc, precision):
+    """16-bit population storage (FP32 arithmetic): after 2000 steps the
+    contact angle stays within 1 deg of the FP64 oracle's, and the mass drift
+    is within 5 sigma of the unbiased stochastic-rounding noise (a rounding
+    bias, or a dither frozen in time, grows in proportion to the steps and
+    fails this)."""
+    nx = ny = nz = 32
+    rr, rb = W.droplet_fields(nx, ny, nz, 8.0, seed=0)
+    er, eb = W.wall_split(0.05)
+    prm = dict(CONTACT, eta_wall_r=er, eta_wall_b=eb)
+    lat = lbsc.Lattice(rr, rb, precision).set_params(**prm)
+    m0 = lat.conservation()[:2]
+    S = 2000
+    lat.step(S)
+    g = lat.contact_angle(3.0)
+    r, b, _, cons = lat.moments()
+    lat.close()
+    o = oracle.State(rr, rb, W.wall_mask(nx, ny, nz), oracle.Params(**prm)).step(S).contact_angle(3.0)
+    assert g["ok"] == 1 and o["ok"] == 1
+    assert abs(g["theta_deg"] - o["theta_deg"]) < 1.0, (g["theta_deg"], o["theta_deg"])
+    fl = W.wall_mask(nx, ny, nz) == 0
+    mant = 10 if precision == "f16" else 7
+    for a, rho in enumerate((r, b)):
+        ref = m0[a] / fl.sum()
+        sigma = _sr_mass_sigma(rho[fl], ref, S, mant)
+        assert abs(cons[a] - m0[a]) < 5 * sigma, (a, cons[a] - m0[a], sigma)
+
+
 # --------------------------------------------------------------- full size, sampled
 def _oracle_node_update(n_t, solid, prm, z, y, x):
     """The oracle's step on the 5x5x5 neighbourhood of (z, y, x) (clipped at solid
