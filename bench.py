@@ -60,7 +60,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--schedule", default=None,
-                    help="fixed step schedule variant:stages:tile_y:z_segments (e.g. ldg:0:4:16); skips tuning")
+                    help="fixed step schedule variant:stages:tile_y:z_segments[:y_tiles] (e.g. ldg:0:8:4:19); "
+                         "skips tuning")
     return ap.parse_args()
 
 
@@ -208,8 +209,7 @@ def run_ours(args):
     lat = lbsc.Lattice(rr, rb, prec).set_params(**prm)
     schedule = None
     if args.schedule:
-        v, ns, ty, seg = args.schedule.split(":")
-        schedule = (v, int(ns), int(ty), int(seg))
+        schedule = tune.parse(args.schedule)
         tune.apply(lat, schedule)
     elif not args.no_tune:
         schedule, _ = tune.tune(lat)
@@ -306,7 +306,8 @@ def run_ours(args):
         "config": {"workload": f"droplet {nx}x{ny}x{nz} R={wl['radius']:g} {prec.upper()}",
                    "lattice": [nx, ny, nz], "fluid_nodes": nf, "params": prm,
                    "schedule": ({"variant": schedule[0], "stages": schedule[1], "tile": f"32x{schedule[2]}",
-                                 "z_segments": schedule[3]} if schedule else "default"),
+                                 "z_segments": schedule[3],
+                                 "y_tiles": schedule[4] or -(-ny // schedule[2])} if schedule else "default"),
                    "l2": "inputs larger than L2 (state %.0f MB, L2 129 MB)" % (nx * ny * nz * bpl / 1e6),
                    "timed": f"{K} steps + FP64 conservation every {CONS_EVERY} + 1 contact angle"},
         "roofline": roof,

@@ -187,6 +187,13 @@ int lb_set_populations(lb_ctx* ctx, const double* n);
  * number of z segments per tile column (0 = automatic). */
 int lb_set_schedule(lb_ctx* ctx, int tile_y, int z_segments);
 
+/* The same, with the ny rows split evenly into y_tiles tiles of at most
+ * tile_y rows (0 = ceil(ny / tile_y)), so that the count of (tile column,
+ * z segment) work items can be matched to the GPU's resident CTAs.
+ * LB_ERR_ARG if a tile would need more than tile_y rows or y_tiles > ny.
+ * Like every schedule choice it changes no value of the result. */
+int lb_set_tiling(lb_ctx* ctx, int tile_y, int y_tiles, int z_segments);
+
 /* Choose the step kernel: LB_STEP_AUTO, LB_STEP_LDG or LB_STEP_TMA, and for
  * the TMA kernel the number of shared-memory stages (2 or 3; 0 = automatic).
  * Every variant computes bit-identical results. LB_STEP_TMA with a

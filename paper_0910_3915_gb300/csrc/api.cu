@@ -40,6 +40,7 @@ struct lb_ctx {
     lb_params prm{};
     KParams kp{};
     int tile_y = 4, nseg_req = 0;
+    int y_tiles_req = 0;  // y-tiles of the step kernel (0 = ceil(ny / tile_y))
     int nseg_cache = 0;  // segments per tile column for the current schedule (0 = not computed)
     long long steps = 0;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
@@ -162,6 +163,11 @@ static bool tau_one(const lb_ctx* c) { return c->prm.tau_r == 1.0 && c->prm.tau_
 static int tma_stages(lb_ctx* c);
 static long long tma_call(int op, lb_ctx* c, int ty, int ns);
 
+static int y_tiles(const lb_ctx* c)
+{
+    return c->y_tiles_req > 0 ? c->y_tiles_req : (c->ny + c->tile_y - 1) / c->tile_y;
+}
+
 static int nseg_for(lb_ctx* c, int ncol)
 {
     if (c->nseg_cache > 0) return c->nseg_cache;
@@ -280,7 +286,7 @@ static StepArgs<S> step_args(lb_ctx* c, int src)
     A.L = c->L;
     A.P = c->kp;
     A.tiles_x = (c->nx + 31) / 32;
-    A.tiles_y = (c->ny + c->tile_y - 1) / c->tile_y;
+    A.tiles_y = y_tiles(c);
     A.zlo = c->zlo;
     A.zhi = c->zhi;
     A.nseg = nseg_for(c, A.tiles_x * A.tiles_y);
@@ -570,15 +576,26 @@ int lb_set_step_variant(lb_ctx* c, int variant, int stages)
     return LB_OK;
 }
 
+int lb_set_tiling(lb_ctx* c, int tile_y, int y_tiles, int z_segments)
+{
+    if (!c) return fail(c, LB_ERR_ARG, "lb_set_tiling: NULL context");
+    if ((tile_y != 4 && tile_y != 8 && tile_y != 16) || z_segments < 0)
+        return fail(c, LB_ERR_ARG, "lb_set_tiling: tile_y must be 4, 8 or 16 and z_segments >= 0");
+    if (y_tiles < 0 || y_tiles > c->ny || (y_tiles > 0 && (c->ny + y_tiles - 1) / y_tiles > tile_y))
+        return fail(c, LB_ERR_ARG, "lb_set_tiling: y_tiles must be 0 or split ny into rows of at most tile_y");
+    if (y_tiles > 0 && (long long)((c->nx + 31) / 32) * y_tiles * (z_segments > 0 ? z_segments : 1) > (1LL << 30))
+        return fail(c, LB_ERR_ARG, "lb_set_tiling: too many tiles");
+    drop_graphs(c);
+    c->tile_y = tile_y;
+    c->y_tiles_req = y_tiles;
+    c->nseg_req = z_segments;
+    return LB_OK;
+}
+
 int lb_set_schedule(lb_ctx* c, int tile_y, int z_segments)
 {
     if (!c) return fail(c, LB_ERR_ARG, "lb_set_schedule: NULL context");
-    if ((tile_y != 4 && tile_y != 8 && tile_y != 16) || z_segments < 0)
-        return fail(c, LB_ERR_ARG, "lb_set_schedule: tile_y must be 4, 8 or 16 and z_segments >= 0");
-    drop_graphs(c);
-    c->tile_y = tile_y;
-    c->nseg_req = z_segments;
-    return LB_OK;
+    return lb_set_tiling(c, tile_y, 0, z_segments);
 }
 
 int lb_step(lb_ctx* c, int nsteps)
@@ -595,7 +612,7 @@ int lb_step(lb_ctx* c, int nsteps)
         int& par = c->cur;
         if (!c->graph[par]) {
             cudaGraph_t g = nullptr;
-            nseg_for(c, ((c->nx + 31) / 32) * ((c->ny + c->tile_y - 1) / c->tile_y));
+            nseg_for(c, ((c->nx + 31) / 32) * y_tiles(c));
             LB_CUDA(c, cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
             int p2 = par;
             cudaError_t e = launch_steps(c, G, p2, c->cap);

@@ -188,12 +188,15 @@ struct StepArgs {
     uint32_t* clock;                      // [0] step counter of the lattice, [1] CTAs done this step
     Layout L;
     KParams P;
-    int tiles_x, tiles_y;
+    int tiles_x, tiles_y;  // tile columns: 32-node rows in x; tiles_y even row splits of ny in y
     int zlo, zhi;  // fluid plane range [zlo, zhi)
     int nseg;      // z segments per tile column
 };
 
 constexpr uint32_t kSelfSolid = 1u << 31;
+
+// first row of y-tile t when n rows are split into nt tiles as evenly as possible
+__host__ __device__ __forceinline__ int tile_row(int t, int n, int nt) { return (int)((long long)t * n / nt); }
 
 __host__ __device__ __forceinline__ int wrapi(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
 

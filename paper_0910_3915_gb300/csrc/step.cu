@@ -40,11 +40,16 @@ __device__ __forceinline__ void step_item(const StepArgs<S>& A, int col, int za,
     const float gk = A.P.gk, Gax = A.P.Gax, Gdi = A.P.Gdi;
     const int tid = threadIdx.x, tx = tid % TX, ty = tid / TX;
 
-    const int x0 = (col % A.tiles_x) * TX, y0 = (col / A.tiles_x) * TY;
+    // tile rows [y0, y0 + hgt): the tiles_y tiles split the ny rows evenly
+    // (hgt <= TY); one warp per row, so a row past hgt is an idle warp
+    const int tyi = col / A.tiles_x;
+    const int x0 = (col - tyi * A.tiles_x) * TX;
+    const int y0 = tile_row(tyi, ny, A.tiles_y), hgt = tile_row(tyi + 1, ny, A.tiles_y) - y0;
     const int gx = x0 + tx, gy = y0 + ty;
-    const bool valid = gx < nx && gy < ny;
-    const int ox = gx % nx, oy = gy % ny;  // ragged tiles: wrapped copy of a real column
-    const int own = (oy + 1) * px + ox + L.gx;
+    const bool active = ty < hgt;
+    const bool valid = active && gx < nx;
+    const int ox = gx % nx;  // ragged x: a wrapped copy of a real column (the +x neighbour's psi)
+    const int own = (gy + 1) * px + ox + L.gx;
 
     // this thread's ring items: smem position, plane offset of the node, component
     int it_sm[NIT], it_a[NIT], it_off[NIT];
@@ -58,11 +63,11 @@ __device__ __forceinline__ void step_item(const StepArgs<S>& A, int col, int za,
             const int a = it >= RING, r = it - a * RING;
             int ix, iy;
             if (r < HX) { ix = r; iy = 0; }
-            else if (r < 2 * HX) { ix = r - HX; iy = HY - 1; }
+            else if (r < 2 * HX) { ix = r - HX; iy = hgt + 1; }
             else if (r < 2 * HX + TY) { ix = 0; iy = r - 2 * HX + 1; }
             else { ix = HX - 1; iy = r - 2 * HX - TY + 1; }
             const int hx = ((x0 - 1 + ix) % nx + nx) % nx, hy = ((y0 - 1 + iy) % ny + ny) % ny;
-            it_a[i] = a;
+            if (r < 2 * HX || iy <= hgt) it_a[i] = a;  // side columns: the tile's own rows only
             it_sm[i] = iy * HX + ix;
             it_off[i] = (hy + 1) * px + hx + L.gx;
         }
@@ -77,8 +82,10 @@ __device__ __forceinline__ void step_item(const StepArgs<S>& A, int col, int za,
     auto issue = [&](int zp) {
         const int zw = kGeneral ? wrapi(zp, nz) : zp;
         const int zoff = zw * plane;
-        if constexpr (kGeneral) so_ = (__ldg(nbmask + zoff + own) & kSelfSolid) != 0;
-        else so_ = (zp == 0 || zp == nz - 1);
+        const bool wall_plane = !kGeneral && (zp == 0 || zp == nz - 1);
+        if (!active) so_ = true;  // idle row: no loads, no psi
+        else if constexpr (kGeneral) so_ = (__ldg(nbmask + zoff + own) & kSelfSolid) != 0;
+        else so_ = wall_plane;
         if (!so_) {
             const S* p = src + (zoff + own);  // per-thread node pointer, uniform slot offsets
 #pragma unroll
@@ -90,7 +97,7 @@ __device__ __forceinline__ void step_item(const StepArgs<S>& A, int col, int za,
         for (int i = 0; i < NIT; ++i) {
             if (it_a[i] < 0) continue;
             if constexpr (kGeneral) si_[i] = (__ldg(nbmask + zoff + it_off[i]) & kSelfSolid) != 0;
-            else si_[i] = so_;
+            else si_[i] = wall_plane;
             if (!si_[i]) {
                 const S* p = src + (it_a[i] * Q * slot + zoff + it_off[i]);
 #pragma unroll
@@ -116,7 +123,7 @@ __device__ __forceinline__ void step_item(const StepArgs<S>& A, int col, int za,
                     for (int k = 0; k < Q; ++k) v[a][k] = ro_[a][k];
                 }
             }
-            spl[(a * HY + ty + 1) * HX + tx + 1] = ps;
+            if (active) spl[(a * HY + ty + 1) * HX + tx + 1] = ps;
         }
 #pragma unroll
         for (int i = 0; i < NIT; ++i) {

@@ -125,9 +125,13 @@ __global__ void __launch_bounds__(32 * TY) step_tma_kernel(const __grid_constant
         const int za = A.zlo + (int)((long long)seg * nzf / A.nseg);
         const int zb = A.zlo + (int)((long long)(seg + 1) * nzf / A.nseg);
         if (za >= zb) continue;
-        const int x0 = (col % A.tiles_x) * TX, y0 = (col / A.tiles_x) * TY;
+        // rows [y0, y0 + hgt) of an even split of ny (hgt <= TY); a row past hgt is an idle warp
+        const int tyi = col / A.tiles_x;
+        const int x0 = (col - tyi * A.tiles_x) * TX;
+        const int y0 = tile_row(tyi, ny, A.tiles_y), hgt = tile_row(tyi + 1, ny, A.tiles_y) - y0;
         const int gx = x0 + tx, gy = y0 + ty;
-        const bool valid = gx < nx && gy < ny;
+        const bool active = ty < hgt;
+        const bool valid = active && gx < nx;
         const int np = zb - za + 2;  // planes za-1 .. zb
 
         int it_sm[NIT], it_st[NIT], it_a[NIT];
@@ -139,10 +143,10 @@ __global__ void __launch_bounds__(32 * TY) step_tma_kernel(const __grid_constant
                 const int a = it >= RING, r = it - a * RING;
                 int ix, iy;
                 if (r < HX) { ix = r; iy = 0; }
-                else if (r < 2 * HX) { ix = r - HX; iy = HY - 1; }
+                else if (r < 2 * HX) { ix = r - HX; iy = hgt + 1; }
                 else if (r < 2 * HX + TY) { ix = 0; iy = r - 2 * HX + 1; }
                 else { ix = HX - 1; iy = r - 2 * HX - TY + 1; }
-                it_a[i] = a;
+                if (r < 2 * HX || iy <= hgt) it_a[i] = a;  // side columns: the tile's own rows only
                 it_sm[i] = iy * HX + ix;
                 it_st[i] = iy * BX + ix - 1 + GX;
             }
@@ -175,7 +179,7 @@ __global__ void __launch_bounds__(32 * TY) step_tma_kernel(const __grid_constant
                     rho[a] = 0.f;
                     m[a] = 0.f;
                     j[a][0] = j[a][1] = j[a][2] = 0.f;
-                    if (!solid) {
+                    if (!solid && active) {
                         float w[Q];
 #pragma unroll
                         for (int k = 0; k < Q; ++k) w[k] = Codec<S>::val(st[((a * Q + k) * HY + ty + 1) * BX + tx + GX]);
@@ -187,7 +191,7 @@ __global__ void __launch_bounds__(32 * TY) step_tma_kernel(const __grid_constant
                             for (int k = 0; k < Q; ++k) v[a][k] = w[k];
                         }
                     }
-                    spl[(a * HY + ty + 1) * HX + tx + 1] = ps;
+                    if (active) spl[(a * HY + ty + 1) * HX + tx + 1] = ps;
                 }
 #pragma unroll
                 for (int q = 0; q < NIT; ++q) {

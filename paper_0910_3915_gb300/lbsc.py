@@ -96,6 +96,7 @@ SIGNATURES = [
     ("lb_get_populations", _I, [_VP, _DP]),
     ("lb_set_populations", _I, [_VP, _DP]),
     ("lb_set_schedule", _I, [_VP, _I, _I]),
+    ("lb_set_tiling", _I, [_VP, _I, _I, _I]),
     ("lb_set_step_variant", _I, [_VP, _I, _I]),
     ("lb_step_backward", _I, [_VP, _I, _I, _I, _DP, _DP]),
     ("lb_observable", _I, [_VP, _I, _DP]),
@@ -225,6 +226,11 @@ class Lattice:
 
     def set_schedule(self, tile_y: int = 8, z_segments: int = 0) -> "Lattice":
         _check(load().lb_set_schedule(self._ctx, tile_y, z_segments), self._ctx)
+        return self
+
+    def set_tiling(self, tile_y: int = 8, y_tiles: int = 0, z_segments: int = 0) -> "Lattice":
+        """Tile height, number of y-tiles (even row split; 0 = ceil(ny / tile_y)) and z segments."""
+        _check(load().lb_set_tiling(self._ctx, tile_y, y_tiles, z_segments), self._ctx)
         return self
 
     def set_step_variant(self, variant: str = "auto", stages: int = 0) -> "Lattice":

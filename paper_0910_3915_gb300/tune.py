@@ -3,7 +3,9 @@
 The step kernel's work split is a kernel variant (planes staged into shared
 memory by TMA, or loaded from global memory by the compute threads), the
 number of TMA stages, a tile height (4, 8 or 16 rows of 32 nodes per CTA)
-and a number of z segments per tile column. None of them changes a single
+a number of z segments per tile column, and an even split of the rows into
+y-tiles (chosen so that the work items fill whole waves of resident CTAs on
+this GPU's SM count). None of them changes a single
 value of the result (the kernel is bitwise schedule-independent); they only
 change occupancy, halo overhead and wave balance. ``tune`` times candidate
 schedules on the lattice itself with CUDA events, restores the lattice state
@@ -18,26 +20,60 @@ import os
 SEGMENTS = (1, 2, 4, 8, 16)
 TMA_PAIRS = ((4, 2), (4, 3), (8, 2), (8, 3), (16, 2))  # (tile height, stages)
 LDG_TILES = (4, 8)
+LDG_CTAS_PER_SM = {4: 3, 8: 2}  # resident CTAs of the tau = 1 load-from-global kernel
 
 
-def candidates(nz_fluid: int, precision: str, segments=SEGMENTS):
+def even_splits(nx: int, ny: int, ty: int, ctas: int, segments=SEGMENTS, waves=(1, 2)):
+    """(y_tiles, z_segments) pairs whose work items fill `waves` whole waves of
+    `ctas` resident CTAs exactly, with the ny rows split evenly into tiles
+    whose largest has ty or ty - 1 rows."""
+    ntx = (nx + 31) // 32
+    out = []
+    for w in waves:
+        for seg in segments:
+            n = w * ctas
+            if n % (ntx * seg):
+                continue
+            nty = n // (ntx * seg)
+            if nty > ny or not ty - 1 <= -(-ny // nty) <= ty:
+                continue
+            out.append((nty, seg))
+    return out
+
+
+def candidates(nz_fluid: int, precision: str, segments=SEGMENTS, nx: int = 0, ny: int = 0, n_sm: int = 0):
+    """(variant, stages, tile_y, z_segments, y_tiles) schedules to time."""
     out = []
     for ty, ns in TMA_PAIRS:
         if ty == 16 and precision == "f32":
             continue  # two FP32 stages of 18 rows exceed shared memory
-        out += [("tma", ns, ty, s) for s in segments if nz_fluid // s >= 4]
+        out += [("tma", ns, ty, s, 0) for s in segments if nz_fluid // s >= 4]
     for ty in LDG_TILES:
-        out += [("ldg", 0, ty, s) for s in segments if nz_fluid // s >= 4]
+        out += [("ldg", 0, ty, s, 0) for s in segments if nz_fluid // s >= 4]
+        if n_sm and nx and ny:
+            out += [("ldg", 0, ty, s, nty) for nty, s in even_splits(nx, ny, ty, n_sm * LDG_CTAS_PER_SM[ty], segments)
+                    if nty != -(-ny // ty) and nz_fluid // s >= 4]
     return out
 
 
 def apply(lat, cand):
-    variant, stages, ty, seg = cand
-    lat.set_step_variant(variant, stages).set_schedule(ty, seg)
+    variant, stages, ty, seg = cand[:4]
+    nty = cand[4] if len(cand) > 4 else 0
+    lat.set_step_variant(variant, stages).set_tiling(ty, nty, seg)
+
+
+def parse(text: str):
+    """'variant:stages:tile_y:z_segments[:y_tiles]' -> candidate tuple."""
+    f = text.split(":")
+    return (f[0],) + tuple(int(x) for x in f[1:]) + ((0,) if len(f) == 4 else ())
+
+
+def name(cand) -> str:
+    return "%s:%d:%d:%d:%d" % tuple(cand)
 
 
 def tune(lat, steps: int = 64, segments=SEGMENTS, cache: str | None = None):
-    """Pick the fastest (variant, stages, tile_y, z_segments) for ``lat``; returns (best, table)."""
+    """Pick the fastest (variant, stages, tile_y, z_segments, y_tiles) for ``lat``; returns (best, table)."""
     import torch
 
     key = f"{lat.precision}:{lat.nx}x{lat.ny}x{lat.nz}:{torch.cuda.get_device_name()}"
@@ -51,7 +87,8 @@ def tune(lat, steps: int = 64, segments=SEGMENTS, cache: str | None = None):
     state = lat.save()
     stream = torch.cuda.current_stream()
     timings = {}
-    for cand in candidates(lat.nz - 2, lat.precision, segments):
+    n_sm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    for cand in candidates(lat.nz - 2, lat.precision, segments, lat.nx, lat.ny, n_sm):
         apply(lat, cand)
         lat.step(steps)  # warm-up, graph capture
         e0 = torch.cuda.Event(enable_timing=True)
@@ -61,11 +98,9 @@ def tune(lat, steps: int = 64, segments=SEGMENTS, cache: str | None = None):
         lat.step(steps)
         e1.record(stream)
         e1.synchronize()
-        timings["%s:%d:%d:%d" % cand] = e0.elapsed_time(e1) / steps
+        timings[name(cand)] = e0.elapsed_time(e1) / steps
     lat.load(state)
-    best_key = min(timings, key=timings.get)
-    v, ns, ty, seg = best_key.split(":")
-    best = (v, int(ns), int(ty), int(seg))
+    best = parse(min(timings, key=timings.get))
     apply(lat, best)
     if cache:
         table = {}

@@ -90,6 +90,17 @@ def test_general_geometry(lbsc, tau):
     prm = dict(CONTACT, tau_r=tau, tau_b=tau, eta_wall_r=-0.04, eta_wall_b=0.04)
     g, o = run_pair(lbsc, rr, rb, solid, 100, prm, walls_default=False)
     assert rel_err(g, o, solid) <= 1e-5
+    # uneven row splits of the mask-driven kernel change no value
+    ref = None
+    for nty, seg in ((0, 2), (3, 1), (7, 3), (20, 2)):
+        lat = lbsc.Lattice(rr, rb).set_geometry(solid).set_params(**prm).set_tiling(8, nty, seg)
+        lat.step(20)
+        out = lat.populations()
+        lat.close()
+        if ref is None:
+            ref = out
+        else:
+            assert np.array_equal(out, ref), (nty, seg)
 
 
 def test_fully_periodic_one_step_from_random_populations(lbsc):
@@ -133,12 +144,15 @@ def test_schedules_are_bitwise_identical(lbsc, precision):
     nx, ny, nz = 37, 23, 21
     rr, rb = W.droplet_fields(nx, ny, nz, 7.0, seed=1)
     ref = None
-    configs = [("ldg", 0, 8, 1), ("tma", 2, 4, 3), ("tma", 3, 8, 2), ("tma", 2, 8, 5), ("ldg", 0, 16, 2),
-               ("auto", 0, 4, 0), ("tma", 3, 4, 1)]
+    # (variant, stages, tile rows, y-tiles (0 = ceil(ny / rows)), z segments); ny = 23
+    configs = [("ldg", 0, 8, 0, 1), ("tma", 2, 4, 0, 3), ("tma", 3, 8, 0, 2), ("tma", 2, 8, 0, 5),
+               ("ldg", 0, 16, 0, 2), ("auto", 0, 4, 0, 0), ("tma", 3, 4, 0, 1),
+               ("ldg", 0, 8, 4, 2), ("ldg", 0, 8, 23, 1), ("ldg", 0, 4, 7, 3), ("tma", 2, 8, 5, 2),
+               ("tma", 2, 4, 23, 1), ("ldg", 0, 16, 3, 4)]
     if precision != "f32":
-        configs.append(("tma", 2, 16, 2))
-    for variant, stages, ty, seg in configs:
-        lat = lbsc.Lattice(rr, rb, precision).set_step_variant(variant, stages).set_schedule(ty, seg)
+        configs += [("tma", 2, 16, 0, 2), ("tma", 2, 16, 2, 3)]
+    for variant, stages, ty, nty, seg in configs:
+        lat = lbsc.Lattice(rr, rb, precision).set_step_variant(variant, stages).set_tiling(ty, nty, seg)
         lat.set_params(**CONTACT, eta_wall_b=0.05, eta_wall_r=-0.05)
         lat.step(20)
         out = lat.populations()
@@ -147,7 +161,7 @@ def test_schedules_are_bitwise_identical(lbsc, precision):
             ref = out
         else:
             fl = (W.wall_mask(nx, ny, nz) == 0)[None, None]
-            assert np.array_equal(np.where(fl, out, 0), np.where(fl, ref, 0)), (variant, stages, ty, seg)
+            assert np.array_equal(np.where(fl, out, 0), np.where(fl, ref, 0)), (variant, stages, ty, nty, seg)
 
 
 def test_ldg_variant_parity(lbsc):
