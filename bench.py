@@ -45,6 +45,12 @@ WORKLOADS = {
                    w=[round(-0.1 + 0.02 * i, 3) for i in range(11)]),
     # adjoint calibration: 64^3, R = 16, 2000 steps, checkpoints every 100
     "adjoint": dict(dims=(64, 64, 64), radius=16.0, precision="f32", steps=2000, ckpt=100),
+    # surface tensions (Sec. 4.1-4.2): 8x8x128 periodic lamellae (gamma_LG), 8x8x(64+2) slabs of each
+    # phase between the walls (gamma_SL, gamma_SG), a free droplet (radial gamma_LG) and sessile
+    # droplets (geometric, Huang and radial-Young angles), 11 wall values in [-0.1, 0.1]
+    "young": dict(lamella=(8, 8, 128), slab=(8, 8, 66), free=(64, 64, 64), free_radius=16.0,
+                  sessile=(96, 96, 96), sessile_radius=24.0, steps=10000, sessile_steps=8000,
+                  w=[round(-0.1 + 0.02 * i, 3) for i in range(11)]),
 }
 BYTES_PER_LU = {"f32": 304, "f16": 152, "bf16": 152}
 CONS_EVERY = 1000
@@ -555,10 +561,8 @@ def run_angles(args):
         hi = box.contact_angle(5.0, level=0.5 * float(phi[1:-1].max()))
         lo = box.contact_angle(5.0, level=0.5 * float(phi[1:-1].min()))
         r_in, r_out = bulk_densities(rr, rb)
-        # Huang: cos theta = (G_ads,r - G_ads,b) / (g (rho_in - rho_out) / 2) with G_ads = g eta, read so that
-        # a wall repelling r (w > 0) gives theta > 90: cos theta = -(2 w) / ((rho_in - rho_out) / 2)
-        c = -(2.0 * w) / ((r_in - r_out) / 2.0)
-        th_h = math.degrees(math.acos(max(-1.0, min(1.0, c))))
+        # Huang's closed form (Eq. huangSigmaLG) with the measured bulk densities
+        th_h = lbsc.huang_theta(W.wall_split(w)[0], W.wall_split(w)[1], r_in, r_out)
         rows.append({"w": w, "theta": round(a0["theta_deg"], 2) if a0["ok"] else None,
                      "theta_fit": round(a0["theta_fit_deg"], 2),
                      "theta_halfmax": [round(hi["theta_deg"], 2) if hi["ok"] else None,
@@ -571,6 +575,104 @@ def run_angles(args):
         "steps": T, "warmup": 64, "ms_per_step": round(ms / (T - 64), 5), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": wl["precision"], "data": "synthetic",
         "config": {"workload": f"theta vs wall parameter: {len(ws)} droplets {nx}^3 R={wl['radius']:g}, {T} steps, one batch"},
+        "angles": rows,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_young(args):
+    """Contact angles from surface tensions (Sec. 4.1-4.2): Young's equation with
+    planar tensions (Eq. gammaMechDef on lamellae and wall slabs), the radial
+    tension of a free droplet (Eq. mechRadGamma), and for sessile droplets
+    the geometric angle, Huang's closed form and Young's equation with the
+    drop's own radial gamma_LG."""
+    import numpy as np
+    import torch
+
+    from paper_0910_3915_gb300 import lbsc
+    from paper_0910_3915_gb300 import workloads as W
+
+    torch.cuda.set_device(0)
+    wl = WORKLOADS["young"]
+    T = args.steps if args.steps != 20000 else wl["steps"]
+    Ts = args.steps if args.steps != 20000 else wl["sessile_steps"]
+    ws = wl["w"]
+    stream = torch.cuda.current_stream()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    # gamma_LG: two periodic lamellae, two interfaces
+    lx, ly, lz = wl["lamella"]
+    rr, rb = W.lamella_fields(lx, ly, lz)
+    lam = lbsc.Lattice(rr, rb).set_geometry(W.periodic_mask(lx, ly, lz)).set_params(**CONTACT)
+    lam.step(T)
+    prof, gsum = lam.pressure_profile()
+    g_lg = 0.5 * gsum
+    lam.close()
+    # gamma_SL, gamma_SG: slabs of liquid (r-rich) and gas (b-rich) between the walls, one batch
+    sx, sy, sz = wl["slab"]
+    fields, params = [], []
+    for w in ws:
+        er, eb = W.wall_split(w)
+        for phase in ("liquid", "gas"):
+            fields.append(W.slab_fields(sx, sy, sz, phase))
+            params.append(lbsc.Params(**CONTACT, eta_wall_r=er, eta_wall_b=eb))
+    batch = lbsc.Batch(fields, params, "f32")
+    batch.step(64)
+    torch.cuda.synchronize()
+    t0.record(stream)
+    batch.step(T - 64)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    slab_ms = t0.elapsed_time(t1)
+    tens = []
+    for i in range(len(ws)):
+        sl = 0.5 * batch.box(2 * i).pressure_profile()[1]
+        sg = 0.5 * batch.box(2 * i + 1).pressure_profile()[1]
+        tens.append((sl, sg))
+    batch.close()
+    # radial gamma_LG of a free droplet in a periodic box
+    n = wl["free"][0]
+    c = (n / 2, n / 2, n / 2)
+    rr, rb = W.droplet_fields(n, n, n, wl["free_radius"], seed=0, centre=c)
+    fr = lbsc.Lattice(rr, rb).set_geometry(W.periodic_mask(n, n, n)).set_params(**CONTACT)
+    fr.step(T)
+    _, g_rad_free, rs_free = fr.pressure_radial(c, 1.0, n // 2, 0.0, n / 2 - 5)
+    fr.close()
+    # sessile droplets: geometric angle, Huang, radial gamma_LG about the fitted centre
+    m = wl["sessile"][0]
+    fields = [W.droplet_fields(m, m, m, wl["sessile_radius"], seed=0) for _ in ws]
+    params = [lbsc.Params(**CONTACT, eta_wall_r=W.wall_split(w)[0], eta_wall_b=W.wall_split(w)[1]) for w in ws]
+    sb = lbsc.Batch(fields, params, "f32")
+    sb.step(Ts)
+    rows = []
+    for i, w in enumerate(ws):
+        box = sb.box(i)
+        a = box.contact_angle(5.0)
+        rr_, rb_, _, _ = box.moments()
+        r_in, r_out = bulk_densities(rr_, rb_)
+        g_rad = rs = None
+        if a["ok"] and a["n_points"] >= 4:
+            cen = (a["xc"], a["yc"], a["zc"])
+            _, g_rad, rs = box.pressure_radial(cen, 1.0, 2 * m, 5.5, m / 2 - 5)
+        sl, sg = tens[i]
+        row = {"w": w, "gamma_sl": sl, "gamma_sg": sg,
+               "theta_young_planar": round(lbsc.young_theta(sg, sl, g_lg), 2),
+               "theta_geometric": round(a["theta_deg"], 2) if a["ok"] else None,
+               "theta_huang": round(lbsc.huang_theta(W.wall_split(w)[0], W.wall_split(w)[1], r_in, r_out), 2),
+               "gamma_lg_radial": g_rad, "R_s": rs,
+               "theta_young_radial": (round(lbsc.young_theta(sg, sl, g_rad), 2)
+                                      if g_rad is not None and g_rad > 0 else None)}
+        rows.append(row)
+    sb.close()
+    nf = len(ws) * 2 * sx * sy * (sz - 2)
+    line = {
+        "metric": METRIC, "value": round(nf * (T - 64) / (slab_ms * 1e-3) / 1e6, 1), "unit": "MLUPS", "n_gpus": 1,
+        "steps": T, "warmup": 64, "ms_per_step": round(slab_ms / (T - 64), 5), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"planar and radial surface tensions: {2 * len(ws)} wall slabs {sx}x{sy}x{sz} as one "
+                               f"batch (timed), lamellae {lx}x{ly}x{lz}, free drop {n}^3, "
+                               f"{len(ws)} sessile drops {m}^3 R={wl['sessile_radius']:g} ({Ts} steps)"},
+        "gamma_lg_planar": g_lg, "gamma_lg_radial_free": g_rad_free, "R_s_free": rs_free,
         "angles": rows,
     }
     print(json.dumps(line), flush=True)
@@ -636,6 +738,8 @@ def main():
         run_adjoint(args)
     elif args.workload == "angles":
         run_angles(args)
+    elif args.workload == "young":
+        run_young(args)
     else:
         run_ours(args)
 

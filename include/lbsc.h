@@ -167,6 +167,56 @@ int lb_contact_angle(lb_ctx* ctx, double offset, lb_droplet* out);
  * maximum |phi|: level = +max(phi)/2 and level = min(phi)/2. */
 int lb_contact_angle_at(lb_ctx* ctx, double offset, double level, lb_droplet* out);
 
+/* ------------------------------------------------------------ pressure tensor and surface tension
+ * The pressure tensor of Sec. 4.1 at a fluid node x:
+ *   P_ij = sum_a sum_k (c_ki - u_i)(c_kj - u_j) n_k^a
+ *        + 1/4 sum_(a, abar) g kappa sum_k G_k [psi^a(x) psi^abar(x+c_k) + psi^abar(x) psi^a(x+c_k)] c_ki c_kj
+ * with u the velocity lb_moments reports, G_k and kappa the force's weights and
+ * scale, and psi of a solid neighbour the wall pseudo-density (as in the
+ * force). Solid nodes contribute nothing. Evaluated in FP64 from the stored
+ * populations. Components are ordered xx, yy, zz, xy, xz, yz. Each call
+ * allocates and frees its device scratch and synchronises the stream. */
+
+/* P: host, 6*nx*ny*nz doubles, P[c*N + idx] (zeros on solid nodes). */
+int lb_pressure_tensor(lb_ctx* ctx, double* P);
+
+/* Plane averages along z (Eq. gammaMechDef with the interface normal to z):
+ * prof (host, nz*8 doubles): prof[z*8 + v] = mean over the fluid nodes of
+ * plane z of P_xx, P_yy, P_zz, P_xy, P_xz, P_yz and phi = rho_r - rho_b,
+ * then the fluid count (zeros for a solid plane). gamma_sum (may be NULL):
+ * sum over planes with fluid of P_N - P_T, P_N = P_zz, P_T = (P_xx + P_yy)/2;
+ * a box with m identical interfaces holds m gamma. The per-plane sums are
+ * deterministic (one block per plane, fixed order). */
+int lb_pressure_profile(lb_ctx* ctx, double* prof, double* gamma_sum);
+
+/* Radial profile about centre[3] (x, y, z lattice coordinates; distances use
+ * the minimum image along x and y, and along z for a mask geometry) for
+ * Eq. mechRadGamma: fluid nodes with z >= zmin at r > 0 fall in bin
+ * floor(r/dr) (1 <= nbins <= 1024, dr > 0); bins (host, nbins*4 doubles) gets
+ * per bin the mean P_N = n.P.n (n the unit vector from the centre), the mean
+ * P_T = (tr P - P_N)/2, the mean phi and the count. R_s (may be NULL) is the
+ * radius where the bin-mean phi first changes sign going outward, by linear
+ * interpolation between bin centres r_b = (b + 1/2) dr (NaN if it never
+ * does); gamma (may be NULL) = sum over bins with r_b <= r_max of
+ * (r_b/R_s)^2 (P_N - P_T) dr (0 without R_s). Sums are accumulated in 64-bit
+ * fixed point (2^-30 units), so the result does not depend on thread order. */
+int lb_pressure_radial(lb_ctx* ctx, const double* centre, double dr, int nbins, double zmin, double r_max,
+                       double* bins, double* gamma, double* R_s);
+
+/* Young's equation (Eq. young): cos theta = (gamma_SG - gamma_SL)/gamma_LG,
+ * theta in degrees, clamped to 0 or 180 outside [-1, 1] (complete wetting or
+ * drying). LB_ERR_ARG for non-finite tensions or gamma_LG <= 0 (message via
+ * lb_last_error(NULL)). Host only. */
+int lb_young_theta(double gamma_sg, double gamma_sl, double gamma_lg, double* theta_deg);
+
+/* Huang's closed form (Eq. huangSigmaLG) for the r droplet, with the same
+ * coupling g for fluid-fluid and fluid-wall pairs (which cancels):
+ * cos theta = (G_ads,b - G_ads,r) / (g (rho_in - rho_out)/2), where
+ * G_ads,r = g eta_wall_b and G_ads,b = g eta_wall_r are the wall
+ * interactions each component feels, and rho_in > rho_out the r densities
+ * inside and outside the drop. Degrees, clamped as above. Host only. */
+int lb_huang_theta(double eta_wall_r, double eta_wall_b, double rho_in, double rho_out, double* theta_deg);
+
 /* Checkpoint: bytes of the state, and copies to / from a host buffer of that
  * size. The state is the population array plus the step counter; params and
  * geometry are not part of it. */

@@ -14,6 +14,7 @@ populations have shape (2, 19, nz, ny, nx).
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 import subprocess
 from dataclasses import dataclass
@@ -192,3 +193,99 @@ def contact_angle(rho_r: np.ndarray, rho_b: np.ndarray, solid: np.ndarray, offse
     lib().lbo_contact_angle_level(nx, ny, nz, _u8(s), _dp(rr), _dp(rb), float(offset), float(level),
                                   ctypes.byref(out))
     return {f: getattr(out, f) for f, _ in _Droplet._fields_}
+
+
+# ---------------------------------------------------------------- surface tension (Sec. 4.1-4.2)
+def pressure_profile(P: np.ndarray, solid: np.ndarray, rho_r: np.ndarray, rho_b: np.ndarray):
+    """Plane averages of the pressure tensor along z and the planar surface
+    tension integral of Eq. gammaMechDef (normal z, dz = 1).
+
+    P: (6, nz, ny, nx) with components xx, yy, zz, xy, xz, yz (``State.pressure_tensor``).
+    Returns (prof, gamma_sum): prof[z] = (mean P_xx, P_yy, P_zz, P_xy, P_xz, P_yz,
+    mean phi, fluid count) over the plane's fluid nodes (zeros for a solid plane),
+    and gamma_sum = sum over planes with fluid of P_N - P_T, P_N = P_zz,
+    P_T = (P_xx + P_yy)/2. A periodic box with two interfaces holds 2 gamma."""
+    nz = P.shape[1]
+    fl = solid == 0
+    phi = rho_r - rho_b
+    prof = np.zeros((nz, 8))
+    for z in range(nz):
+        m = fl[z]
+        n = int(m.sum())
+        if n == 0:
+            continue
+        for c in range(6):
+            prof[z, c] = P[c, z][m].sum() / n
+        prof[z, 6] = phi[z][m].sum() / n
+        prof[z, 7] = n
+    has = prof[:, 7] > 0
+    gamma_sum = float(np.sum(prof[has, 2] - 0.5 * (prof[has, 0] + prof[has, 1])))
+    return prof, gamma_sum
+
+
+def pressure_radial(P: np.ndarray, solid: np.ndarray, rho_r: np.ndarray, rho_b: np.ndarray, centre,
+                    dr: float, nbins: int, zmin: float, r_max: float, periodic_z: bool = False):
+    """Radial profile of the normal and transversal pressure about `centre`
+    (x, y, z) and the curved-interface surface tension of Eq. mechRadGamma.
+
+    For a fluid node at distance r (minimum image along x, y, and z when
+    periodic_z) with unit vector n = (x - centre)/r: P_N = n.P.n and
+    P_T = (tr P - P_N)/2. Nodes with z < zmin or r = 0 are skipped; node r
+    falls in bin floor(r/dr). Returns (bins, gamma, R_s): bins[b] = (mean P_N,
+    mean P_T, mean phi, count); R_s the radius where the bin-mean phi first
+    changes sign going outward (linear interpolation between bin centres
+    r_b = (b + 1/2) dr); gamma = sum over bins with r_b <= r_max of
+    (r_b/R_s)^2 (P_N - P_T) dr (0 and R_s = nan when phi never changes sign)."""
+    nz, ny, nx = rho_r.shape
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+
+    def sep(a, c, n, periodic):
+        d = a - c
+        if periodic:
+            d = d - n * np.round(d / n)
+        return d
+
+    dx = sep(x, centre[0], nx, True)
+    dy = sep(y, centre[1], ny, True)
+    dz = sep(z, centre[2], nz, periodic_z)
+    r = np.sqrt(dx * dx + dy * dy + dz * dz)
+    use = (solid == 0) & (z >= zmin) & (r > 0)
+    b = np.floor(r / dr).astype(np.int64)
+    use &= b < nbins
+    rs = np.where(r > 0, r, 1.0)
+    n = [dx / rs, dy / rs, dz / rs]
+    T = [[P[0], P[3], P[4]], [P[3], P[1], P[5]], [P[4], P[5], P[2]]]
+    pn = sum(n[i] * T[i][j] * n[j] for i in range(3) for j in range(3))
+    pt = 0.5 * (P[0] + P[1] + P[2] - pn)
+    phi = rho_r - rho_b
+    bins = np.zeros((nbins, 4))
+    for k in range(nbins):
+        m = use & (b == k)
+        cnt = int(m.sum())
+        if cnt:
+            bins[k] = (pn[m].sum() / cnt, pt[m].sum() / cnt, phi[m].sum() / cnt, cnt)
+    R_s = float("nan")
+    prev = None
+    for k in range(nbins):
+        if bins[k, 3] == 0:
+            continue
+        if prev is not None and (bins[prev, 2] > 0) != (bins[k, 2] > 0):
+            r0, r1 = (prev + 0.5) * dr, (k + 0.5) * dr
+            p0, p1 = bins[prev, 2], bins[k, 2]
+            R_s = r0 + (r1 - r0) * p0 / (p0 - p1)
+            break
+        prev = k
+    gamma = 0.0
+    if R_s == R_s:
+        for k in range(nbins):
+            rb = (k + 0.5) * dr
+            if bins[k, 3] and rb <= r_max:
+                gamma += (rb / R_s) ** 2 * (bins[k, 0] - bins[k, 1]) * dr
+    return bins, gamma, R_s
+
+
+def young_theta(gamma_sg: float, gamma_sl: float, gamma_lg: float) -> float:
+    """Young's equation (Eq. young): cos theta = (gamma_SG - gamma_SL)/gamma_LG,
+    in degrees; 0 or 180 when the ratio leaves [-1, 1] (complete wetting or drying)."""
+    c = (gamma_sg - gamma_sl) / gamma_lg
+    return math.degrees(math.acos(max(-1.0, min(1.0, c))))

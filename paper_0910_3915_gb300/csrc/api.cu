@@ -1375,3 +1375,142 @@ extern "C" int lb_observable(lb_ctx* c, int observable, double* J)
     LB_CUDA(c, cudaStreamSynchronize(c->stream));
     return LB_OK;
 }
+
+// ---------------------------------------------------------------- pressure tensor and surface tension
+template <class S>
+static cudaError_t pressure_field_of(lb_ctx* c, double* out)
+{
+    return launch_pressure_field<S>(field_args(c), (const S*)c->f[c->cur], c->W, out, c->stream);
+}
+template <class S>
+static cudaError_t pressure_planes_of(lb_ctx* c, double* out)
+{
+    return launch_pressure_planes<S>(field_args(c), (const S*)c->f[c->cur], c->W, out, c->stream);
+}
+
+extern "C" int lb_pressure_tensor(lb_ctx* c, double* P)
+{
+    if (!c || !P) return fail(c, LB_ERR_ARG, "lb_pressure_tensor: NULL argument");
+    const size_t N = (size_t)c->nx * c->ny * c->nz;
+    AdjScratch M;
+    double* d = nullptr;
+    LB_CUDA(c, M.alloc((void**)&d, 6 * N * sizeof(double)));
+    LB_CUDA(c, dispatch_fields(c, true));
+    switch (c->prec) {
+    case LB_F32: LB_CUDA(c, pressure_field_of<float>(c, d)); break;
+    case LB_F16: LB_CUDA(c, pressure_field_of<__half>(c, d)); break;
+    default: LB_CUDA(c, pressure_field_of<__nv_bfloat16>(c, d)); break;
+    }
+    LB_CUDA(c, cudaMemcpyAsync(P, d, 6 * N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    LB_CUDA(c, cudaStreamSynchronize(c->stream));
+    return LB_OK;
+}
+
+extern "C" int lb_pressure_profile(lb_ctx* c, double* prof, double* gamma_sum)
+{
+    if (!c || !prof) return fail(c, LB_ERR_ARG, "lb_pressure_profile: NULL argument");
+    const int nz = c->nz;
+    AdjScratch M;
+    double* d = nullptr;
+    LB_CUDA(c, M.alloc((void**)&d, (size_t)nz * 8 * sizeof(double)));
+    LB_CUDA(c, dispatch_fields(c, true));
+    switch (c->prec) {
+    case LB_F32: LB_CUDA(c, pressure_planes_of<float>(c, d)); break;
+    case LB_F16: LB_CUDA(c, pressure_planes_of<__half>(c, d)); break;
+    default: LB_CUDA(c, pressure_planes_of<__nv_bfloat16>(c, d)); break;
+    }
+    LB_CUDA(c, cudaMemcpyAsync(prof, d, (size_t)nz * 8 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    LB_CUDA(c, cudaStreamSynchronize(c->stream));
+    // sums -> plane means; Eq. gammaMechDef with P_N = P_zz, P_T = (P_xx + P_yy)/2, dz = 1
+    double g = 0.0;
+    for (int z = 0; z < nz; ++z) {
+        double* p = prof + (size_t)z * 8;
+        const double n = p[7];
+        if (n > 0) {
+            for (int v = 0; v < 7; ++v) p[v] /= n;
+            g += p[2] - 0.5 * (p[0] + p[1]);
+        }
+    }
+    if (gamma_sum) *gamma_sum = g;
+    return LB_OK;
+}
+
+extern "C" int lb_pressure_radial(lb_ctx* c, const double* centre, double dr, int nbins, double zmin, double r_max,
+                                  double* bins, double* gamma, double* R_s)
+{
+    if (!c || !centre || !bins || !(dr > 0) || nbins < 1 || nbins > kRadialBinsMax || !std::isfinite(zmin) ||
+        !std::isfinite(r_max) || !std::isfinite(centre[0]) || !std::isfinite(centre[1]) || !std::isfinite(centre[2]))
+        return fail(c, LB_ERR_ARG, "lb_pressure_radial: bad argument (dr > 0, 1 <= nbins <= 1024, finite centre)");
+    AdjScratch M;
+    unsigned long long* d = nullptr;
+    LB_CUDA(c, M.alloc((void**)&d, (size_t)nbins * 4 * sizeof(unsigned long long)));
+    LB_CUDA(c, dispatch_fields(c, true));
+    LB_CUDA(c, launch_pressure_radial(field_args(c), c->f[c->cur], c->prec, c->W, centre, dr, nbins, zmin, d,
+                                      c->stream));
+    std::vector<unsigned long long> h((size_t)nbins * 4);
+    LB_CUDA(c, cudaMemcpyAsync(h.data(), d, h.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream));
+    LB_CUDA(c, cudaStreamSynchronize(c->stream));
+    for (int b = 0; b < nbins; ++b) {
+        const double n = (double)h[(size_t)b * 4 + 3];
+        for (int v = 0; v < 3; ++v) {
+            const double sum = (double)(long long)h[(size_t)b * 4 + v] / kRadialFix;
+            bins[(size_t)b * 4 + v] = n > 0 ? sum / n : 0.0;
+        }
+        bins[(size_t)b * 4 + 3] = n;
+    }
+    // Eq. mechRadGamma: R_s where the bin-mean phi first changes sign going
+    // outward (linear between bin centres), then sum (r_b/R_s)^2 (P_N - P_T) dr
+    double rs = std::nan("");
+    int prev = -1;
+    for (int b = 0; b < nbins; ++b) {
+        if (bins[(size_t)b * 4 + 3] == 0) continue;
+        if (prev >= 0 && (bins[(size_t)prev * 4 + 2] > 0) != (bins[(size_t)b * 4 + 2] > 0)) {
+            const double r0 = (prev + 0.5) * dr, r1 = (b + 0.5) * dr;
+            const double p0 = bins[(size_t)prev * 4 + 2], p1 = bins[(size_t)b * 4 + 2];
+            rs = r0 + (r1 - r0) * p0 / (p0 - p1);
+            break;
+        }
+        prev = b;
+    }
+    double g = 0.0;
+    if (rs == rs)
+        for (int b = 0; b < nbins; ++b) {
+            const double rb = (b + 0.5) * dr;
+            if (bins[(size_t)b * 4 + 3] > 0 && rb <= r_max)
+                g += (rb / rs) * (rb / rs) * (bins[(size_t)b * 4 + 0] - bins[(size_t)b * 4 + 1]) * dr;
+        }
+    if (gamma) *gamma = g;
+    if (R_s) *R_s = rs;
+    return LB_OK;
+}
+
+// ---------------------------------------------------------------- closed forms of the contact angle
+static double clamp_acos_deg(double c)
+{
+    c = c > 1.0 ? 1.0 : (c < -1.0 ? -1.0 : c);
+    return std::acos(c) * 180.0 / 3.14159265358979323846;
+}
+
+extern "C" int lb_young_theta(double gamma_sg, double gamma_sl, double gamma_lg, double* theta_deg)
+{
+    if (!theta_deg || !std::isfinite(gamma_sg) || !std::isfinite(gamma_sl) || !std::isfinite(gamma_lg) ||
+        !(gamma_lg > 0)) {
+        lbsc_set_global_error("lb_young_theta: finite tensions and gamma_lg > 0 required");
+        return LB_ERR_ARG;
+    }
+    *theta_deg = clamp_acos_deg((gamma_sg - gamma_sl) / gamma_lg);
+    return LB_OK;
+}
+
+extern "C" int lb_huang_theta(double eta_wall_r, double eta_wall_b, double rho_in, double rho_out, double* theta_deg)
+{
+    if (!theta_deg || !std::isfinite(eta_wall_r) || !std::isfinite(eta_wall_b) || !std::isfinite(rho_in) ||
+        !std::isfinite(rho_out) || !(rho_in > rho_out)) {
+        lbsc_set_global_error("lb_huang_theta: finite arguments and rho_in > rho_out required");
+        return LB_ERR_ARG;
+    }
+    // G_ads of the r droplet's own component is g eta_wall_b (the wall as felt by r), that of the
+    // surrounding b component g eta_wall_r; g cancels against the denominator g (rho_in - rho_out)/2
+    *theta_deg = clamp_acos_deg((eta_wall_r - eta_wall_b) / (0.5 * (rho_in - rho_out)));
+    return LB_OK;
+}

@@ -245,6 +245,140 @@ __global__ void __launch_bounds__(kRedThreads) angle_kernel(FieldArgs F, Scratch
     block_reduce<kAngleVals>(acc, 1u, part);
 }
 
+// ---------------------------------------------------------------- pressure tensor
+// Pressure tensor of Sec. 4.1 at a node, in FP64 from the FP32 fields:
+//   P_ij = sum_a sum_k (c_ki - u_i)(c_kj - u_j) n_k^a
+//        + 1/4 sum over the two ordered component pairs (a, abar) of
+//          g kappa sum_k G_k [psi^a(x) psi^abar(x+c_k) + psi^abar(x) psi^a(x+c_k)] c_ki c_kj,
+// u the moments' velocity (j + F/2)/rho, psi of a solid neighbour the wall
+// pseudo-density (the force's reading of the wall). Both ordered pairs give the
+// same bracket, so the interaction is 1/2 g kappa sum_k G_k [..] c_ki c_kj.
+// Components xx, yy, zz, xy, xz, yz; zero on solid nodes.
+template <class S>
+__device__ bool node_pressure(const FieldArgs& F, const S* __restrict__ f, const Scratch& W, int x, int y, int z,
+                              double (&P)[6])
+{
+    const int nx = F.L.nx, ny = F.L.ny, nz = F.L.nz;
+    for (int c = 0; c < 6; ++c) P[c] = 0.0;
+    const long long off = F.L.off(x, y, z);
+    if (node_solid(F, x, y, z, off)) return false;
+    const long long i = (long long)x + (long long)nx * (y + (long long)ny * z);
+    const double u[3] = {W.u[0][i], W.u[1][i], W.u[2][i]};
+    for (int a = 0; a < 2; ++a)
+        for (int k = 0; k < Q; ++k) {
+            const double n = decode<S>(f + (long long)(a * Q + k) * F.L.slot + off, k, F.P.ref[a]);
+            const double d[3] = {cx(k) - u[0], cy(k) - u[1], cz(k) - u[2]};
+            P[0] += d[0] * d[0] * n;
+            P[1] += d[1] * d[1] * n;
+            P[2] += d[2] * d[2] * n;
+            P[3] += d[0] * d[1] * n;
+            P[4] += d[0] * d[2] * n;
+            P[5] += d[1] * d[2] * n;
+        }
+    const double pr = W.psi[0][i], pb = W.psi[1][i];
+    double I[6] = {0, 0, 0, 0, 0, 0};
+    for (int k = 1; k < Q; ++k) {
+        const long long ip = (long long)wrapi(x + cx(k), nx) + (long long)nx * (wrapi(y + cy(k), ny) + (long long)ny * wrapi(z + cz(k), nz));
+        const double G = is_axis(k) ? F.P.Gax : F.P.Gdi;
+        const double pair = G * (pr * (double)W.psi[1][ip] + pb * (double)W.psi[0][ip]);
+        const double c3[3] = {(double)cx(k), (double)cy(k), (double)cz(k)};
+        I[0] += pair * c3[0] * c3[0];
+        I[1] += pair * c3[1] * c3[1];
+        I[2] += pair * c3[2] * c3[2];
+        I[3] += pair * c3[0] * c3[1];
+        I[4] += pair * c3[0] * c3[2];
+        I[5] += pair * c3[1] * c3[2];
+    }
+    const double h = 0.5 * (double)F.P.gk;
+    for (int c = 0; c < 6; ++c) P[c] += h * I[c];
+    return true;
+}
+
+// every node: P[c*N + i] (FP64)
+template <class S>
+__global__ void pressure_field_kernel(FieldArgs F, const S* __restrict__ f, Scratch W, double* __restrict__ out)
+{
+    const int nx = F.L.nx, ny = F.L.ny, nz = F.L.nz;
+    const long long N = (long long)nx * ny * nz;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(i % nx), y = (int)((i / nx) % ny), z = (int)(i / ((long long)nx * ny));
+        double P[6];
+        node_pressure<S>(F, f, W, x, y, z, P);
+        for (int c = 0; c < 6; ++c) out[c * N + i] = P[c];
+    }
+}
+
+// one block per z plane: sums over the plane's fluid nodes of the six
+// components, phi = rho_r - rho_b and the count -> out[z*8 + v]
+template <class S>
+__global__ void __launch_bounds__(kRedThreads) pressure_plane_kernel(FieldArgs F, const S* __restrict__ f, Scratch W,
+                                                                     double* __restrict__ out)
+{
+    const int nx = F.L.nx, ny = F.L.ny, z = blockIdx.x;
+    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int c = threadIdx.x; c < nx * ny; c += blockDim.x) {
+        const int x = c % nx, y = c / nx;
+        double P[6];
+        if (!node_pressure<S>(F, f, W, x, y, z, P)) continue;
+        const long long i = (long long)c + (long long)nx * ny * z;
+        for (int v = 0; v < 6; ++v) acc[v] += P[v];
+        acc[6] += (double)W.rho[0][i] - (double)W.rho[1][i];
+        acc[7] += 1.0;
+    }
+    block_reduce<8>(acc, 0u, out);
+}
+
+// Radial bins about a centre: per fluid node with z >= zmin at distance
+// r > 0 (minimum image along x, y, and z for the mask-driven periodic
+// geometry), bin floor(r/dr) < nbins collects P_N = n.P.n,
+// P_T = (tr P - P_N)/2, phi and 1. Sums are kept in 64-bit fixed point
+// (units of 2^-30) so that the atomic accumulation is exact and the result
+// does not depend on the order the nodes are added in.
+__global__ void __launch_bounds__(kRedThreads) pressure_radial_kernel(FieldArgs F, const void* f, int prec, Scratch W,
+                                                                      double cxx, double cyy, double czz, double dr,
+                                                                      int nbins, double zmin,
+                                                                      unsigned long long* __restrict__ out)
+{
+    __shared__ unsigned long long sh[kRadialBinsMax * 4];
+    for (int b = threadIdx.x; b < nbins * 4; b += blockDim.x) sh[b] = 0ull;
+    __syncthreads();
+    const int nx = F.L.nx, ny = F.L.ny, nz = F.L.nz;
+    const long long N = (long long)nx * ny * nz;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(i % nx), y = (int)((i / nx) % ny), z = (int)(i / ((long long)nx * ny));
+        if (z < zmin) continue;
+        double d[3] = {x - cxx, y - cyy, z - czz};
+        d[0] -= nx * rint(d[0] / nx);
+        d[1] -= ny * rint(d[1] / ny);
+        if (F.general) d[2] -= nz * rint(d[2] / nz);
+        const double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+        if (!(r > 0)) continue;
+        const double bf = floor(r / dr);
+        if (bf >= nbins) continue;
+        double P[6];
+        bool fluid;
+        if (prec == 0) fluid = node_pressure<float>(F, (const float*)f, W, x, y, z, P);
+        else if (prec == 1) fluid = node_pressure<__half>(F, (const __half*)f, W, x, y, z, P);
+        else fluid = node_pressure<__nv_bfloat16>(F, (const __nv_bfloat16*)f, W, x, y, z, P);
+        if (!fluid) continue;
+        const double n[3] = {d[0] / r, d[1] / r, d[2] / r};
+        const double T[3][3] = {{P[0], P[3], P[4]}, {P[3], P[1], P[5]}, {P[4], P[5], P[2]}};
+        double pn = 0;
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) pn += n[a] * T[a][b] * n[b];
+        const double pt = 0.5 * (P[0] + P[1] + P[2] - pn);
+        const double phi = (double)W.rho[0][i] - (double)W.rho[1][i];
+        const int b = (int)bf;
+        atomicAdd(&sh[b * 4 + 0], (unsigned long long)__double2ll_rn(pn * kRadialFix));
+        atomicAdd(&sh[b * 4 + 1], (unsigned long long)__double2ll_rn(pt * kRadialFix));
+        atomicAdd(&sh[b * 4 + 2], (unsigned long long)__double2ll_rn(phi * kRadialFix));
+        atomicAdd(&sh[b * 4 + 3], 1ull);
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < nbins * 4; b += blockDim.x)
+        if (sh[b]) atomicAdd(&out[b], sh[b]);
+}
+
 // ---------------------------------------------------------------- ghost images
 // Refresh the ghost columns x = -1, nx and rows y = -1, ny (corners
 // included) of planes [z0, z1) from the real nodes they mirror.
@@ -385,13 +519,41 @@ cudaError_t launch_set_pop(const FieldArgs& F, S* f, const double* in, cudaStrea
     return cudaGetLastError();
 }
 
+template <class S>
+cudaError_t launch_pressure_field(const FieldArgs& F, const S* f, const Scratch& W, double* out, cudaStream_t st)
+{
+    const long long N = (long long)F.L.nx * F.L.ny * F.L.nz;
+    pressure_field_kernel<S><<<grid_for(N, 256, 65536), 256, 0, st>>>(F, f, W, out);
+    return cudaGetLastError();
+}
+
+template <class S>
+cudaError_t launch_pressure_planes(const FieldArgs& F, const S* f, const Scratch& W, double* out, cudaStream_t st)
+{
+    pressure_plane_kernel<S><<<F.L.nz, kRedThreads, 0, st>>>(F, f, W, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pressure_radial(const FieldArgs& F, const void* f, int prec, const Scratch& W, const double* centre,
+                                   double dr, int nbins, double zmin, unsigned long long* out, cudaStream_t st)
+{
+    if (nbins < 1 || nbins > kRadialBinsMax) return cudaErrorInvalidValue;
+    cudaError_t e = cudaMemsetAsync(out, 0, sizeof(unsigned long long) * 4 * nbins, st);
+    if (e != cudaSuccess) return e;
+    pressure_radial_kernel<<<kRedBlocks, kRedThreads, 0, st>>>(F, f, prec, W, centre[0], centre[1], centre[2], dr,
+                                                                nbins, zmin, out);
+    return cudaGetLastError();
+}
+
 #define LBSC_INST(S)                                                                                  \
     template cudaError_t launch_init<S>(const FieldArgs&, S*, const double*, const double*, cudaStream_t); \
     template cudaError_t launch_conservation<S>(const FieldArgs&, const S*, double*, double*, cudaStream_t); \
     template cudaError_t launch_fields<S>(const FieldArgs&, const S*, const Scratch&, bool, cudaStream_t); \
     template cudaError_t launch_get_pop<S>(const FieldArgs&, const S*, double*, cudaStream_t);       \
     template cudaError_t launch_set_pop<S>(const FieldArgs&, S*, const double*, cudaStream_t);   \
-    template cudaError_t launch_ghosts<S>(const Layout&, S*, int, int, cudaStream_t);
+    template cudaError_t launch_ghosts<S>(const Layout&, S*, int, int, cudaStream_t);                 \
+    template cudaError_t launch_pressure_field<S>(const FieldArgs&, const S*, const Scratch&, double*, cudaStream_t); \
+    template cudaError_t launch_pressure_planes<S>(const FieldArgs&, const S*, const Scratch&, double*, cudaStream_t);
 LBSC_INST(float)
 LBSC_INST(__half)
 LBSC_INST(__nv_bfloat16)

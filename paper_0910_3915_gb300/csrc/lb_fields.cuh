@@ -78,6 +78,16 @@ template <class S>
 cudaError_t launch_fields(const FieldArgs& F, const S* f, const Scratch& W, bool velocity, cudaStream_t st);
 cudaError_t launch_angle(const FieldArgs& F, const Scratch& W, double zref, double level, double* part, double* out,
                          cudaStream_t st);
+// pressure tensor of Sec. 4.1 (after launch_fields with velocity): every node,
+// per-plane sums, and fixed-point radial bins (see fields.cu)
+template <class S>
+cudaError_t launch_pressure_field(const FieldArgs& F, const S* f, const Scratch& W, double* out, cudaStream_t st);
+template <class S>
+cudaError_t launch_pressure_planes(const FieldArgs& F, const S* f, const Scratch& W, double* out, cudaStream_t st);
+constexpr int kRadialBinsMax = 1024;
+constexpr double kRadialFix = 1073741824.0;  // fixed-point unit of the radial sums: 2^-30
+cudaError_t launch_pressure_radial(const FieldArgs& F, const void* f, int prec, const Scratch& W, const double* centre,
+                                   double dr, int nbins, double zmin, unsigned long long* out, cudaStream_t st);
 template <class S>
 cudaError_t launch_get_pop(const FieldArgs& F, const S* f, double* out, cudaStream_t st);
 template <class S>

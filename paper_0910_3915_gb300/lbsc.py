@@ -97,6 +97,11 @@ SIGNATURES = [
     ("lb_set_populations", _I, [_VP, _DP]),
     ("lb_set_schedule", _I, [_VP, _I, _I]),
     ("lb_set_tiling", _I, [_VP, _I, _I, _I]),
+    ("lb_pressure_tensor", _I, [_VP, _DP]),
+    ("lb_pressure_profile", _I, [_VP, _DP, _DP]),
+    ("lb_pressure_radial", _I, [_VP, _DP, ctypes.c_double, _I, ctypes.c_double, ctypes.c_double, _DP, _DP, _DP]),
+    ("lb_young_theta", _I, [ctypes.c_double, ctypes.c_double, ctypes.c_double, _DP]),
+    ("lb_huang_theta", _I, [ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double, _DP]),
     ("lb_set_step_variant", _I, [_VP, _I, _I]),
     ("lb_step_backward", _I, [_VP, _I, _I, _I, _DP, _DP]),
     ("lb_observable", _I, [_VP, _I, _DP]),
@@ -113,6 +118,21 @@ SIGNATURES = [
     ("lb_last_error", ctypes.c_char_p, [_VP]),
     ("lb_free", None, [_VP]),
 ]
+
+
+def young_theta(gamma_sg: float, gamma_sl: float, gamma_lg: float) -> float:
+    """Young's equation in degrees (clamped at 0 / 180)."""
+    t = ctypes.c_double()
+    _check(load().lb_young_theta(float(gamma_sg), float(gamma_sl), float(gamma_lg), ctypes.byref(t)))
+    return t.value
+
+
+def huang_theta(eta_wall_r: float, eta_wall_b: float, rho_in: float, rho_out: float) -> float:
+    """Huang's closed-form contact angle of the r droplet in degrees."""
+    t = ctypes.c_double()
+    _check(load().lb_huang_theta(float(eta_wall_r), float(eta_wall_b), float(rho_in), float(rho_out),
+                                 ctypes.byref(t)))
+    return t.value
 
 
 def load(path: str = _LIB_PATH):
@@ -266,6 +286,30 @@ class Lattice:
         d = lb_droplet()
         _check(load().lb_contact_angle_at(self._ctx, float(offset), float(level), ctypes.byref(d)), self._ctx)
         return {f: getattr(d, f) for f, _ in lb_droplet._fields_}
+
+    def pressure_tensor(self) -> np.ndarray:
+        """P (6, nz, ny, nx): xx, yy, zz, xy, xz, yz of the pressure tensor (Sec. 4.1)."""
+        P = np.empty((6,) + self.shape)
+        _check(load().lb_pressure_tensor(self._ctx, _dp(P)), self._ctx)
+        return P
+
+    def pressure_profile(self):
+        """(prof (nz, 8), gamma_sum): plane means of P and phi, fluid counts, and
+        sum_z (P_N - P_T) (Eq. gammaMechDef, normal z)."""
+        prof = np.empty((self.shape[0], 8))
+        g = ctypes.c_double()
+        _check(load().lb_pressure_profile(self._ctx, _dp(prof), ctypes.byref(g)), self._ctx)
+        return prof, g.value
+
+    def pressure_radial(self, centre, dr: float = 1.0, nbins: int = 64, zmin: float = 0.0, r_max: float = 1e30):
+        """(bins (nbins, 4), gamma, R_s): radial means of P_N, P_T, phi and counts
+        about `centre` (x, y, z) and the surface tension of Eq. mechRadGamma."""
+        c = np.ascontiguousarray(centre, dtype=np.float64)
+        bins = np.empty((int(nbins), 4))
+        g, rs = ctypes.c_double(), ctypes.c_double()
+        _check(load().lb_pressure_radial(self._ctx, _dp(c), float(dr), int(nbins), float(zmin), float(r_max),
+                                         _dp(bins), ctypes.byref(g), ctypes.byref(rs)), self._ctx)
+        return bins, g.value, rs.value
 
     def populations(self) -> np.ndarray:
         n = np.empty((2, 19) + self.shape)

@@ -67,6 +67,14 @@ def lamella_fields(nx: int, ny: int, nz: int, seed: int = 0, noise: float = 0.0,
     return rr, rb
 
 
+def slab_fields(nx: int, ny: int, nz: int, phase: str, dens=(RHO_MAJOR, RHO_MINOR)):
+    """A box filled with one bulk phase: "liquid" (r-rich) or "gas" (b-rich),
+    for the fluid-wall surface tensions of the planar-interface measurement."""
+    hi, lo = dens
+    a, b = (hi, lo) if phase == "liquid" else (lo, hi)
+    return np.full((nz, ny, nx), float(a)), np.full((nz, ny, nx), float(b))
+
+
 def random_populations(nx: int, ny: int, nz: int, seed: int, lo: float = 0.01, hi: float = 0.06):
     """Arbitrary positive populations (2, 19, nz, ny, nx) for tests that start off-equilibrium."""
     rng = np.random.Generator(np.random.PCG64(seed))

@@ -106,3 +106,28 @@ def test_binding_fails_loudly_without_library(tmp_path):
             lbsc.load(str(tmp_path / "missing.so"))
     finally:
         lbsc._lib = saved
+
+
+def test_closed_form_angles_host(lib):
+    """Young's equation and Huang's closed form are host-only entry points."""
+    import math
+    from paper_0910_3915_gb300 import lbsc
+    import oracle
+    assert lbsc.young_theta(1.0, 1.0, 0.5) == 90.0
+    assert lbsc.young_theta(0.0, 1.0, 0.5) == 180.0 and lbsc.young_theta(1.0, 0.0, 0.5) == 0.0
+    rng = np.random.default_rng(3)
+    for _ in range(20):
+        sg, sl, lg = rng.uniform(-0.02, 0.02), rng.uniform(-0.02, 0.02), rng.uniform(0.01, 0.1)
+        assert math.isclose(lbsc.young_theta(sg, sl, lg), oracle.young_theta(sg, sl, lg), rel_tol=1e-14)
+    with pytest.raises(lbsc.LBError):
+        lbsc.young_theta(0.1, 0.0, 0.0)
+    with pytest.raises(lbsc.LBError):
+        lbsc.young_theta(float("nan"), 0.0, 0.1)
+    # Huang (Eq. huangSigmaLG): a neutral wall gives 90 deg; w > 0 (eta_r = -w, eta_b = +w) repels r
+    assert lbsc.huang_theta(0.0, 0.0, 0.7, 0.04) == 90.0
+    w = 0.05
+    c = -(2 * w) / ((0.7 - 0.04) / 2)
+    assert math.isclose(lbsc.huang_theta(-w, w, 0.7, 0.04), math.degrees(math.acos(c)), rel_tol=1e-14)
+    assert lbsc.huang_theta(-w, w, 0.7, 0.04) > 90.0 > lbsc.huang_theta(w, -w, 0.7, 0.04)
+    with pytest.raises(lbsc.LBError):
+        lbsc.huang_theta(0.0, 0.0, 0.04, 0.7)

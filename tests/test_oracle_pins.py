@@ -313,3 +313,96 @@ def test_cap_relation_worked_example():
         assert math.isclose((4 * h * h + b * b) / (8 * h), ex["r"], rel_tol=1e-12)
         th = math.degrees(math.atan2(b / 2, ex["r"] - h))
         assert math.isclose(th, ex["theta_deg"], abs_tol=1e-9)
+
+
+# ---------------------------------------------------------------- surface tension reductions
+def test_pressure_profile_on_analytic_planar_field():
+    """Eq. gammaMechDef on a synthetic tensor field whose P_N - P_T along z is a
+    Gaussian of known integral: the plane means drop in-plane variations of
+    zero mean, solid planes are skipped, and the integral is recovered."""
+    nx, ny, nz = 6, 5, 40
+    A, w, z0, p0 = 0.013, 1.7, 19.3, 0.31
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    s = A * np.exp(-((z - z0) ** 2) / (2 * w * w))
+    P = np.zeros((6, nz, ny, nx))
+    P[0] = p0 - s / 3 + 0.02 * np.cos(2 * np.pi * x / nx)
+    P[1] = p0 - s / 3 - 0.03 * np.sin(2 * np.pi * y / ny)
+    P[2] = p0 + 2 * s / 3
+    P[3] = 0.01 * np.cos(2 * np.pi * x / nx)
+    solid = W.wall_mask(nx, ny, nz)
+    P[:, solid == 1] = 5.0  # must not enter
+    phi = np.tanh((z - z0) / 2.0)
+    rr, rb = 0.37 + 0.33 * phi, 0.37 - 0.33 * phi
+    prof, gsum = oracle.pressure_profile(P, solid, rr, rb)
+    assert np.all(prof[[0, -1]] == 0)
+    assert np.allclose(prof[1:-1, 7], nx * ny)
+    assert np.allclose(prof[1:-1, 3], 0, atol=1e-15)
+    assert np.allclose(prof[1:-1, 6], 0.66 * np.tanh((np.arange(1, nz - 1) - z0) / 2.0), atol=1e-14)
+    assert math.isclose(gsum, A * w * math.sqrt(2 * math.pi), rel_tol=1e-6)
+
+
+def _spherical_field(n=40, R=10.0, centre=(20.3, 19.8, 20.1), A=0.01, w=1.5, p0=0.3):
+    z, y, x = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    d = [x - centre[0], y - centre[1], z - centre[2]]
+    r = np.sqrt(d[0] ** 2 + d[1] ** 2 + d[2] ** 2)
+    nv = [di / r for di in d]
+    s = A * np.exp(-((r - R) ** 2) / (2 * w * w))
+    P = np.zeros((6, n, n, n))
+    for c, (i, j) in enumerate(((0, 0), (1, 1), (2, 2), (0, 1), (0, 2), (1, 2))):
+        P[c] = s * nv[i] * nv[j] + (p0 - s / 3 if i == j else 0.0)
+    phi = np.tanh((R - r) / 2.0)
+    return P, 0.37 + 0.33 * phi, 0.37 - 0.33 * phi
+
+
+def test_pressure_radial_on_analytic_spherical_field():
+    """Eq. mechRadGamma on P = p0 I + s(r) (n n - I/3), for which P_N - P_T = s(r)
+    exactly: the binned normal/transversal split, the phi = 0 radius and the
+    (r/R_s)^2-weighted integral are recovered; the minimum image makes the
+    result independent of where the periodic box is cut."""
+    n, R, A, w = 40, 10.0, 0.01, 1.5
+    c = (20.3, 19.8, 20.1)
+    P, rr, rb = _spherical_field(n, R, c, A, w)
+    solid = W.periodic_mask(n, n, n)
+    bins, gamma, R_s = oracle.pressure_radial(P, solid, rr, rb, c, 1.0, 20, 0.0, 15.0, periodic_z=True)
+    assert abs(R_s - R) < 0.05
+    rq = np.linspace(0, 15.0, 30001)
+    exact = np.trapezoid((rq / R) ** 2 * A * np.exp(-((rq - R) ** 2) / (2 * w * w)), rq)
+    assert math.isclose(gamma, exact, rel_tol=0.01)
+    assert np.all(bins[:, 0] - bins[:, 1] >= 0)
+    # cut the periodic box elsewhere: roll the fields and the centre together
+    sh = (7, -5, 11)
+    P2 = np.roll(P, sh, axis=(3, 2, 1))
+    rr2, rb2 = (np.roll(a, sh, axis=(2, 1, 0)) for a in (rr, rb))
+    c2 = ((c[0] + sh[0]) % n, (c[1] + sh[1]) % n, (c[2] + sh[2]) % n)
+    bins2, gamma2, R2 = oracle.pressure_radial(P2, solid, rr2, rb2, c2, 1.0, 20, 0.0, 15.0, periodic_z=True)
+    assert np.allclose(bins2, bins, rtol=1e-12, atol=1e-15) and math.isclose(gamma2, gamma, rel_tol=1e-12)
+
+
+def _wall_gamma(phase, w, steps=3000, nz=34):
+    """gamma of a fluid-wall interface: a slab of one bulk phase between the two
+    walls (two identical interfaces), Eq. gammaMechDef."""
+    rr, rb = W.slab_fields(4, 4, nz, phase)
+    er, eb = W.wall_split(w)
+    st = oracle.State(rr, rb, W.wall_mask(4, 4, nz), Params(g_br=0.08, force_weights=1, force_scale=1.25,
+                                                              eta_wall_r=er, eta_wall_b=eb))
+    st.step(steps)
+    r, b, _, _ = st.moments()
+    _, gsum = oracle.pressure_profile(st.pressure_tensor(), st.solid, r, b)
+    return 0.5 * gsum
+
+
+def test_young_planar_wall_tensions_mirror_and_sign():
+    """Young's equation with planar tensions (Sec. 4.1): swapping the
+    components and the sign of the wall parameter maps liquid-wall onto
+    gas-wall exactly, a neutral wall gives gamma_SL = gamma_SG (theta = 90 deg),
+    and a wall parameter w > 0, which repels the r-rich liquid, gives theta > 90."""
+    w = 0.05
+    sl, sg = _wall_gamma("liquid", w), _wall_gamma("gas", w)
+    assert math.isclose(_wall_gamma("gas", -w), sl, rel_tol=1e-9, abs_tol=1e-13)
+    assert math.isclose(_wall_gamma("liquid", -w), sg, rel_tol=1e-9, abs_tol=1e-13)
+    s0l, s0g = _wall_gamma("liquid", 0.0), _wall_gamma("gas", 0.0)
+    assert math.isclose(s0l, s0g, rel_tol=1e-9, abs_tol=1e-13)
+    assert sl > sg
+    assert oracle.young_theta(sg, sl, 0.01) > 90.0
+    assert oracle.young_theta(1.0, 1.0, 0.5) == 90.0
+    assert oracle.young_theta(0.0, 1.0, 0.5) == 180.0 and oracle.young_theta(1.0, 0.0, 0.5) == 0.0
