@@ -71,13 +71,6 @@ def parse():
     return ap.parse_args()
 
 
-def dist_env():
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return ws, rank, local
-
-
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -169,7 +162,9 @@ def omp_threads():
 
 
 def run_reference(args):
-    ws, rank, _ = dist_env()
+    from paper_0910_3915_gb300 import replicas
+
+    ws, rank, _ = replicas.world()
     if rank != 0:
         return
     wl = WORKLOADS[args.workload]
@@ -196,7 +191,9 @@ def run_ours(args):
     from paper_0910_3915_gb300 import lbsc, tune
     from paper_0910_3915_gb300 import workloads as W
 
-    ws, rank, local = dist_env()
+    from paper_0910_3915_gb300 import replicas
+
+    ws, rank, local = replicas.world()
     torch.cuda.set_device(local)
     dist = None
     if ws > 1:
@@ -229,8 +226,7 @@ def run_ours(args):
         dev_id = os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0] or "0"
     sampler = ClockSampler(dev_id)
     time.sleep(0.3)
-    if dist:
-        dist.barrier()
+    replicas.barrier()
     torch.cuda.synchronize()
     ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
     t0, t1 = ev(), ev()
@@ -253,16 +249,13 @@ def run_ours(args):
     launches += 3
     t1.record(stream)
     torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
+    replicas.barrier()
     clocks = sampler.stop()
     ms = t0.elapsed_time(t1)
     step_ms = sum(a.elapsed_time(b) for a, b in chunks) / K
-    if dist:
-        tt = torch.tensor([ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
-    value = nf * K * ws / (ms * 1e-3) / 1e6
+    units, secs = replicas.whole_job(nf * K, ms * 1e-3, device="cuda")  # all ranks' updates, slowest rank
+    ms = secs * 1e3
+    value = units / secs / 1e6
     cons = lat.conservation()
     lat.close()
 
@@ -270,6 +263,7 @@ def run_ours(args):
     rr_p = torch.from_numpy(rr).pin_memory().numpy()
     rb_p = torch.from_numpy(rb).pin_memory().numpy()
     torch.cuda.synchronize()
+    replicas.barrier()
     te = time.perf_counter()
     lat2 = lbsc.Lattice(rr_p, rb_p, prec).set_params(**prm)
     if schedule:
@@ -286,7 +280,8 @@ def run_ours(args):
     lat2.close()
     h2d = 2 * rr.size * 8
     d2h = 2 * rr.size * 4 + (K // CONS_EVERY + 2) * 64
-    e2e = nf * K * ws / e2e_s / 1e6
+    e_units, e_secs = replicas.whole_job(nf * K, e2e_s, device="cuda")
+    e2e = e_units / e_secs / 1e6
 
     if rank != 0:
         if dist:
@@ -343,7 +338,9 @@ def run_sweep(args):
     from paper_0910_3915_gb300 import lbsc
     from paper_0910_3915_gb300 import workloads as W
 
-    ws, rank, local = dist_env()
+    from paper_0910_3915_gb300 import replicas
+
+    ws, rank, local = replicas.world()
     torch.cuda.set_device(local)
     wl = WORKLOADS["sweep"]
     boxes = W.sweep_boxes(wl["boxes"], seed=wl["seed"])
