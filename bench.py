@@ -80,15 +80,26 @@ def peaks():
         return 6800.0, "fallback"
 
 
+STEP_SOURCES = ("step.cu", "step_common.cuh", "lb_internal.cuh")
+
+
+def step_source_sha256() -> str:
+    """sha256 over the step kernel's sources (the files its code comes from)."""
+    h = hashlib.sha256()
+    for name in STEP_SOURCES:
+        with open(os.path.join(ROOT, "paper_0910_3915_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
 def step_kernel_traffic(workload: str):
     """Per-launch DRAM bytes of the step kernel from the committed ncu summary,
-    or None when the kernel source changed since it was taken."""
+    or None when the kernel's sources changed since it was taken."""
     path = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
     try:
         with open(path) as f:
             rec = json.load(f)
-        src = open(os.path.join(ROOT, "paper_0910_3915_gb300", "csrc", "step.cu"), "rb").read()
-        if rec.get("step_cu_sha256") != hashlib.sha256(src).hexdigest():
+        if rec.get("step_sources_sha256") != step_source_sha256():
             return None
         return rec.get("bytes_per_launch", {}).get(workload)
     except Exception:

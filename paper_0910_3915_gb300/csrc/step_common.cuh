@@ -20,41 +20,45 @@ namespace lbsc {
 template <class S>
 __device__ __forceinline__ float rho_of(const float (&v)[Q], float ref, float* m36 = nullptr)
 {
+    // opposite velocities come in pairs (k, k+1), k odd: sum each pair first
     if constexpr (Codec<S>::kDeviation) {
-        float ax = 0.f, di = 0.f;
-#pragma unroll
-        for (int k = 1; k <= 6; ++k) ax += v[k];
-#pragma unroll
-        for (int k = 7; k < Q; ++k) di += v[k];
+        const float ax = ((v[1] + v[2]) + (v[3] + v[4])) + (v[5] + v[6]);
+        const float di = (((v[7] + v[8]) + (v[9] + v[10])) + ((v[11] + v[12]) + (v[13] + v[14]))) +
+                         ((v[15] + v[16]) + (v[17] + v[18]));
         const float m = fmaf(12.0f, v[0], fmaf(2.0f, ax, di));
         if (m36) *m36 = m;
         return ref + m * (1.0f / 36.0f);
     } else {
-        float s = 0.f;
-#pragma unroll
-        for (int k = 0; k < Q; ++k) s += v[k];
-        return s;
+        const float ax = ((v[1] + v[2]) + (v[3] + v[4])) + (v[5] + v[6]);
+        const float di = (((v[7] + v[8]) + (v[9] + v[10])) + ((v[11] + v[12]) + (v[13] + v[14]))) +
+                         ((v[15] + v[16]) + (v[17] + v[18]));
+        return (v[0] + ax) + di;
     }
 }
 
-// j = sum_k n_k c_k
+// j = sum_k n_k c_k, from the differences of opposite pairs: d = n_k - n_kbar
+// (k odd), j = sum over pairs of c_k d
 template <class S>
 __device__ __forceinline__ void mom_of(const float (&v)[Q], float (&j)[3])
 {
+    float d[Q / 2 + 1];
+#pragma unroll
+    for (int k = 1; k < Q; k += 2) d[(k + 1) / 2] = v[k] - v[k + 1];
     float ax[3] = {0.f, 0.f, 0.f}, di[3] = {0.f, 0.f, 0.f};
 #pragma unroll
-    for (int k = 1; k < Q; ++k) {
+    for (int k = 1; k < Q; k += 2) {
+        const float dk = d[(k + 1) / 2];
         float* acc = is_axis(k) ? ax : di;
-        if (cx(k)) acc[0] += cx(k) * v[k];
-        if (cy(k)) acc[1] += cy(k) * v[k];
-        if (cz(k)) acc[2] += cz(k) * v[k];
+        if (cx(k)) acc[0] = cx(k) > 0 ? acc[0] + dk : acc[0] - dk;
+        if (cy(k)) acc[1] = cy(k) > 0 ? acc[1] + dk : acc[1] - dk;
+        if (cz(k)) acc[2] = cz(k) > 0 ? acc[2] + dk : acc[2] - dk;
     }
     if constexpr (Codec<S>::kDeviation) {
 #pragma unroll
-        for (int d = 0; d < 3; ++d) j[d] = ax[d] * (1.0f / 18.0f) + di[d] * (1.0f / 36.0f);
+        for (int q = 0; q < 3; ++q) j[q] = ax[q] * (1.0f / 18.0f) + di[q] * (1.0f / 36.0f);
     } else {
 #pragma unroll
-        for (int d = 0; d < 3; ++d) j[d] = ax[d] + di[d];
+        for (int q = 0; q < 3; ++q) j[q] = ax[q] + di[q];
     }
 }
 
@@ -71,15 +75,19 @@ __device__ __forceinline__ void sc_force(const float* s0, const float* s1, const
 #pragma unroll
     for (int a = 0; a < 2; ++a) {
         const int ab = 1 - a;
+        auto psi_at = [&](int k) {
+            const float* sl = cz(k) < 0 ? s0 : (cz(k) > 0 ? s2 : s1);
+            return sl[(ab * HY + ty + 1 + cy(k)) * HX + tx + 1 + cx(k)];
+        };
+        // opposite neighbours in pairs: psi(x + c_k) - psi(x - c_k), k odd
         float ax[3] = {0.f, 0.f, 0.f}, di[3] = {0.f, 0.f, 0.f};
 #pragma unroll
-        for (int k = 1; k < Q; ++k) {
-            const float* sl = cz(k) < 0 ? s0 : (cz(k) > 0 ? s2 : s1);
-            const float ps = sl[(ab * HY + ty + 1 + cy(k)) * HX + tx + 1 + cx(k)];
+        for (int k = 1; k < Q; k += 2) {
+            const float dk = psi_at(k) - psi_at(k + 1);
             float* acc = is_axis(k) ? ax : di;
-            if (cx(k)) acc[0] += cx(k) * ps;
-            if (cy(k)) acc[1] += cy(k) * ps;
-            if (cz(k)) acc[2] += cz(k) * ps;
+            if (cx(k)) acc[0] = cx(k) > 0 ? acc[0] + dk : acc[0] - dk;
+            if (cy(k)) acc[1] = cy(k) > 0 ? acc[1] + dk : acc[1] - dk;
+            if (cz(k)) acc[2] = cz(k) > 0 ? acc[2] + dk : acc[2] - dk;
         }
         const float pre = -gk * s1[(a * HY + ty + 1) * HX + tx + 1];
 #pragma unroll
