@@ -27,6 +27,14 @@ __device__ __forceinline__ long long didx(int x, int y, int z, int nx, int ny)
     return (long long)x + (long long)nx * (y + (long long)ny * z);
 }
 __device__ __forceinline__ bool wall_z(int z, int nz) { return z == 0 || z == nz - 1; }
+// coordinates of dense node index i (32-bit: node counts stay below 2^31)
+__device__ __forceinline__ void node_xyz(int i, int nx, int ny, int& x, int& y, int& z)
+{
+    const int t = i / nx;
+    x = i - t * nx;
+    z = t / ny;
+    y = t - z * ny;
+}
 
 // forward rho, j, psi of the stored state (lattice layout L)
 template <class S>
@@ -34,12 +42,15 @@ __global__ void adj_forward_kernel(Layout L, KParams P, const S* __restrict__ f,
 {
     const long long N = (long long)L.nx * L.ny * L.nz;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
-        const int x = (int)(i % L.nx), y = (int)((i / L.nx) % L.ny), z = (int)(i / ((long long)L.nx * L.ny));
+        int x, y, z;
+        node_xyz((int)i, L.nx, L.ny, x, y, z);
         const bool solid = wall_z(z, L.nz);
         const long long off = L.off(x, y, z);
+        #pragma unroll
         for (int a = 0; a < 2; ++a) {
             float r = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
             if (!solid) {
+                #pragma unroll
                 for (int k = 0; k < Q; ++k) {
                     float v = Codec<S>::load(f + (long long)(a * Q + k) * L.slot + off);
                     if constexpr (Codec<S>::kDeviation) v = zeta(k) * (P.ref[a] + v);
@@ -69,26 +80,35 @@ __global__ void __launch_bounds__(256)
     const long long N = (long long)nx * ny * nz;
     double geta[2] = {0.0, 0.0};
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
-        const int x = (int)(i % nx), y = (int)((i / nx) % ny), z = (int)(i / ((long long)nx * ny));
+        int x, y, z;
+        node_xyz((int)i, nx, ny, x, y, z);
         if (wall_z(z, nz)) {
+            #pragma unroll
             for (int k = 0; k < 2 * Q; ++k) lam_cur[(long long)k * N + i] = 0.f;
+            #pragma unroll
             for (int a = 0; a < 2; ++a) {
                 A.rhob[a][i] = 0.f;
                 A.psib[a][i] = 0.f;
+                #pragma unroll
                 for (int d = 0; d < 3; ++d) A.jb[a][d][i] = A.V[a][d][i] = 0.f;
             }
             continue;
         }
         float rho[2], j[2][3], psi[2], S[2][3], F[2][3];
+        #pragma unroll
         for (int a = 0; a < 2; ++a) {
             rho[a] = A.rho[a][i];
             psi[a] = A.psi[a][i];
+            #pragma unroll
             for (int d = 0; d < 3; ++d) j[a][d] = A.j[a][d][i];
         }
         // S^a = sum_m G_m psi~^abar(y + c_m) c_m, wall links flagged
+        #pragma unroll
         for (int a = 0; a < 2; ++a) S[a][0] = S[a][1] = S[a][2] = 0.f;
+        #pragma unroll
         for (int m = 1; m < Q; ++m) {
             const long long n = didx(wrapi(x + cx(m), nx), wrapi(y + cy(m), ny), z + cz(m), nx, ny);
+            #pragma unroll
             for (int a = 0; a < 2; ++a) {
                 const float ps = G.G[m] * A.psi[1 - a][n];
                 S[a][0] += ps * cx(m);
@@ -96,20 +116,26 @@ __global__ void __launch_bounds__(256)
                 S[a][2] += ps * cz(m);
             }
         }
+        #pragma unroll
         for (int a = 0; a < 2; ++a)
+            #pragma unroll
             for (int d = 0; d < 3; ++d) F[a][d] = -G.gk * psi[a] * S[a][d];
         const float D = G.omega[0] * rho[0] + G.omega[1] * rho[1];
         float up[3] = {0.f, 0.f, 0.f};
         if (D > 0.f)
+            #pragma unroll
             for (int d = 0; d < 3; ++d) up[d] = (G.omega[0] * j[0][d] + G.omega[1] * j[1][d]) / D;
 
         float rhob[2] = {0.f, 0.f}, ub[2][3], upb[3] = {0.f, 0.f, 0.f};
+        #pragma unroll
         for (int a = 0; a < 2; ++a) {
             const bool shift = rho[a] > 1e-12f;
             float u[3];
+            #pragma unroll
             for (int d = 0; d < 3; ++d) u[d] = up[d] + (shift ? G.tau[a] * F[a][d] / rho[a] : 0.f);
             const float usq = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
             ub[a][0] = ub[a][1] = ub[a][2] = 0.f;
+            #pragma unroll
             for (int k = 0; k < Q; ++k) {
                 // mu_k = lambda_k(y + c_k), or lambda_kbar(y) when y + c_k is a wall
                 const int zt = z + cz(k);
@@ -127,12 +153,15 @@ __global__ void __launch_bounds__(256)
                 ub[a][1] += w * (cy(k) * Ak + u[1] * Bk);
                 ub[a][2] += w * (cz(k) * Ak + u[2] * Bk);
             }
+            #pragma unroll
             for (int d = 0; d < 3; ++d) upb[d] += ub[a][d];
         }
         float Fb[2][3];
+        #pragma unroll
         for (int a = 0; a < 2; ++a) {
             const bool shift = rho[a] > 1e-12f;
             float dot = 0.f;
+            #pragma unroll
             for (int d = 0; d < 3; ++d) {
                 Fb[a][d] = shift ? ub[a][d] * G.tau[a] / rho[a] : 0.f;
                 dot += ub[a][d] * F[a][d];
@@ -142,34 +171,42 @@ __global__ void __launch_bounds__(256)
         float jb[2][3];
         if (D > 0.f) {
             const float updot = upb[0] * up[0] + upb[1] * up[1] + upb[2] * up[2];
+            #pragma unroll
             for (int a = 0; a < 2; ++a) {
+                #pragma unroll
                 for (int d = 0; d < 3; ++d) jb[a][d] = G.omega[a] * upb[d] / D;
                 rhob[a] -= G.omega[a] * updot / D;
             }
         } else {
+            #pragma unroll
             for (int a = 0; a < 2; ++a) jb[a][0] = jb[a][1] = jb[a][2] = 0.f;
         }
         // force: psi^a(y) factor and the neighbour sum
+        #pragma unroll
         for (int a = 0; a < 2; ++a) {
             float V[3];
             float sdot = 0.f;
+            #pragma unroll
             for (int d = 0; d < 3; ++d) {
                 V[d] = -G.gk * psi[a] * Fb[a][d];
                 sdot += Fb[a][d] * S[a][d];
             }
             A.psib[a][i] = -G.gk * sdot;
+            #pragma unroll
             for (int d = 0; d < 3; ++d) {
                 A.V[a][d][i] = V[d];
                 A.jb[a][d][i] = jb[a][d];
             }
             A.rhob[a][i] = rhob[a];
             // wall links of the neighbour sum feed d J / d eta_abar
+            #pragma unroll
             for (int m = 1; m < Q; ++m)
                 if (wall_z(z + cz(m), nz)) geta[1 - a] += (double)(G.G[m] * (V[0] * cx(m) + V[1] * cy(m) + V[2] * cz(m)));
         }
     }
     // block reduction of the wall gradient
     __shared__ double sh[8][2];
+    #pragma unroll
     for (int a = 0; a < 2; ++a) {
         double v = geta[a];
         for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -190,11 +227,14 @@ __global__ void adj_gather_kernel(AdjArgs G, AdjFields A, float* __restrict__ la
     const int nx = G.nx, ny = G.ny, nz = G.nz;
     const long long N = (long long)nx * ny * nz;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
-        const int x = (int)(i % nx), y = (int)((i / nx) % ny), z = (int)(i / ((long long)nx * ny));
+        int x, y, z;
+        node_xyz((int)i, nx, ny, x, y, z);
         if (wall_z(z, nz)) continue;
+        #pragma unroll
         for (int a = 0; a < 2; ++a) {
             // psi^a(x) is used by F^abar(x - c_m) for every fluid x - c_m
             float pb = A.psib[a][i];
+            #pragma unroll
             for (int m = 1; m < Q; ++m) {
                 const int zs = z - cz(m);
                 if (wall_z(zs, nz)) continue;
@@ -203,6 +243,7 @@ __global__ void adj_gather_kernel(AdjArgs G, AdjFields A, float* __restrict__ la
             }
             const float rb = A.rhob[a][i] + pb * expf(-A.rho[a][i]);
             const float jb[3] = {A.jb[a][0][i], A.jb[a][1][i], A.jb[a][2][i]};
+            #pragma unroll
             for (int k = 0; k < Q; ++k)
                 lam_cur[(long long)(a * Q + k) * N + i] += rb + cx(k) * jb[0] + cy(k) * jb[1] + cz(k) * jb[2];
         }
@@ -290,6 +331,7 @@ __global__ void obs_grad_kernel(int nx, int ny, int nz, int obs, double eps, con
                 gb = -gphi;
             }
         }
+        #pragma unroll
         for (int k = 0; k < Q; ++k) {
             lam[(long long)k * N + i] = (float)gr;
             lam[(long long)(Q + k) * N + i] = (float)gb;

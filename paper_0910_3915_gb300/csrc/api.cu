@@ -1290,19 +1290,58 @@ extern "C" int lb_step_backward(lb_ctx* c, int nsteps, int ckpt_every, int obser
         G.omega[a] = c->kp.itau[a];
         G.eta[a] = c->kp.eta[a];
     }
-    auto fwd = [&](const void* f) -> cudaError_t {
+    auto fwd_on = [&](const void* f, cudaStream_t s2) -> cudaError_t {
         switch (c->prec) {
-        case LB_F32: return adj_forward_of<float>(c, f, A, st);
-        case LB_F16: return adj_forward_of<__half>(c, f, A, st);
-        default: return adj_forward_of<__nv_bfloat16>(c, f, A, st);
+        case LB_F32: return adj_forward_of<float>(c, f, A, s2);
+        case LB_F16: return adj_forward_of<__half>(c, f, A, s2);
+        default: return adj_forward_of<__nv_bfloat16>(c, f, A, s2);
         }
     };
-    auto step_into = [&](const void* src, void* dst) -> cudaError_t {
+    auto fwd = [&](const void* f) { return fwd_on(f, st); };
+    auto step_into = [&](const void* src, void* dst, cudaStream_t s2) -> cudaError_t {
         switch (c->prec) {
-        case LB_F32: return adj_step_into<float>(c, src, dst, st);
-        case LB_F16: return adj_step_into<__half>(c, src, dst, st);
-        default: return adj_step_into<__nv_bfloat16>(c, src, dst, st);
+        case LB_F32: return adj_step_into<float>(c, src, dst, s2);
+        case LB_F16: return adj_step_into<__half>(c, src, dst, s2);
+        default: return adj_step_into<__nv_bfloat16>(c, src, dst, s2);
         }
+    };
+    // One segment's recompute and reverse sweep, as launched on stream s2. The
+    // launches depend only on the segment length and on which lambda buffer
+    // holds lambda(t+1) at its end, so each such pair is captured once into a
+    // CUDA graph and replayed (about 5 launches per step otherwise).
+    auto segment = [&](int len, float* ln, float* lc, cudaStream_t s2) -> cudaError_t {
+        cudaError_t e = cudaSuccess;
+        for (int i = 0; i < len && e == cudaSuccess; ++i) e = step_into(store + sb * (size_t)i, store + sb * (size_t)(i + 1), s2);
+        for (int i = len - 1; i >= 0 && e == cudaSuccess; --i) {
+            e = fwd_on(store + sb * (size_t)i, s2);
+            if (e == cudaSuccess) e = launch_adj_backstep(G, A, ln, lc, part, acc, s2);
+            std::swap(ln, lc);
+        }
+        return e;
+    };
+    struct SegGraphs {
+        std::vector<std::pair<long long, cudaGraphExec_t>> g;
+        ~SegGraphs()
+        {
+            for (auto& p : g) cudaGraphExecDestroy(p.second);
+        }
+    } graphs;
+    auto run_segment = [&](int len, float* ln, float* lc) -> cudaError_t {
+        const long long key = 2LL * len + (ln == lam ? 0 : 1);
+        for (auto& p : graphs.g)
+            if (p.first == key) return cudaGraphLaunch(p.second, st);
+        cudaGraph_t gr = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return e;
+        const cudaError_t e1 = segment(len, ln, lc, c->cap);
+        e = cudaStreamEndCapture(c->cap, &gr);
+        if (e1 != cudaSuccess) e = e1;
+        cudaGraphExec_t ex = nullptr;
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&ex, gr, 0);
+        if (gr) cudaGraphDestroy(gr);
+        if (e != cudaSuccess) return e;
+        graphs.g.emplace_back(key, ex);
+        return cudaGraphLaunch(ex, st);
     };
 
     // forward: a checkpoint at the start of every segment (with the step count,
@@ -1328,12 +1367,8 @@ extern "C" int lb_step_backward(lb_ctx* c, int nsteps, int ckpt_every, int obser
         const int len = nsteps - t0 < ckpt_every ? nsteps - t0 : ckpt_every;
         LB_CUDA(c, cudaMemcpyAsync(store, ck + sb * (size_t)s, sb, cudaMemcpyDeviceToDevice, st));
         LB_CUDA(c, launch_clock_set(c->clock, (uint32_t)ck_steps[s], st));
-        for (int i = 0; i < len; ++i) LB_CUDA(c, step_into(store + sb * (size_t)i, store + sb * (size_t)(i + 1)));
-        for (int i = len - 1; i >= 0; --i) {
-            LB_CUDA(c, fwd(store + sb * (size_t)i));
-            LB_CUDA(c, launch_adj_backstep(G, A, lam_next, lam_cur, part, acc, st));
-            std::swap(lam_next, lam_cur);
-        }
+        LB_CUDA(c, run_segment(len, lam_next, lam_cur));
+        if (len & 1) std::swap(lam_next, lam_cur);
     }
     LB_CUDA(c, launch_clock_set(c->clock, (uint32_t)c->steps, st));
     double h[3] = {0, 0, 0};

@@ -72,7 +72,7 @@ def name(cand) -> str:
     return "%s:%d:%d:%d:%d" % tuple(cand)
 
 
-def tune(lat, steps: int = 64, segments=SEGMENTS, cache: str | None = None):
+def tune(lat, steps: int = 128, segments=SEGMENTS, cache: str | None = None):
     """Pick the fastest (variant, stages, tile_y, z_segments, y_tiles) for ``lat``; returns (best, table)."""
     import torch
 
@@ -91,14 +91,17 @@ def tune(lat, steps: int = 64, segments=SEGMENTS, cache: str | None = None):
     for cand in candidates(lat.nz - 2, lat.precision, segments, lat.nx, lat.ny, n_sm):
         apply(lat, cand)
         lat.step(steps)  # warm-up, graph capture
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        lat.sync()
-        e0.record(stream)
-        lat.step(steps)
-        e1.record(stream)
-        e1.synchronize()
-        timings[name(cand)] = e0.elapsed_time(e1) / steps
+        best = float("inf")
+        for _ in range(2):  # the better of two timings: a one-off stall on a shared host does not pick the schedule
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            lat.sync()
+            e0.record(stream)
+            lat.step(steps)
+            e1.record(stream)
+            e1.synchronize()
+            best = min(best, e0.elapsed_time(e1) / steps)
+        timings[name(cand)] = best
     lat.load(state)
     best = parse(min(timings, key=timings.get))
     apply(lat, best)

@@ -406,3 +406,15 @@ def test_young_planar_wall_tensions_mirror_and_sign():
     assert oracle.young_theta(sg, sl, 0.01) > 90.0
     assert oracle.young_theta(1.0, 1.0, 0.5) == 90.0
     assert oracle.young_theta(0.0, 1.0, 0.5) == 180.0 and oracle.young_theta(1.0, 0.0, 0.5) == 0.0
+
+
+def test_oracle_counts_non_finite_populations():
+    """A NaN fed to the oracle is counted in the conservation sums' non-finite
+    slot (the GPU reduction reports the same count as LB_ERR_NAN)."""
+    rr, rb = W.droplet_fields(6, 5, 6, 2.0)
+    st = oracle.State(rr, rb, W.wall_mask(6, 5, 6), Params())
+    st.n[1, 7, 2, 3, 4] = np.nan
+    st.n[0, 0, 3, 1, 1] = np.inf
+    assert st.moments()[3][5] == 2
+    st.n[0, 0, 0, 1, 1] = np.nan  # a solid node holds no populations and is not counted
+    assert st.moments()[3][5] == 2
