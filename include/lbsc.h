@@ -233,6 +233,14 @@ int lb_get_populations(lb_ctx* ctx, double* n);
 /* Replace the populations from a host array laid out as in lb_get_populations. */
 int lb_set_populations(lb_ctx* ctx, const double* n);
 
+/* Build properties: LB_BUILD_BOUNDS_CHECKED is set in a library compiled
+ * with LBSC_DEBUG_BOUNDS, whose step kernels check every population index
+ * against its buffer, skip an access that falls outside and report
+ * LB_ERR_STATE at the next lb_sync or readback (a stand-in for a memory
+ * checker: no access leaves the buffer, no trap). */
+#define LB_BUILD_BOUNDS_CHECKED 1
+int lb_build_flags(int* flags);
+
 /* Choose the step kernel's tile height (4, 8 or 16 rows of 32 nodes) and the
  * number of z segments per tile column (0 = automatic). */
 int lb_set_schedule(lb_ctx* ctx, int tile_y, int z_segments);

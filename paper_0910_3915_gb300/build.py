@@ -1,6 +1,6 @@
 """Build the lbsc C-ABI shared library (CUDA for sm_103a) in-tree.
 
-    python -m paper_0910_3915_gb300.build [--verbose]
+    python -m paper_0910_3915_gb300.build [--verbose] [--debug-bounds]
 
 Compiles csrc/*.cu in parallel with nvcc into _build/ and links
 paper_0910_3915_gb300/liblbsc.so against the shared CUDA runtime.
@@ -33,20 +33,28 @@ def sources():
     return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cu"))
 
 
-def build(verbose: bool = False, force: bool = False) -> str:
-    os.makedirs(BUILD, exist_ok=True)
+DEBUG_OUT = os.path.join(PKG, "liblbsc_debug.so")
+
+
+def build(verbose: bool = False, force: bool = False, debug_bounds: bool = False) -> str:
+    """Build liblbsc.so, or with debug_bounds liblbsc_debug.so, whose step
+    kernels check every population index (LBSC_DEBUG_BOUNDS)."""
+    out_path = DEBUG_OUT if debug_bounds else OUT
+    build_dir = BUILD + ("_debug" if debug_bounds else "")
+    extra = ["-DLBSC_DEBUG_BOUNDS"] if debug_bounds else []
+    os.makedirs(build_dir, exist_ok=True)
     srcs = sources()
     deps = srcs + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cuh")]
     deps.append(os.path.join(ROOT, "include", "lbsc.h"))
     newest = max(os.path.getmtime(d) for d in deps)
-    if not force and os.path.exists(OUT) and os.path.getmtime(OUT) >= newest:
-        return OUT
+    if not force and os.path.exists(out_path) and os.path.getmtime(out_path) >= newest:
+        return out_path
     cc = nvcc()
     procs, objs = [], []
     for s in srcs:
-        o = os.path.join(BUILD, os.path.basename(s)[:-3] + ".o")
+        o = os.path.join(build_dir, os.path.basename(s)[:-3] + ".o")
         objs.append(o)
-        cmd = [cc, *ARCH, *FLAGS, "-c", s, "-o", o]
+        cmd = [cc, *ARCH, *FLAGS, *extra, "-c", s, "-o", o]
         if verbose:
             cmd += ["-Xptxas", "-v"]
         procs.append((s, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)))
@@ -59,12 +67,12 @@ def build(verbose: bool = False, force: bool = False) -> str:
     if failed:
         raise RuntimeError("nvcc failed")
     cudalib = os.path.join(os.path.dirname(os.path.dirname(cc)), "lib64")
-    tmp = OUT + f".tmp{os.getpid()}"
+    tmp = out_path + f".tmp{os.getpid()}"
     subprocess.run([cc, *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs,
                     "-Xlinker", f"-rpath,{cudalib}"], check=True)
-    os.replace(tmp, OUT)
-    return OUT
+    os.replace(tmp, out_path)
+    return out_path
 
 
 if __name__ == "__main__":
-    print(build(verbose="--verbose" in sys.argv, force=True))
+    print(build(verbose="--verbose" in sys.argv, force=True, debug_bounds="--debug-bounds" in sys.argv))

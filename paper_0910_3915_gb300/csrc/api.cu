@@ -557,6 +557,13 @@ int lb_set_params(lb_ctx* c, const lb_params* p)
     return LB_OK;
 }
 
+int lb_build_flags(int* flags)
+{
+    if (!flags) return LB_ERR_ARG;
+    *flags = kCheckBounds ? LB_BUILD_BOUNDS_CHECKED : 0;
+    return LB_OK;
+}
+
 int lb_selftest_bounded_wait(lb_ctx* c, unsigned spin_limit)
 {
     if (!c || spin_limit < 1 || spin_limit > (1u << 20))
@@ -806,6 +813,8 @@ static int check_device_status(lb_ctx* c)
     LB_CUDA(c, cudaMemcpy(&h, c->dev_err, sizeof(int), cudaMemcpyDeviceToHost));
     if (h != 0) {
         LB_CUDA(c, cudaMemset(c->dev_err, 0, sizeof(int)));
+        if (h & kErrBounds)
+            return fail(c, LB_ERR_STATE, "an index fell outside its buffer (bounds-checked build); the access was skipped");
         return fail(c, LB_ERR_BARRIER_TIMEOUT, "a bounded wait in the step kernel gave up (TMA stage never landed)");
     }
     return LB_OK;

@@ -195,6 +195,24 @@ struct StepArgs {
 
 constexpr uint32_t kSelfSolid = 1u << 31;
 
+// Device status word bits (StepArgs::err): a bounded wait gave up; an index
+// fell outside its buffer (only a build with LBSC_DEBUG_BOUNDS checks indices).
+constexpr int kErrWait = 1;
+constexpr int kErrBounds = 2;
+#ifdef LBSC_DEBUG_BOUNDS
+constexpr bool kCheckBounds = true;
+#else
+constexpr bool kCheckBounds = false;
+#endif
+// Bounds check of the debug build: true if 0 <= i < n; otherwise records
+// kErrBounds in the status word and the caller skips the access.
+__device__ __forceinline__ bool in_bounds(long long i, long long n, int* err)
+{
+    if (i >= 0 && i < n) return true;
+    atomicOr(err, kErrBounds);
+    return false;
+}
+
 // first row of y-tile t when n rows are split into nt tiles as evenly as possible
 __host__ __device__ __forceinline__ int tile_row(int t, int n, int nt) { return (int)((long long)t * n / nt); }
 

@@ -84,6 +84,8 @@ __device__ __forceinline__ void step_item(const StepArgs<S>& A, int col, int za,
         const int zoff = zw * plane;
         const bool wall_plane = !kGeneral && (zp == 0 || zp == nz - 1);
         if (!active) so_ = true;  // idle row: no loads, no psi
+        // bounds-checked build: every slot of a node lies in the buffer iff its offset in the slot does
+        else if (kCheckBounds && !in_bounds((long long)zoff + own, L.slot, A.err)) so_ = true;
         else if constexpr (kGeneral) so_ = (__ldg(nbmask + zoff + own) & kSelfSolid) != 0;
         else so_ = wall_plane;
         if (!so_) {
@@ -96,7 +98,8 @@ __device__ __forceinline__ void step_item(const StepArgs<S>& A, int col, int za,
 #pragma unroll
         for (int i = 0; i < NIT; ++i) {
             if (it_a[i] < 0) continue;
-            if constexpr (kGeneral) si_[i] = (__ldg(nbmask + zoff + it_off[i]) & kSelfSolid) != 0;
+            if (kCheckBounds && !in_bounds((long long)zoff + it_off[i], L.slot, A.err)) si_[i] = true;
+            else if constexpr (kGeneral) si_[i] = (__ldg(nbmask + zoff + it_off[i]) & kSelfSolid) != 0;
             else si_[i] = wall_plane;
             if (!si_[i]) {
                 const S* p = src + (it_a[i] * Q * slot + zoff + it_off[i]);
@@ -144,6 +147,7 @@ __device__ __forceinline__ void step_item(const StepArgs<S>& A, int col, int za,
 
     Dest D;
     D.set_column(L, valid ? gx : 0, valid ? gy : 0);
+    D.err = A.err;
 
     for (int z = za; z < zb; ++z) {
         reduce(z + 1, rn, jn, vn, mn);

@@ -106,6 +106,7 @@ struct Dest {
     int zo[3];         // plane offsets of z-1, z, z+1 (offsets stay below 2^31: slot < 2^31)
     bool bot, top;     // planar walls: solid plane below / above
     uint32_t nb;       // general geometry: bit k = link k ends on a solid node
+    int* err;          // status word (bounds-checked build only)
 
     // per-thread part that stays fixed while the thread marches in z
     __device__ __forceinline__ void set_column(const Layout& L, int x, int y)
@@ -189,7 +190,10 @@ __device__ __forceinline__ void collide_store(const float (&rc)[2], const float 
         if constexpr (kGeneral) wall = (D.nb >> k) & 1u;
         else wall = (cz(k) < 0 && D.bot) || (cz(k) > 0 && D.top);
         // destination: the neighbour x + c_k, or slot kbar of this node (bounce-back)
-        S* q = dst + (wall ? self : D.zo[cz(k) + 1] + D.ro[cy(k) + 1] + D.xo[cx(k) + 1]);
+        const int qo = wall ? self : D.zo[cz(k) + 1] + D.ro[cy(k) + 1] + D.xo[cx(k) + 1];
+        if constexpr (kCheckBounds)
+            if (!in_bounds(qo, slot, D.err)) continue;
+        S* q = dst + qo;
         const long long so = (long long)(wall ? opp(k) : k) * slot;
 #pragma unroll
         for (int a = 0; a < 2; ++a) {
@@ -214,6 +218,8 @@ __device__ __forceinline__ void collide_store(const float (&rc)[2], const float 
             }
         }
     }
+    if constexpr (kCheckBounds)
+        if (!in_bounds(self, slot, D.err)) return;
     S* q0 = dst + self;
     uint32_t hrest = 0;
     if constexpr (Codec<S>::kDitherMoving) hrest = node_hash(hsh, 0x632BE5ABu);  // a second full mixing round

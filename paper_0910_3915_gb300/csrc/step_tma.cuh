@@ -210,7 +210,7 @@ __global__ void __launch_bounds__(32 * TY) step_tma_kernel(const __grid_constant
             const bool bad = __syncthreads_or(!ok);
             if (bad) {
                 if (tid == 0) {
-                    atomicExch(A.err, 1);
+                    atomicOr(A.err, kErrWait);
                     for (int k2 = i; k2 < np && k2 < i + NS; ++k2) mbar_wait(&bar[(g + k2) % NS], ((g + k2) / NS) & 1u);
                 }
                 return false;
@@ -231,6 +231,7 @@ __global__ void __launch_bounds__(32 * TY) step_tma_kernel(const __grid_constant
 
         Dest D;
         D.set_column(L, valid ? gx : 0, valid ? gy : 0);
+        D.err = A.err;
 
         for (int z = za; z < zb; ++z) {
             if (!consume(z - za + 2, rn, jn, vn, mn)) {

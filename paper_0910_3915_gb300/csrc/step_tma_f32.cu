@@ -28,7 +28,7 @@ __global__ void wait_probe_kernel(int* err, uint32_t limit)
     __syncthreads();
     bool ok = false;
     for (uint32_t i = 0; i < limit && !ok; ++i) ok = mbar_try_wait(&bar, 0);
-    if (__syncthreads_or(!ok) && threadIdx.x == 0) atomicExch(err, 1);
+    if (__syncthreads_or(!ok) && threadIdx.x == 0) atomicOr(err, kErrWait);
 }
 
 cudaError_t launch_wait_probe(int* err, unsigned limit, cudaStream_t st)

@@ -16,7 +16,8 @@ from dataclasses import dataclass
 
 import numpy as np
 
-_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "liblbsc.so")
+# LBSC_LIBRARY selects another build of the library (e.g. the bounds-checked liblbsc_debug.so)
+_LIB_PATH = os.environ.get("LBSC_LIBRARY") or os.path.join(os.path.dirname(os.path.abspath(__file__)), "liblbsc.so")
 
 LB_OK = 0
 LB_ERR_ARG = -1
@@ -31,6 +32,7 @@ PRECISIONS = {"f32": LB_F32, "f16": LB_F16, "bf16": LB_BF16}
 LB_WEIGHTS_UNIT, LB_WEIGHTS_W36 = 0, 1
 LB_STEP_AUTO, LB_STEP_LDG, LB_STEP_TMA = 0, 1, 2
 LB_OBS_COM, LB_OBS_COM_SOFT, LB_OBS_WETTED = 0, 1, 2
+LB_BUILD_BOUNDS_CHECKED = 1
 OBSERVABLES = {"com": LB_OBS_COM, "com_soft": LB_OBS_COM_SOFT, "wetted": LB_OBS_WETTED}
 STEP_VARIANTS = {"auto": LB_STEP_AUTO, "ldg": LB_STEP_LDG, "tma": LB_STEP_TMA}
 
@@ -96,6 +98,7 @@ SIGNATURES = [
     ("lb_get_populations", _I, [_VP, _DP]),
     ("lb_set_populations", _I, [_VP, _DP]),
     ("lb_set_schedule", _I, [_VP, _I, _I]),
+    ("lb_build_flags", _I, [ctypes.POINTER(_I)]),
     ("lb_set_tiling", _I, [_VP, _I, _I, _I]),
     ("lb_pressure_tensor", _I, [_VP, _DP]),
     ("lb_pressure_profile", _I, [_VP, _DP, _DP]),
@@ -133,6 +136,12 @@ def huang_theta(eta_wall_r: float, eta_wall_b: float, rho_in: float, rho_out: fl
     _check(load().lb_huang_theta(float(eta_wall_r), float(eta_wall_b), float(rho_in), float(rho_out),
                                  ctypes.byref(t)))
     return t.value
+
+
+def build_flags() -> int:
+    f = ctypes.c_int()
+    _check(load().lb_build_flags(ctypes.byref(f)))
+    return f.value
 
 
 def load(path: str = _LIB_PATH):

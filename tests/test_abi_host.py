@@ -62,7 +62,7 @@ def test_constants_match_header():
     for name in ("LB_OK", "LB_ERR_ARG", "LB_ERR_CUDA", "LB_ERR_NAN", "LB_ERR_BARRIER_TIMEOUT",
                  "LB_ERR_STATE", "LB_ERR_UNSUPPORTED", "LB_F32", "LB_F16", "LB_BF16",
                  "LB_WEIGHTS_UNIT", "LB_WEIGHTS_W36", "LB_STEP_AUTO", "LB_STEP_LDG", "LB_STEP_TMA", "LB_OBS_COM",
-                 "LB_OBS_COM_SOFT", "LB_OBS_WETTED"):
+                 "LB_OBS_COM_SOFT", "LB_OBS_WETTED", "LB_BUILD_BOUNDS_CHECKED"):
         assert int(defs[name]) == getattr(lbsc, name), name
 
 
