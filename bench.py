@@ -167,6 +167,19 @@ def oracle_mlups(dims, radius, w, seconds: float):
     return nf * n / el / 1e6, n, el
 
 
+def oracle_mlups_one_core(dims, radius, w, seconds: float):
+    """oracle_mlups with one OpenMP thread (a child process: the thread count is
+    fixed when the oracle library starts)."""
+    code = ("import json, sys; sys.path.insert(0, %r); import bench; "
+            "print(json.dumps(bench.oracle_mlups(%r, %r, %r, %r)))" % (ROOT, tuple(dims), radius, w, seconds))
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    try:
+        out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600)
+        return json.loads(out.stdout.strip().splitlines()[-1])
+    except Exception:
+        return None
+
+
 def omp_threads():
     v = os.environ.get("OMP_NUM_THREADS")
     return int(v) if v and v.isdigit() else (os.cpu_count() or 1)
@@ -311,6 +324,10 @@ def run_ours(args):
         c_mlups, c_n, c_el = oracle_mlups(wl["dims"], wl["radius"], wl["w"], seconds=15.0)
         cpu = {"value": round(c_mlups, 3), "unit": "MLUPS", "cores": omp_threads(), "kind": "oracle",
                "sample": f"{nx}x{ny}x{nz} droplet, {c_n} oracle steps ({c_el:.1f} s)"}
+        one = oracle_mlups_one_core(wl["dims"], wl["radius"], wl["w"], seconds=8.0)
+        if one:
+            cpu["one_core"] = {"value": round(one[0], 3), "unit": "MLUPS", "cores": 1,
+                               "sample": f"{one[1]} oracle steps ({one[2]:.1f} s)"}
     line = {
         "metric": METRIC, "value": round(value, 1), "unit": "MLUPS", "n_gpus": ws, "steps": K, "warmup": Wm,
         "ms_per_step": round(ms / K, 5), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
