@@ -60,14 +60,24 @@ def test_small_droplet_100_steps(lbsc, w, reading):
     assert rel_err(g, o, W.wall_mask(nx, ny, nz)) <= 1e-5
 
 
-@pytest.mark.parametrize("dims", [(45, 27, 19), (33, 9, 7), (5, 3, 6), (70, 41, 12)])
+@pytest.mark.parametrize("dims", [(45, 27, 19), (33, 9, 7), (5, 3, 6), (70, 41, 12), (1, 1, 10), (2, 3, 3),
+                                  (31, 1, 5), (1, 17, 4)])
 def test_ragged_lattices(lbsc, dims):
-    """Sizes that leave ragged tiles in x and y and short z columns."""
+    """Sizes that leave ragged tiles in x and y and short z columns, down to a
+    single column (1 x 1) and a single fluid plane (nz = 3)."""
     nx, ny, nz = dims
     rr, rb = W.droplet_fields(nx, ny, nz, min(nx, ny) / 3, seed=4)
     prm = dict(CONTACT, eta_wall_r=-0.03, eta_wall_b=0.03)
     g, o = run_pair(lbsc, rr, rb, W.wall_mask(nx, ny, nz), 100, prm)
     assert rel_err(g, o, W.wall_mask(nx, ny, nz)) <= 1e-5
+
+
+def test_single_column_periodic_lamella(lbsc):
+    """A 1 x 1 x 32 fully periodic column (the oracle's flat-interface set-up):
+    every neighbour in x and y is the node itself."""
+    rr, rb = W.lamella_fields(1, 1, 32, seed=2, noise=1e-3)
+    g, o = run_pair(lbsc, rr, rb, W.periodic_mask(1, 1, 32), 300, dict(CONTACT), walls_default=False)
+    assert rel_err(g, o, W.periodic_mask(1, 1, 32)) <= 1e-5
 
 
 def test_unequal_tau(lbsc):
