@@ -253,7 +253,9 @@ int lb_set_schedule(lb_ctx* ctx, int tile_y, int z_segments);
 int lb_set_tiling(lb_ctx* ctx, int tile_y, int y_tiles, int z_segments);
 
 /* Choose the step kernel: LB_STEP_AUTO, LB_STEP_LDG or LB_STEP_TMA, and for
- * the TMA kernel the number of shared-memory stages (2 or 3; 0 = automatic).
+ * the TMA kernel the number of shared-memory stages, i.e. planes in flight
+ * (1, 2 or 3; 0 = automatic: 3, else 2). One stage leaves room for more
+ * resident CTAs per SM.
  * Every variant computes bit-identical results. LB_STEP_TMA with a
  * non-planar geometry, or a (tile height, stages) pair that is not built for
  * the precision, falls back to LB_STEP_LDG. */

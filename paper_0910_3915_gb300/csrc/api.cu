@@ -210,7 +210,7 @@ static long long tma_call(int op, lb_ctx* c, int ty, int ns)
 static cudaError_t tma_prepare(lb_ctx* c)
 {
     for (int ty : kTmaTiles)
-        for (int ns = 2; ns <= 3; ++ns) {
+        for (int ns = 1; ns <= 3; ++ns) {
             const long long e = tma_call(1, c, ty, ns);  // cudaErrorInvalidValue: pair not built
             if (e != (long long)cudaSuccess && e != (long long)cudaErrorInvalidValue) return (cudaError_t)e;
         }
@@ -575,7 +575,7 @@ int lb_selftest_bounded_wait(lb_ctx* c, unsigned spin_limit)
 int lb_set_step_variant(lb_ctx* c, int variant, int stages)
 {
     if (!c) return fail(c, LB_ERR_ARG, "lb_set_step_variant: NULL context");
-    if (variant < LB_STEP_AUTO || variant > LB_STEP_TMA || (stages != 0 && stages != 2 && stages != 3))
+    if (variant < LB_STEP_AUTO || variant > LB_STEP_TMA || stages < 0 || stages > 3)
         return fail(c, LB_ERR_ARG, "lb_set_step_variant: unknown variant or stages");
     drop_graphs(c);
     c->variant = variant;

@@ -309,11 +309,14 @@ static long long tma_dispatch(int op, int ty, int ns, bool t1, const CUtensorMap
         }                                                                                             \
         return t1 ? tma_occ_one<S, TY_, NS_, true>() : tma_occ_one<S, TY_, NS_, false>();             \
     }
+    LBSC_TMA_CASE(4, 1)
     LBSC_TMA_CASE(4, 2)
     LBSC_TMA_CASE(4, 3)
+    LBSC_TMA_CASE(8, 1)
     LBSC_TMA_CASE(8, 2)
     LBSC_TMA_CASE(8, 3)
     if constexpr (sizeof(S) == 2) {
+        LBSC_TMA_CASE(16, 1)
         LBSC_TMA_CASE(16, 2)
     }
 #undef LBSC_TMA_CASE

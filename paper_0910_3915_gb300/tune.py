@@ -18,7 +18,7 @@ import json
 import os
 
 SEGMENTS = (1, 2, 4, 8, 16)
-TMA_PAIRS = ((4, 2), (4, 3), (8, 2), (8, 3), (16, 2))  # (tile height, stages)
+TMA_PAIRS = ((4, 1), (4, 2), (4, 3), (8, 1), (8, 2), (8, 3), (16, 1), (16, 2))  # (tile height, stages)
 LDG_TILES = (4, 8)
 LDG_CTAS_PER_SM = {4: 3, 8: 2}  # resident CTAs of the tau = 1 load-from-global kernel
 

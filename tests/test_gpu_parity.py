@@ -158,9 +158,10 @@ def test_schedules_are_bitwise_identical(lbsc, precision):
     configs = [("ldg", 0, 8, 0, 1), ("tma", 2, 4, 0, 3), ("tma", 3, 8, 0, 2), ("tma", 2, 8, 0, 5),
                ("ldg", 0, 16, 0, 2), ("auto", 0, 4, 0, 0), ("tma", 3, 4, 0, 1),
                ("ldg", 0, 8, 4, 2), ("ldg", 0, 8, 23, 1), ("ldg", 0, 4, 7, 3), ("tma", 2, 8, 5, 2),
-               ("tma", 2, 4, 23, 1), ("ldg", 0, 16, 3, 4)]
+               ("tma", 2, 4, 23, 1), ("ldg", 0, 16, 3, 4), ("tma", 1, 8, 0, 3), ("tma", 1, 4, 7, 2),
+               ("tma", 1, 8, 23, 1)]
     if precision != "f32":
-        configs += [("tma", 2, 16, 0, 2), ("tma", 2, 16, 2, 3)]
+        configs += [("tma", 2, 16, 0, 2), ("tma", 2, 16, 2, 3), ("tma", 1, 16, 0, 2)]
     for variant, stages, ty, nty, seg in configs:
         lat = lbsc.Lattice(rr, rb, precision).set_step_variant(variant, stages).set_tiling(ty, nty, seg)
         lat.set_params(**CONTACT, eta_wall_b=0.05, eta_wall_r=-0.05)
