@@ -65,6 +65,8 @@ def parse():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="single")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--no-accuracy", action="store_true",
+                    help="precision workloads: skip the accuracy runs against FP32 and the oracle")
     ap.add_argument("--schedule", default=None,
                     help="fixed step schedule variant:stages:tile_y:z_segments[:y_tiles] (e.g. ldg:0:8:4:19); "
                          "skips tuning")
@@ -351,7 +353,7 @@ def run_ours(args):
     }
     m0 = float(rr[1:-1].sum()), float(rb[1:-1].sum())
     line["mass_rel_drift"] = [float(cons[0] / m0[0] - 1), float(cons[1] / m0[1] - 1)]
-    if args.workload.startswith("precision") and ws == 1:
+    if args.workload.startswith("precision") and ws == 1 and not args.no_accuracy:
         line["accuracy"] = precision_accuracy(prec, 10000)
     print(json.dumps(line), flush=True)
     if dist:
