@@ -45,7 +45,7 @@ struct lb_ctx {
     long long steps = 0;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     int variant = LB_STEP_AUTO, stages = 0;  // step kernel selection
-    CUtensorMap tmap[2][3];                  // per buffer, per tile height 4/8/16
+    CUtensorMap tmap[2][3][2];               // per buffer, per tile height 4/8/16: main box, x-edge strip
     bool tmap_ok[2][3] = {{false, false, false}, {false, false, false}};
     int* dev_err = nullptr;                  // device status word of the step kernels
     uint32_t* clock = nullptr;               // device step counter {steps mod 2^32, done-ticket}
@@ -261,15 +261,19 @@ static int tensor_map(lb_ctx* c, int buf, int ty)
     const cuuint64_t dims[5] = {(cuuint64_t)L.px, (cuuint64_t)(L.ny + 2), (cuuint64_t)L.nz, (cuuint64_t)Q, 2};
     const cuuint64_t strides[4] = {(cuuint64_t)L.px * es, (cuuint64_t)L.plane * es, (cuuint64_t)L.slot * es,
                                    (cuuint64_t)Q * L.slot * es};
+    // main box: the tile plus 16 bytes of columns on each side; strip: 16 bytes of columns (x edges)
     const cuuint32_t box[5] = {(cuuint32_t)(es == 4 ? 40 : 48), (cuuint32_t)(ty + 2), 1, (cuuint32_t)Q, 2};
+    const cuuint32_t sbox[5] = {(cuuint32_t)(16 / es), (cuuint32_t)(ty + 2), 1, (cuuint32_t)Q, 2};
     const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
     const CUtensorMapDataType dt = c->prec == LB_F32   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
                                    : c->prec == LB_F16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
                                                        : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
-    const CUresult r = enc(&c->tmap[buf][ti], dt, 5, c->f[buf], dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                           CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) return fail(c, LB_ERR_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
+    for (int kind = 0; kind < 2; ++kind) {
+        const CUresult r = enc(&c->tmap[buf][ti][kind], dt, 5, c->f[buf], dims, strides, kind ? sbox : box, estr,
+                               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return fail(c, LB_ERR_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
+    }
     c->tmap_ok[buf][ti] = true;
     return LB_OK;
 }
@@ -308,13 +312,13 @@ static cudaError_t refresh_ghosts_any(lb_ctx* c, int buf, cudaStream_t st)
     }
 }
 
-// one TMA-staged step, then the ghost images of its output
+// one TMA-staged step, then the ghost rows of its output
 template <class S>
 static cudaError_t launch_tma(lb_ctx* c, int parity, int ns, cudaStream_t st)
 {
     const StepArgs<S> A = step_args<S>(c, parity);
     cudaError_t e =
-        (cudaError_t)tma_step<S>(0, c->tile_y, ns, tau_one(c), &c->tmap[parity][tile_index(c->tile_y)], &A, st);
+        (cudaError_t)tma_step<S>(0, c->tile_y, ns, tau_one(c), c->tmap[parity][tile_index(c->tile_y)], &A, st);
     if (e != cudaSuccess) return e;
     return refresh_ghosts<S>(c, 1 - parity, st);
 }

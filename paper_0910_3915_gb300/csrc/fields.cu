@@ -56,6 +56,13 @@ __global__ void finish_kernel(const double* __restrict__ part, int nblocks, uint
     out[i] = v;
 }
 
+// blocks for n items at `threads` per block, at most cap (grid-stride loops cover the rest)
+static int grid_for(long long n, int threads, int cap)
+{
+    long long b = (n + threads - 1) / threads;
+    return (int)(b < 1 ? 1 : (b > cap ? cap : b));
+}
+
 template <class S>
 __device__ __forceinline__ float decode(const S* p, int k, float ref)
 {
@@ -379,33 +386,21 @@ __global__ void __launch_bounds__(kRedThreads) pressure_radial_kernel(FieldArgs 
         if (sh[b]) atomicAdd(&out[b], sh[b]);
 }
 
-// ---------------------------------------------------------------- ghost images
-// Refresh the ghost columns x = -1, nx and rows y = -1, ny (corners
-// included) of planes [z0, z1) from the real nodes they mirror.
+// ---------------------------------------------------------------- ghost rows
+// Refresh the ghost rows y = -1 and y = ny of planes [z0, z0 + nzp) from
+// rows ny-1 and 0 (x = 0 .. nx-1; the TMA-staged step reads them as the
+// periodic images in y, and takes its x images from strips of real columns).
 template <class S>
-__global__ void ghost_kernel(Layout L, S* __restrict__ f, int z0, int z1)
+__global__ void ghost_rows_kernel(Layout L, S* __restrict__ f, int z0, int nzp)
 {
-    const int per_plane = 2 * L.ny + 2 * (L.nx + 2);
-    const long long total = (long long)2 * Q * (z1 - z0) * per_plane;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
-        const int item = (int)(i % per_plane);
-        const long long rest = i / per_plane;
-        const int z = z0 + (int)(rest % (z1 - z0));
-        const int ak = (int)(rest / (z1 - z0));
-        S* p = f + (long long)ak * L.slot;
-        int sx, sy, gx, gy;  // source node, ghost position
-        if (item < 2 * L.ny) {
-            sy = gy = item >> 1;
-            gx = (item & 1) ? L.nx : -1;
-            sx = (item & 1) ? 0 : L.nx - 1;
-        } else {
-            const int r = item - 2 * L.ny;
-            gx = (r >> 1) - 1;  // -1 .. nx
-            sx = wrapi(gx, L.nx);
-            gy = (r & 1) ? L.ny : -1;
-            sy = (r & 1) ? 0 : L.ny - 1;
-        }
-        p[L.off(gx, gy, z)] = p[L.off(sx, sy, z)];
+    const int n = 2 * Q * nzp * L.nx;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int x = i % L.nx, t = i / L.nx;
+        const int z = z0 + t % nzp, ak = t / nzp;
+        S* p = f + (long long)ak * L.slot + (long long)z * L.plane + L.gx + x;  // row y = -1
+        const long long row = L.px;
+        p[0] = p[(long long)L.ny * row];          // y = -1  <- y = ny-1
+        p[(long long)(L.ny + 1) * row] = p[row];  // y = ny  <- y = 0
     }
 }
 
@@ -413,10 +408,9 @@ template <class S>
 cudaError_t launch_ghosts(const Layout& L, S* f, int z0, int z1, cudaStream_t st)
 {
     if (z1 <= z0) return cudaSuccess;
-    const long long total = (long long)2 * Q * (z1 - z0) * (2 * L.ny + 2 * (L.nx + 2));
-    long long b = (total + 255) / 256;
-    if (b > 4096) b = 4096;
-    ghost_kernel<S><<<(int)b, 256, 0, st>>>(L, f, z0, z1);
+    const int nzp = z1 - z0;
+    const long long n = (long long)2 * Q * nzp * L.nx;
+    ghost_rows_kernel<S><<<grid_for(n, 256, 8192), 256, 0, st>>>(L, f, z0, nzp);
     return cudaGetLastError();
 }
 
@@ -452,11 +446,6 @@ __global__ void set_pop_kernel(FieldArgs F, S* __restrict__ f, const double* __r
 }
 
 // ---------------------------------------------------------------- launchers
-static int grid_for(long long n, int threads, int cap)
-{
-    long long b = (n + threads - 1) / threads;
-    return (int)(b < 1 ? 1 : (b > cap ? cap : b));
-}
 
 __global__ void clock_set_kernel(uint32_t* clk, uint32_t v)
 {

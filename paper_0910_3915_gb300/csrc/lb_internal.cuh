@@ -119,11 +119,13 @@ struct Codec<__nv_bfloat16> {
 //   z*plane + (y + 1)*px + (x + gx),
 // with gx = 128 bytes of row padding on the left (so x = 0 starts a 128-byte
 // line) and at least one element on the right, and one ghost row above and
-// below each plane. Ghost column x = -1 mirrors x = nx-1, x = nx mirrors
-// x = 0, and likewise rows y = -1 and y = ny, so a tile plus its one-node
-// ring is one box even on the periodic edges. The step kernels write real
-// nodes only; the images are refreshed by a separate pass where a reader
-// needs them (the TMA-staged step).
+// below each plane. Ghost row y = -1 mirrors y = ny-1 and y = ny mirrors
+// y = 0, so a tile plus its one-node ring is one box across the periodic y
+// edges; the step kernels write real nodes only, and a row copy refreshes
+// the images where a reader needs them (the TMA-staged step, which takes the
+// periodic x images from strips of real columns instead). The initial
+// populations also fill ghost columns x = -1 and x = nx; nothing relies on
+// them afterwards.
 struct Layout {
     int nx, ny, nz, px, gx;
     long long plane, slot;

@@ -8,10 +8,10 @@
 // cp.async.bulk.tensor, completion tracked by one mbarrier per stage. The
 // compute warps reduce a landed plane to rho, j and psi out of shared memory
 // while the following planes are in flight, then collide and push the plane
-// below. Periodic x and y need no special case: the storage's ghost columns
-// and rows (kept current by every writer) make the tile plus ring one
-// 16-byte aligned box. Every wait is bounded: a wait that gives up writes an
-// error status, drains the CTA's copies in flight and leaves the kernel.
+// below. Periodic y comes from the storage's ghost rows (refreshed after each
+// step by a cheap row copy); periodic x from two 16-byte strips that the edge
+// tiles load beside the main box. Every wait is bounded: a wait that gives up
+// writes an error status, drains the CTA's copies in flight and leaves the kernel.
 #pragma once
 
 #include <cuda.h>
@@ -68,28 +68,45 @@ __device__ __forceinline__ void tma_load_5d(void* dst, const CUtensorMap* map, u
         : "memory");
 }
 
-// Geometry of one stage: the box [a][k][row][col] of 2 x 19 x (TY+2) x BX
-// elements; column c holds x = x0 - GX + c (16 bytes of columns left of the
-// tile, so the box starts on a 16-byte boundary), row r holds y = y0 - 1 + r.
+// Geometry of one stage: the main box [a][k][row][col] of 2 x 19 x (TY+2) x BX
+// elements, column c holding x = x0 - GX + c (16 bytes of columns left of the
+// tile, so the box starts on a 16-byte boundary), row r holding y = y0 - 1 + r;
+// then two strips [a][k][row][SX] of 16 bytes of columns each, loaded only by
+// the tiles at the x edges: the left strip holds the columns around
+// x = nx - 1 (the periodic image of x = -1), the right strip x = 0 .. SX - 1
+// (the image of x = nx). Rows y = -1 and y = ny come from the ghost rows.
 template <class S, int TY>
 struct TmaGeom {
     static constexpr int TX = 32, HX = TX + 2, HY = TY + 2;
     static constexpr int GX = ghost_x<S>();
     static constexpr int BX = sizeof(S) == 4 ? 40 : 48;  // >= 32 + 2 GX, a multiple of 16 bytes
-    static constexpr int STAGE_ELEMS = 2 * Q * HY * BX;
+    static constexpr int SX = GX;                        // strip width: 16 bytes of columns
+    static constexpr int MAIN_ELEMS = 2 * Q * HY * BX;
+    static constexpr int STRIP_BOX_ELEMS = 2 * Q * HY * SX;
+    static constexpr int STRIP_ELEMS = (STRIP_BOX_ELEMS * (int)sizeof(S) + 127) / 128 * 128 / (int)sizeof(S);
+    static constexpr int STAGE_ELEMS = MAIN_ELEMS + 2 * STRIP_ELEMS;
+    static constexpr uint32_t MAIN_BYTES = MAIN_ELEMS * sizeof(S);
+    static constexpr uint32_t STRIP_BOX_BYTES = STRIP_BOX_ELEMS * sizeof(S);
     static constexpr uint32_t STAGE_BYTES = STAGE_ELEMS * sizeof(S);
     static constexpr int PSI_FLOATS = 4 * 2 * HY * HX;
     static constexpr size_t smem(int NS) { return 128 + (size_t)NS * STAGE_BYTES + PSI_FLOATS * 4 + NS * 8; }
 };
 
+// Resident CTAs per SM the registers are held to (tau = 1): three CTAs of
+// 8-row tiles, five of 4-row tiles; other variants take the compiler's choice.
+template <int TY, bool kTauOne>
+constexpr int kTmaCtas = !kTauOne ? 1 : (TY == 8 ? 3 : (TY == 4 ? 5 : 1));
+
 template <class S, int TY, int NS, bool kTauOne>
-__global__ void __launch_bounds__(32 * TY) step_tma_kernel(const __grid_constant__ CUtensorMap tmap, const StepArgs<S> A)
+__global__ void __launch_bounds__(32 * TY, (kTmaCtas<TY, kTauOne>)) step_tma_kernel(const __grid_constant__ CUtensorMap tmap,
+                                                           const __grid_constant__ CUtensorMap tstrip,
+                                                           const StepArgs<S> A)
 {
     using G = TmaGeom<S, TY>;
-    constexpr int TX = 32, NT = TX * TY, HX = G::HX, HY = G::HY, GX = G::GX, BX = G::BX;
+    constexpr int TX = 32, NT = TX * TY, HX = G::HX, HY = G::HY, GX = G::GX, BX = G::BX, SX = G::SX;
     constexpr int RING = 2 * HX + 2 * TY;
     constexpr int NIT = (2 * RING + NT - 1) / NT;
-    static_assert(G::STAGE_BYTES % 128 == 0, "stages must stay 128-byte aligned");
+    static_assert(G::STAGE_BYTES % 128 == 0 && G::MAIN_BYTES % 128 == 0, "stages and strips stay 128-byte aligned");
 
     extern __shared__ unsigned char smem_raw[];
     unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
@@ -133,8 +150,18 @@ __global__ void __launch_bounds__(32 * TY) step_tma_kernel(const __grid_constant
         const bool active = ty < hgt;
         const bool valid = active && gx < nx;
         const int np = zb - za + 2;  // planes za-1 .. zb
+        // x edges: the periodic images come from the strips (column of x = nx - 1 in the left strip)
+        const bool left_edge = x0 == 0, right_edge = x0 + TX >= nx;
+        const int sl = (L.gx + nx - 1) / SX * SX, ol = L.gx + nx - 1 - sl;
+        // own node: the main box; lanes past x = nx - 1 of a ragged last tile
+        // hold the periodic images x - nx from the right strip (the one at
+        // x = nx is the +x neighbour of x = nx - 1), as far as the strip reaches
+        const bool own_strip = gx >= nx;
+        const bool own_rd = active && gx - nx < SX;
 
-        int it_sm[NIT], it_st[NIT], it_a[NIT];
+        // ring items: shared-memory position, stage position of slot 0 of the
+        // item's component, source (0 main box, 1 left strip, 2 right strip)
+        int it_sm[NIT], it_base[NIT], it_src[NIT], it_a[NIT];
 #pragma unroll
         for (int i = 0; i < NIT; ++i) {
             const int it = tid + i * NT;
@@ -148,7 +175,17 @@ __global__ void __launch_bounds__(32 * TY) step_tma_kernel(const __grid_constant
                 else { ix = HX - 1; iy = r - 2 * HX - TY + 1; }
                 if (r < 2 * HX || iy <= hgt) it_a[i] = a;  // side columns: the tile's own rows only
                 it_sm[i] = iy * HX + ix;
-                it_st[i] = iy * BX + ix - 1 + GX;
+                const int xr = x0 - 1 + ix;  // the ring node's x (unwrapped)
+                if (xr < 0) {
+                    it_src[i] = 1;  // x = -1: the image of x = nx - 1
+                    it_base[i] = G::MAIN_ELEMS + (a * Q * HY + iy) * SX + ol;
+                } else if (xr >= nx && xr - nx < SX) {
+                    it_src[i] = 2;  // x >= nx: the images of x - nx
+                    it_base[i] = G::MAIN_ELEMS + G::STRIP_ELEMS + (a * Q * HY + iy) * SX + xr - nx;
+                } else {
+                    it_src[i] = 0;
+                    it_base[i] = (a * Q * HY + iy) * BX + ix - 1 + GX;
+                }
             }
         }
 
@@ -157,9 +194,13 @@ __global__ void __launch_bounds__(32 * TY) step_tma_kernel(const __grid_constant
             if (zp == 0 || zp == nz - 1) {
                 mbar_arrive(b);  // a solid plane: nothing to load
             } else {
+                S* stg = stages + (size_t)(gi % NS) * G::STAGE_ELEMS;
                 fence_proxy_async();
-                mbar_expect_tx(b, G::STAGE_BYTES);
-                tma_load_5d(stages + (size_t)(gi % NS) * G::STAGE_ELEMS, &tmap, b, x0 + L.gx - GX, y0, zp, 0, 0);
+                mbar_expect_tx(b, G::MAIN_BYTES + (left_edge ? G::STRIP_BOX_BYTES : 0u) +
+                                      (right_edge ? G::STRIP_BOX_BYTES : 0u));
+                tma_load_5d(stg, &tmap, b, x0 + L.gx - GX, y0, zp, 0, 0);
+                if (left_edge) tma_load_5d(stg + G::MAIN_ELEMS, &tstrip, b, sl, y0, zp, 0, 0);
+                if (right_edge) tma_load_5d(stg + G::MAIN_ELEMS + G::STRIP_ELEMS, &tstrip, b, L.gx, y0, zp, 0, 0);
             }
         };
 
@@ -179,10 +220,17 @@ __global__ void __launch_bounds__(32 * TY) step_tma_kernel(const __grid_constant
                     rho[a] = 0.f;
                     m[a] = 0.f;
                     j[a][0] = j[a][1] = j[a][2] = 0.f;
-                    if (!solid && active) {
+                    if (!solid && own_rd) {
                         float w[Q];
+                        if (!own_strip) {
+                            const S* so = st + (a * Q * HY + ty + 1) * BX + tx + GX;
 #pragma unroll
-                        for (int k = 0; k < Q; ++k) w[k] = Codec<S>::val(st[((a * Q + k) * HY + ty + 1) * BX + tx + GX]);
+                            for (int k = 0; k < Q; ++k) w[k] = Codec<S>::val(so[k * HY * BX]);
+                        } else {
+                            const S* so = st + G::MAIN_ELEMS + G::STRIP_ELEMS + (a * Q * HY + ty + 1) * SX + gx - nx;
+#pragma unroll
+                            for (int k = 0; k < Q; ++k) w[k] = Codec<S>::val(so[k * HY * SX]);
+                        }
                         rho[a] = rho_of<S>(w, ref[a], &m[a]);
                         mom_of<S>(w, j[a]);
                         ps = psi_of(rho[a]);
@@ -200,8 +248,14 @@ __global__ void __launch_bounds__(32 * TY) step_tma_kernel(const __grid_constant
                     float ps = eta[a];
                     if (!solid) {
                         float w[Q];
+                        const S* si = st + it_base[q];
+                        if (it_src[q] == 0) {
 #pragma unroll
-                        for (int k = 0; k < Q; ++k) w[k] = Codec<S>::val(st[(a * Q + k) * HY * BX + it_st[q]]);
+                            for (int k = 0; k < Q; ++k) w[k] = Codec<S>::val(si[k * HY * BX]);
+                        } else {
+#pragma unroll
+                            for (int k = 0; k < Q; ++k) w[k] = Codec<S>::val(si[k * HY * SX]);
+                        }
                         ps = psi_of(rho_of<S>(w, ref[a]));
                     }
                     spl[a * HY * HX + it_sm[q]] = ps;
@@ -268,11 +322,11 @@ __global__ void __launch_bounds__(32 * TY) step_tma_kernel(const __grid_constant
 }
 
 template <class S, int TY, int NS, bool T1>
-static cudaError_t tma_launch_one(const CUtensorMap& m, const StepArgs<S>& A, cudaStream_t st)
+static cudaError_t tma_launch_one(const CUtensorMap* m, const StepArgs<S>& A, cudaStream_t st)
 {
     const size_t smem = TmaGeom<S, TY>::smem(NS);
     const int items = A.tiles_x * A.tiles_y * A.nseg;
-    step_tma_kernel<S, TY, NS, T1><<<items, 32 * TY, smem, st>>>(m, A);
+    step_tma_kernel<S, TY, NS, T1><<<items, 32 * TY, smem, st>>>(m[0], m[1], A);
     return cudaGetLastError();
 }
 
@@ -301,8 +355,8 @@ static long long tma_dispatch(int op, int ty, int ns, bool t1, const CUtensorMap
 {
 #define LBSC_TMA_CASE(TY_, NS_)                                                                       \
     if (ty == TY_ && ns == NS_) {                                                                     \
-        if (op == 0) return t1 ? tma_launch_one<S, TY_, NS_, true>(*m, *A, st)                        \
-                               : tma_launch_one<S, TY_, NS_, false>(*m, *A, st);                      \
+        if (op == 0) return t1 ? tma_launch_one<S, TY_, NS_, true>(m, *A, st)                         \
+                               : tma_launch_one<S, TY_, NS_, false>(m, *A, st);                       \
         if (op == 1) {                                                                                \
             cudaError_t e = tma_prepare_one<S, TY_, NS_, true>();                                     \
             return e != cudaSuccess ? e : tma_prepare_one<S, TY_, NS_, false>();                      \
