@@ -82,7 +82,7 @@ def peaks():
         return 6800.0, "fallback"
 
 
-STEP_SOURCES = ("step.cu", "step_common.cuh", "lb_internal.cuh")
+STEP_SOURCES = ("step.cu", "step_common.cuh", "lb_internal.cuh", "step_tma.cuh")
 
 
 def step_source_sha256() -> str:
