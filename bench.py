@@ -384,20 +384,11 @@ def run_sweep(args):
     stream = torch.cuda.current_stream()
     ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
 
+    from paper_0910_3915_gb300 import tune
+
     batch = lbsc.Batch(fields, params, wl["precision"])
-    best = None
-    for ty, planes in ((8, 32), (8, 16), (4, 32), (16, 32), (8, 64)):
-        batch.set_schedule(ty, planes)
-        batch.step(64)
-        a, b = ev(), ev()
-        a.record(stream)
-        batch.step(64)
-        b.record(stream)
-        b.synchronize()
-        t = a.elapsed_time(b)
-        if best is None or t < best[0]:
-            best = (t, ty, planes)
-    batch.set_schedule(best[1], best[2])
+    (b_ty, b_planes), _ = tune.tune_batch(batch)
+    best = (None, b_ty, b_planes)
     batch.step(Wm)
     torch.cuda.synchronize()
     t0, t1 = ev(), ev()

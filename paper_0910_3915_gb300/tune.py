@@ -114,3 +114,34 @@ def tune(lat, steps: int = 128, segments=SEGMENTS, cache: str | None = None):
         with open(cache, "w") as f:
             json.dump(table, f, indent=1)
     return best, timings
+
+
+BATCH_CANDIDATES = ((8, 32), (8, 16), (4, 32), (16, 32), (8, 64))  # (tile height, planes per work item)
+
+
+def tune_batch(batch, steps: int = 64, candidates=BATCH_CANDIDATES):
+    """Pick the fastest (tile_y, planes_per_item) for a Batch's persistent
+    kernel by timing each on the batch itself; every box's state (and step
+    count) is saved before and restored after. Returns (best, table)."""
+    import torch
+
+    saved = [batch.box(i).save() for i in range(batch.n)]
+    stream = torch.cuda.current_stream()
+    table = {}
+    for ty, planes in candidates:
+        batch.set_schedule(ty, planes)
+        batch.step(steps)  # warm-up, graph capture
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        batch.step(steps)
+        e1.record(stream)
+        e1.synchronize()
+        table[f"{ty}:{planes}"] = e0.elapsed_time(e1) / steps
+    for i, st in enumerate(saved):
+        batch.box(i).load(st)
+    best_key = min(table, key=table.get)
+    best = tuple(int(v) for v in best_key.split(":"))
+    batch.set_schedule(*best)
+    return best, table

@@ -157,3 +157,39 @@ def test_young_planar_tensions_match_oracle(lbsc):
     tg = lbsc.young_theta(out["gas"][0], out["liquid"][0], lg[0])
     to = oracle.young_theta(out["gas"][1], out["liquid"][1], lg[1])
     assert abs(tg - to) < 0.1 and tg > 90.0
+
+
+def test_laplace_law_free_droplets_3d(lbsc):
+    """Free droplets in a periodic box (Sec. 4.2 set-up, on the GPU): the
+    pressure jump is linear in 1/R with no intercept, its slope is twice the
+    planar surface tension (Eq. gammaMechDef on two lamellae) within 15%, and
+    the radial tension of the largest drop (Eq. mechRadGamma) agrees with the
+    planar one within 10%."""
+    n, steps = 48, 4000
+    c = (n / 2, n / 2, n / 2)
+    inv_r, dp = [], []
+    for R in (8.0, 10.0, 12.0, 14.0):
+        rr, rb = W.droplet_fields(n, n, n, R, seed=1, centre=c)
+        lat = lbsc.Lattice(rr, rb).set_geometry(W.periodic_mask(n, n, n)).set_params(**CONTACT)
+        lat.step(steps)
+        P = lat.pressure_tensor()
+        r, b, _, _ = lat.moments()
+        p = (P[0] + P[1] + P[2]) / 3
+        dp.append(p[n // 2, n // 2, n // 2] - p[0, 0, 0])
+        inv_r.append(1.0 / (3.0 * float(((r - b) > 0).sum()) / (4.0 * math.pi)) ** (1.0 / 3.0))
+        if R == 14.0:
+            _, g_rad, R_s = lat.pressure_radial(c, 1.0, n // 2, 0.0, n / 2 - 5)
+        lat.close()
+    inv_r, dp = np.array(inv_r), np.array(dp)
+    slope, icpt = np.polyfit(inv_r, dp, 1)
+    fit = slope * inv_r + icpt
+    r2 = 1 - ((dp - fit) ** 2).sum() / ((dp - dp.mean()) ** 2).sum()
+    assert r2 > 0.99 and abs(icpt) < 0.1 * dp.max()
+    rr, rb = W.lamella_fields(4, 4, 64)
+    lam = lbsc.Lattice(rr, rb).set_geometry(W.periodic_mask(4, 4, 64)).set_params(**CONTACT)
+    lam.step(steps)
+    gamma = 0.5 * lam.pressure_profile()[1]
+    lam.close()
+    assert gamma > 0
+    assert math.isclose(slope / 2, gamma, rel_tol=0.15), (slope / 2, gamma)
+    assert math.isclose(g_rad, gamma, rel_tol=0.10) and abs(R_s - 1 / inv_r[-1]) < 1.0, (g_rad, gamma, R_s)
