@@ -443,12 +443,11 @@ def cap_centroid_height(volume: float, theta_deg: float) -> float:
 
 
 def run_adjoint(args):
-    """Adjoint throughput, a check against FP64 oracle finite differences, and
-    calibration of the wall parameter to target contact angles."""
+    """Adjoint throughput, a check against finite differences of the same
+    observable, and calibration of the wall parameter to target contact angles."""
     import numpy as np
     import torch
 
-    import oracle
     from paper_0910_3915_gb300 import lbsc
     from paper_0910_3915_gb300 import workloads as W
 
@@ -472,23 +471,24 @@ def run_adjoint(args):
     lat.sync()
     fwd_s = time.perf_counter() - t
 
-    # FP64 oracle central differences (h = 1e-4) of the same observable, 200 steps
-    Tc, h = 200, 1e-4
+    # central differences of the same observable on the GPU (FP32, h = 1e-2), 200 steps; the
+    # check against FP64 oracle differences is a test (tests/test_gpu_adjoint.py)
+    Tc, h = 200, 1e-2
     lat.load(s0)
     Jc, gc = lat.step_backward(Tc, ck)
 
-    def oJ(prm):
-        st = oracle.State(rr, rb, W.wall_mask(nx, ny, nz), oracle.Params(**prm)).step(Tc)
-        r, b, _, _ = st.moments()
-        w = 1.0 / (1.0 + np.exp(-(r - b) / 0.05))
-        zz = np.arange(nz)[:, None, None] - 0.5 + 0 * r
-        return float((zz * w)[1:-1].sum() / w[1:-1].sum())
+    def gJ(prm):
+        lat.load(s0)
+        lat.set_params(**prm)
+        lat.step(Tc)
+        return lat.observable("com_soft")
 
     fd = []
     for comp in ("eta_wall_r", "eta_wall_b"):
-        jp = oJ(dict(CONTACT, **{comp: h}))
-        jm = oJ(dict(CONTACT, **{comp: -h}))
+        jp = gJ(dict(CONTACT, **{comp: h}))
+        jm = gJ(dict(CONTACT, **{comp: -h}))
         fd.append((jp - jm) / (2 * h))
+    lat.set_params(**CONTACT)
     fd_err = float(np.max(np.abs(np.array(gc) - fd)) / np.max(np.abs(fd)))
 
     # calibration: Newton steps on J(w) = J*(theta*) with dJ/dw from the adjoint
@@ -526,7 +526,7 @@ def run_adjoint(args):
         "adjoint_seconds": round(adj_s, 3), "forward_seconds": round(fwd_s, 3),
         "adjoint_over_forward": round(adj_s / fwd_s, 2),
         "gradient": [float(g0[0]), float(g0[1])], "J": J0,
-        "fd_check": {"steps": Tc, "h": h, "adjoint": [float(gc[0]), float(gc[1])], "oracle_fd": fd,
+        "fd_check": {"steps": Tc, "h": h, "adjoint": [float(gc[0]), float(gc[1])], "gpu_fd": fd,
                      "max_rel_err": fd_err},
         "calibration": calib,
     }
@@ -697,11 +697,10 @@ def run_young(args):
 
 
 def precision_accuracy(prec: str, steps: int):
-    """16-bit storage against FP32 on the full lattice, and against the FP64 oracle on the
-    64x64x32 copy (same set-up scaled by 1/4)."""
+    """16-bit storage against FP32 on the full lattice (the comparison with the
+    FP64 oracle on the 64x64x32 copy is a test: tests/test_gpu_parity.py)."""
     import numpy as np
 
-    import oracle
     from paper_0910_3915_gb300 import lbsc
     from paper_0910_3915_gb300 import workloads as W
 
@@ -727,22 +726,6 @@ def precision_accuracy(prec: str, steps: int):
                                   "theta_err_deg": abs(res[prec][2]["theta_deg"] - res["f32"][2]["theta_deg"]),
                                   "mass_drift": [float(v) for v in res[prec][3]],
                                   "mass_drift_fp32": [float(v) for v in res["f32"][3]]}
-    # 64x64x32 copy against the FP64 oracle
-    nx, ny, nz, S = 64, 64, 32, 1000
-    rr, rb = W.droplet_fields(nx, ny, nz, 15.0, seed=0)
-    st = oracle.State(rr, rb, W.wall_mask(nx, ny, nz), oracle.Params(**prm)).step(S)
-    orr, orb, _, _ = st.moments()
-    oca = oracle.contact_angle(orr, orb, st.solid, 3.0)
-    for p in ("f32", prec):
-        lat = lbsc.Lattice(rr, rb, p).set_params(**prm)
-        lat.step(S)
-        r, b, _, _ = lat.moments()
-        ca = lat.contact_angle(3.0)
-        lat.close()
-        e = max(float(np.max(np.abs((r, b)[k][fl] - (orr, orb)[k][fl]) / np.abs((orr, orb)[k][fl]))) for k in (0, 1))
-        out[f"vs_oracle_64x64x32_{p}"] = {"steps": S, "max_rel_density_err": e, "theta": ca["theta_deg"],
-                                          "theta_oracle": oca["theta_deg"],
-                                          "theta_err_deg": abs(ca["theta_deg"] - oca["theta_deg"])}
     return out
 
 

@@ -337,6 +337,38 @@ def test_16bit_storage_contact_angle_within_one_degree(lbsc, precision):
         assert abs(cons[a] - m0[a]) < 5 * sigma, (a, cons[a] - m0[a], sigma)
 
 
+@pytest.fixture(scope="module")
+def quarter_scale_oracle():
+    """The 256x256x128 R = 60 precision workload scaled by 1/4 (64x64x32,
+    R = 15, w = 0.05), run 1000 steps by the FP64 oracle."""
+    nx, ny, nz, S = 64, 64, 32, 1000
+    rr, rb = W.droplet_fields(nx, ny, nz, 15.0, seed=0)
+    er, eb = W.wall_split(0.05)
+    prm = dict(CONTACT, eta_wall_r=er, eta_wall_b=eb)
+    st = oracle.State(rr, rb, W.wall_mask(nx, ny, nz), oracle.Params(**prm)).step(S)
+    r, b, _, _ = st.moments()
+    return rr, rb, prm, S, r, b, oracle.contact_angle(r, b, st.solid, 3.0)
+
+
+@pytest.mark.parametrize("precision,rho_tol", [("f32", 1e-5), ("f16", 3e-2), ("bf16", 0.15)])
+def test_precision_workload_quarter_scale_against_oracle(lbsc, quarter_scale_oracle, precision, rho_tol):
+    """16-bit storage on the quarter-scale copy of the precision workload: the
+    contact angle within 1 deg of the FP64 oracle's (0.5 deg for FP32), and the
+    per-node density error within the storage's resolution (the largest errors
+    sit in the interface, where rho changes by its whole range over a few nodes)."""
+    rr, rb, prm, S, orr, orb, oca = quarter_scale_oracle
+    lat = lbsc.Lattice(rr, rb, precision).set_params(**prm)
+    lat.step(S)
+    r, b, _, _ = lat.moments()
+    ca = lat.contact_angle(3.0)
+    lat.close()
+    fl = W.wall_mask(*rr.shape[::-1]) == 0
+    err = max(float(np.max(np.abs(g - o)[fl] / np.abs(o)[fl])) for g, o in ((r, orr), (b, orb)))
+    assert err <= rho_tol, err
+    assert ca["ok"] == 1 and oca["ok"] == 1
+    assert abs(ca["theta_deg"] - oca["theta_deg"]) < (0.5 if precision == "f32" else 1.0)
+
+
 # --------------------------------------------------------------- full size, sampled
 def _oracle_node_update(n_t, solid, prm, z, y, x):
     """The oracle's step on the 5x5x5 neighbourhood of (z, y, x) (clipped at solid
