@@ -80,15 +80,13 @@ static int cuda_fail(lb_ctx* c, cudaError_t e, const char* where)
 static size_t elem_size(int prec) { return prec == LB_F32 ? 4 : 2; }
 static size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
-static size_t elem_size_of(int prec) { return prec == LB_F32 ? 4 : 2; }
-
-// rows of nx nodes behind 128 bytes of left padding (x = 0 starts a line; the
-// ghost column x = -1 is its last element), at least one ghost column on the
-// right, pitch a multiple of 128 bytes; one ghost row above and below each plane
+// rows of nx nodes behind 128 bytes of left padding (x = 0 starts a line), at
+// least one element of padding on the right, pitch a multiple of 128 bytes;
+// one ghost row above and below each plane
 static Layout make_layout(int nx, int ny, int nz, int prec)
 {
     Layout L;
-    const int line = (int)(128 / elem_size_of(prec));
+    const int line = (int)(128 / elem_size(prec));
     L.nx = nx;
     L.ny = ny;
     L.nz = nz;
@@ -248,15 +246,16 @@ static EncodeTiledFn encode_fn()
     return fn;
 }
 
-// 5-D map over a population buffer: (x incl. ghosts, y incl. ghost rows, z, k, a);
-// box = tile of 32 + 2*ghost columns, TY + 2 rows, one plane, all 38 slots
+// 5-D maps over a population buffer: (x incl. padding, y incl. ghost rows, z, k, a);
+// main box = the 32-node tile plus 16 bytes of columns on each side, TY + 2 rows,
+// one plane, all 38 slots; strip box = 16 bytes of columns (the x-edge images)
 static int tensor_map(lb_ctx* c, int buf, int ty)
 {
     const int ti = tile_index(ty);
     if (c->tmap_ok[buf][ti]) return LB_OK;
     EncodeTiledFn enc = encode_fn();
     if (!enc) return fail(c, LB_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
-    const size_t es = elem_size_of(c->prec);
+    const size_t es = elem_size(c->prec);
     const Layout& L = c->L;
     const cuuint64_t dims[5] = {(cuuint64_t)L.px, (cuuint64_t)(L.ny + 2), (cuuint64_t)L.nz, (cuuint64_t)Q, 2};
     const cuuint64_t strides[4] = {(cuuint64_t)L.px * es, (cuuint64_t)L.plane * es, (cuuint64_t)L.slot * es,
@@ -297,6 +296,7 @@ static StepArgs<S> step_args(lb_ctx* c, int src)
     return A;
 }
 
+// the ghost rows of buffer `buf` (read by the TMA-staged step)
 template <class S>
 static cudaError_t refresh_ghosts(lb_ctx* c, int buf, cudaStream_t st)
 {
