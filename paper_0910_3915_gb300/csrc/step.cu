@@ -132,7 +132,9 @@ __device__ __forceinline__ void step_item(const StepArgs<S>& A, int col, int za,
         for (int i = 0; i < NIT; ++i) {
             if (it_a[i] < 0) continue;
             const int a = it_a[i];
-            spl[a * HY * HX + it_sm[i]] = si_[i] ? eta[a] : psi_of(rho_of<S>(ri_[i], ref[a]));
+            // select, not index: a runtime index would put eta and ref in local memory
+            const float eta_a = a ? eta[1] : eta[0], ref_a = a ? ref[1] : ref[0];
+            spl[a * HY * HX + it_sm[i]] = si_[i] ? eta_a : psi_of(rho_of<S>(ri_[i], ref_a));
         }
     };
 

@@ -245,7 +245,9 @@ __global__ void __launch_bounds__(32 * TY, (kTmaCtas<TY, kTauOne>)) step_tma_ker
                 for (int q = 0; q < NIT; ++q) {
                     if (it_a[q] < 0) continue;
                     const int a = it_a[q];
-                    float ps = eta[a];
+                    // select, not index: a runtime index would put eta and ref in local memory
+                    const float ref_a = a ? ref[1] : ref[0];
+                    float ps = a ? eta[1] : eta[0];
                     if (!solid) {
                         float w[Q];
                         const S* si = st + it_base[q];
@@ -256,7 +258,7 @@ __global__ void __launch_bounds__(32 * TY, (kTmaCtas<TY, kTauOne>)) step_tma_ker
 #pragma unroll
                             for (int k = 0; k < Q; ++k) w[k] = Codec<S>::val(si[k * HY * SX]);
                         }
-                        ps = psi_of(rho_of<S>(w, ref[a]));
+                        ps = psi_of(rho_of<S>(w, ref_a));
                     }
                     spl[a * HY * HX + it_sm[q]] = ps;
                 }
