@@ -41,19 +41,23 @@ __device__ __forceinline__ void block_reduce(double (&acc)[NV], uint32_t is_max,
     }
 }
 
-// Sum (or max) nblocks partial rows of NV values in block order.
+// Sum (or max) nblocks partial rows of NV values: thread t takes rows t,
+// t + kRedThreads, ... in order, then the fixed warp and block tree of
+// block_reduce. Launched as one block of kRedThreads threads.
 template <int NV>
-__global__ void finish_kernel(const double* __restrict__ part, int nblocks, uint32_t is_max, double* __restrict__ out)
+__global__ void __launch_bounds__(kRedThreads) finish_kernel(const double* __restrict__ part, int nblocks,
+                                                             uint32_t is_max, double* __restrict__ out)
 {
-    const int i = threadIdx.x;
-    if (i >= NV) return;
-    const bool mx = (is_max >> i) & 1u;
-    double v = mx ? -1e300 : 0.0;
-    for (int b = 0; b < nblocks; ++b) {
-        const double p = part[(long long)b * NV + i];
-        v = mx ? fmax(v, p) : v + p;
-    }
-    out[i] = v;
+    double acc[NV];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) acc[i] = ((is_max >> i) & 1u) ? -1e300 : 0.0;
+    for (int b = threadIdx.x; b < nblocks; b += kRedThreads)
+#pragma unroll
+        for (int i = 0; i < NV; ++i) {
+            const double p = part[(long long)b * NV + i];
+            acc[i] = ((is_max >> i) & 1u) ? fmax(acc[i], p) : acc[i] + p;
+        }
+    block_reduce<NV>(acc, is_max, out);
 }
 
 // blocks for n items at `threads` per block, at most cap (grid-stride loops cover the rest)
@@ -99,32 +103,48 @@ __global__ void init_kernel(FieldArgs F, S* __restrict__ f, const double* __rest
 
 // ---------------------------------------------------------------- conservation
 // cons = {M_r, M_b, Px, Py, Pz, non-finite count, fluid nodes, -}
+// Warp w of the fixed grid takes lattice rows (y, z) = w, w + nwarps, ...;
+// its lanes step along x. A node's mass and momentum are summed in FP32 over
+// its 19 values, then added into per-thread FP64 sums (two masses and the
+// total momentum: five FP64 additions a node); the counts stay integers.
 template <class S>
 __global__ void __launch_bounds__(kRedThreads) cons_kernel(FieldArgs F, const S* __restrict__ f, double* __restrict__ part)
 {
     double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    const long long N = (long long)F.L.nx * F.L.ny * F.L.nz;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
-        const int x = (int)(i % F.L.nx), y = (int)((i / F.L.nx) % F.L.ny), z = (int)(i / ((long long)F.L.nx * F.L.ny));
-        const long long off = F.L.off(x, y, z);
-        if (node_solid(F, x, y, z, off)) continue;
-        acc[6] += 1.0;
-        for (int a = 0; a < 2; ++a) {
-            float rho = 0.f, j[3] = {0.f, 0.f, 0.f};
-            for (int k = 0; k < Q; ++k) {
-                const float n = decode<S>(f + (long long)(a * Q + k) * F.L.slot + off, k, F.P.ref[a]);
-                if (!isfinite(n)) acc[5] += 1.0;
-                rho += n;
-                j[0] += cx(k) * n;
-                j[1] += cy(k) * n;
-                j[2] += cz(k) * n;
+    int bad = 0, fluid = 0;
+    const int nx = F.L.nx, ny = F.L.ny, rows = F.L.ny * F.L.nz;
+    const int lane = threadIdx.x & 31;
+    const int nwarps = gridDim.x * (kRedThreads / 32);
+    for (int r = blockIdx.x * (kRedThreads / 32) + (threadIdx.x >> 5); r < rows; r += nwarps) {
+        const int y = r % ny, z = r / ny;
+        for (int x = lane; x < nx; x += 32) {
+            const long long off = F.L.off(x, y, z);
+            if (node_solid(F, x, y, z, off)) continue;
+            ++fluid;
+            float rho[2], j[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+            for (int a = 0; a < 2; ++a) {
+                float m = 0.f;
+#pragma unroll
+                for (int k = 0; k < Q; ++k) {
+                    const float n = decode<S>(f + (long long)(a * Q + k) * F.L.slot + off, k, F.P.ref[a]);
+                    bad += isfinite(n) ? 0 : 1;
+                    m += n;
+                    if (cx(k)) j[0] += cx(k) * n;
+                    if (cy(k)) j[1] += cy(k) * n;
+                    if (cz(k)) j[2] += cz(k) * n;
+                }
+                rho[a] = m;
             }
-            acc[a] += rho;
+            acc[0] += rho[0];
+            acc[1] += rho[1];
             acc[2] += j[0];
             acc[3] += j[1];
             acc[4] += j[2];
         }
     }
+    acc[5] = bad;
+    acc[6] = fluid;
     block_reduce<8>(acc, 0u, part);
 }
 
@@ -471,7 +491,7 @@ template <class S>
 cudaError_t launch_conservation(const FieldArgs& F, const S* f, double* part, double* out, cudaStream_t st)
 {
     cons_kernel<S><<<kRedBlocks, kRedThreads, 0, st>>>(F, f, part);
-    finish_kernel<8><<<1, 32, 0, st>>>(part, kRedBlocks, 0u, out);
+    finish_kernel<8><<<1, kRedThreads, 0, st>>>(part, kRedBlocks, 0u, out);
     return cudaGetLastError();
 }
 
@@ -488,7 +508,7 @@ cudaError_t launch_angle(const FieldArgs& F, const Scratch& W, double zref, doub
                          cudaStream_t st)
 {
     angle_kernel<<<kRedBlocks, kRedThreads, 0, st>>>(F, W, zref, level, part);
-    finish_kernel<kAngleVals><<<1, 32, 0, st>>>(part, kRedBlocks, 1u, out);
+    finish_kernel<kAngleVals><<<1, kRedThreads, 0, st>>>(part, kRedBlocks, 1u, out);
     return cudaGetLastError();
 }
 

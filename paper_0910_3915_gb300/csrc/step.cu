@@ -111,22 +111,24 @@ __device__ __forceinline__ void step_item(const StepArgs<S>& A, int col, int za,
     // reduce the raw registers of plane zp: psi into its ring slot, own moments out
     auto reduce = [&](int zp, float (&rho)[2], float (&j)[2][3], float (&v)[2][Q], float (&m)[2]) {
         float* spl = &sp[zp & 3][0][0][0];
+        float ps[2] = {eta[0], eta[1]};
+        rho[0] = rho[1] = m[0] = m[1] = 0.f;
 #pragma unroll
-        for (int a = 0; a < 2; ++a) {
-            float ps = eta[a];
-            rho[a] = 0.f;
-            m[a] = 0.f;
-            j[a][0] = j[a][1] = j[a][2] = 0.f;
-            if (!so_) {
-                rho[a] = rho_of<S>(ro_[a], ref[a], &m[a]);
-                mom_of<S>(ro_[a], j[a]);
-                ps = psi_of(rho[a]);
-                if constexpr (!kTauOne) {
+        for (int a = 0; a < 2; ++a) j[a][0] = j[a][1] = j[a][2] = 0.f;
+        if (!so_) {
+            moments2<S>(ro_, ref, rho, j, m);
+            ps[0] = psi_of(rho[0]);
+            ps[1] = psi_of(rho[1]);
+            if constexpr (!kTauOne) {
+#pragma unroll
+                for (int a = 0; a < 2; ++a)
 #pragma unroll
                     for (int k = 0; k < Q; ++k) v[a][k] = ro_[a][k];
-                }
             }
-            if (active) spl[(a * HY + ty + 1) * HX + tx + 1] = ps;
+        }
+        if (active) {
+            spl[(ty + 1) * HX + tx + 1] = ps[0];
+            spl[(HY + ty + 1) * HX + tx + 1] = ps[1];
         }
 #pragma unroll
         for (int i = 0; i < NIT; ++i) {

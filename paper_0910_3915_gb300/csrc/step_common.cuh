@@ -9,9 +9,33 @@
 
 namespace lbsc {
 
+// The two components go through the same arithmetic, so a node's moments,
+// force and collision run on (red, blue) pairs in the packed FP32
+// instructions (FADD2/FMUL2/FFMA2): each lane rounds exactly as the scalar
+// operation would, so pairing halves the instruction count without changing
+// a value. Subtraction is a fused multiply-add with -1 (exact product, one
+// rounding).
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 sp2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, sp2(-1.0f), a); }
+__device__ __forceinline__ float2 neg2(float2 a) { return __fmul2_rn(a, sp2(-1.0f)); }
+
+// Accumulate signed terms into a sum that starts with its first term
+// (whose sign is positive for every sum formed here).
+__device__ __forceinline__ void acc_signed(float2& acc, bool& has, float2 t, int sign)
+{
+    if (!has) acc = sign > 0 ? t : neg2(t);
+    else acc = sign > 0 ? add2(acc, t) : sub2(acc, t);
+    has = true;
+}
+
 // rho of one component from its 19 stored values v_k: FP32 stores n_k;
-// 16-bit formats store e_k with n_k = zeta_k (rho_ref + e_k). The same routine
-// serves a tile's own nodes and its ring, so both see bit-identical rho.
+// 16-bit formats store e_k with n_k = zeta_k (rho_ref + e_k). This routine
+// (for a tile's ring) and moments2 (for the tile's own nodes) perform the
+// same operations in the same order, so both see bit-identical rho.
 //
 // For 16-bit storage, m36 = 36 (rho - rho_ref) = 12 e_0 + 2 sum_axis e_k + sum_diag e_k
 // is also returned: the values are 16-bit numbers, so these FP32 sums are exact
@@ -21,44 +45,63 @@ template <class S>
 __device__ __forceinline__ float rho_of(const float (&v)[Q], float ref, float* m36 = nullptr)
 {
     // opposite velocities come in pairs (k, k+1), k odd: sum each pair first
+    const float ax = ((v[1] + v[2]) + (v[3] + v[4])) + (v[5] + v[6]);
+    const float di = (((v[7] + v[8]) + (v[9] + v[10])) + ((v[11] + v[12]) + (v[13] + v[14]))) +
+                     ((v[15] + v[16]) + (v[17] + v[18]));
     if constexpr (Codec<S>::kDeviation) {
-        const float ax = ((v[1] + v[2]) + (v[3] + v[4])) + (v[5] + v[6]);
-        const float di = (((v[7] + v[8]) + (v[9] + v[10])) + ((v[11] + v[12]) + (v[13] + v[14]))) +
-                         ((v[15] + v[16]) + (v[17] + v[18]));
         const float m = fmaf(12.0f, v[0], fmaf(2.0f, ax, di));
         if (m36) *m36 = m;
-        return ref + m * (1.0f / 36.0f);
+        return fmaf(m, 1.0f / 36.0f, ref);
     } else {
-        const float ax = ((v[1] + v[2]) + (v[3] + v[4])) + (v[5] + v[6]);
-        const float di = (((v[7] + v[8]) + (v[9] + v[10])) + ((v[11] + v[12]) + (v[13] + v[14]))) +
-                         ((v[15] + v[16]) + (v[17] + v[18]));
         return (v[0] + ax) + di;
     }
 }
 
-// j = sum_k n_k c_k, from the differences of opposite pairs: d = n_k - n_kbar
-// (k odd), j = sum over pairs of c_k d
+// Both components' rho (as rho_of), m36 (16-bit storage) and
+// j = sum_k n_k c_k, the latter from the differences of opposite pairs:
+// d = n_k - n_kbar (k odd), j = sum over pairs of c_k d.
 template <class S>
-__device__ __forceinline__ void mom_of(const float (&v)[Q], float (&j)[3])
+__device__ __forceinline__ void moments2(const float (&v)[2][Q], const float (&ref)[2], float (&rho)[2],
+                                         float (&j)[2][3], float (&m36)[2])
 {
-    float d[Q / 2 + 1];
+    float2 p[Q];
 #pragma unroll
-    for (int k = 1; k < Q; k += 2) d[(k + 1) / 2] = v[k] - v[k + 1];
-    float ax[3] = {0.f, 0.f, 0.f}, di[3] = {0.f, 0.f, 0.f};
+    for (int k = 0; k < Q; ++k) p[k] = f2(v[0][k], v[1][k]);
+    const float2 ax = add2(add2(add2(p[1], p[2]), add2(p[3], p[4])), add2(p[5], p[6]));
+    const float2 di = add2(add2(add2(add2(p[7], p[8]), add2(p[9], p[10])), add2(add2(p[11], p[12]), add2(p[13], p[14]))),
+                           add2(add2(p[15], p[16]), add2(p[17], p[18])));
+    float2 r, m = sp2(0.f);
+    if constexpr (Codec<S>::kDeviation) {
+        m = fma2(sp2(12.0f), p[0], fma2(sp2(2.0f), ax, di));
+        r = fma2(m, sp2(1.0f / 36.0f), f2(ref[0], ref[1]));
+    } else {
+        r = add2(add2(p[0], ax), di);
+    }
+    rho[0] = r.x;
+    rho[1] = r.y;
+    m36[0] = m.x;
+    m36[1] = m.y;
+
+    float2 jax[3], jdi[3];
+    bool hax[3] = {false, false, false}, hdi[3] = {false, false, false};
 #pragma unroll
     for (int k = 1; k < Q; k += 2) {
-        const float dk = d[(k + 1) / 2];
-        float* acc = is_axis(k) ? ax : di;
-        if (cx(k)) acc[0] = cx(k) > 0 ? acc[0] + dk : acc[0] - dk;
-        if (cy(k)) acc[1] = cy(k) > 0 ? acc[1] + dk : acc[1] - dk;
-        if (cz(k)) acc[2] = cz(k) > 0 ? acc[2] + dk : acc[2] - dk;
+        const float2 dk = sub2(p[k], p[k + 1]);
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            const int c = q == 0 ? cx(k) : (q == 1 ? cy(k) : cz(k));
+            if (!c) continue;
+            if (is_axis(k)) acc_signed(jax[q], hax[q], dk, c);
+            else acc_signed(jdi[q], hdi[q], dk, c);
+        }
     }
-    if constexpr (Codec<S>::kDeviation) {
 #pragma unroll
-        for (int q = 0; q < 3; ++q) j[q] = ax[q] * (1.0f / 18.0f) + di[q] * (1.0f / 36.0f);
-    } else {
-#pragma unroll
-        for (int q = 0; q < 3; ++q) j[q] = ax[q] + di[q];
+    for (int q = 0; q < 3; ++q) {
+        float2 jq;
+        if constexpr (Codec<S>::kDeviation) jq = fma2(jax[q], sp2(1.0f / 18.0f), mul2(jdi[q], sp2(1.0f / 36.0f)));
+        else jq = add2(jax[q], jdi[q]);
+        j[0][q] = jq.x;
+        j[1][q] = jq.y;
     }
 }
 
@@ -68,30 +111,37 @@ __device__ __forceinline__ float psi_of(float rho) { return -expm1f(-rho); }
 // Eq. SCforce on the psi ring: s0, s1, s2 are the planes z-1, z, z+1 of a
 // [2][HY][HX] psi array, the node at row ty+1, column tx+1.
 // S^a = sum_k G_k psi^abar(x + c_k) c_k ;  F^a = -g kappa psi^a(x) S^a
+// Pairs hold (psi^b, psi^r) at each neighbour: lane a sums psi^abar.
 template <int HX, int HY>
 __device__ __forceinline__ void sc_force(const float* s0, const float* s1, const float* s2, int ty, int tx, float gk,
                                          float Gax, float Gdi, float (&F)[2][3])
 {
+    auto psi_at = [&](int k) {
+        const float* sl = cz(k) < 0 ? s0 : (cz(k) > 0 ? s2 : s1);
+        const int o = (ty + 1 + cy(k)) * HX + tx + 1 + cx(k);
+        return f2(sl[HY * HX + o], sl[o]);
+    };
+    // opposite neighbours in pairs: psi(x + c_k) - psi(x - c_k), k odd
+    float2 ax[3], di[3];
+    bool hax[3] = {false, false, false}, hdi[3] = {false, false, false};
 #pragma unroll
-    for (int a = 0; a < 2; ++a) {
-        const int ab = 1 - a;
-        auto psi_at = [&](int k) {
-            const float* sl = cz(k) < 0 ? s0 : (cz(k) > 0 ? s2 : s1);
-            return sl[(ab * HY + ty + 1 + cy(k)) * HX + tx + 1 + cx(k)];
-        };
-        // opposite neighbours in pairs: psi(x + c_k) - psi(x - c_k), k odd
-        float ax[3] = {0.f, 0.f, 0.f}, di[3] = {0.f, 0.f, 0.f};
+    for (int k = 1; k < Q; k += 2) {
+        const float2 dk = sub2(psi_at(k), psi_at(k + 1));
 #pragma unroll
-        for (int k = 1; k < Q; k += 2) {
-            const float dk = psi_at(k) - psi_at(k + 1);
-            float* acc = is_axis(k) ? ax : di;
-            if (cx(k)) acc[0] = cx(k) > 0 ? acc[0] + dk : acc[0] - dk;
-            if (cy(k)) acc[1] = cy(k) > 0 ? acc[1] + dk : acc[1] - dk;
-            if (cz(k)) acc[2] = cz(k) > 0 ? acc[2] + dk : acc[2] - dk;
+        for (int q = 0; q < 3; ++q) {
+            const int c = q == 0 ? cx(k) : (q == 1 ? cy(k) : cz(k));
+            if (!c) continue;
+            if (is_axis(k)) acc_signed(ax[q], hax[q], dk, c);
+            else acc_signed(di[q], hdi[q], dk, c);
         }
-        const float pre = -gk * s1[(a * HY + ty + 1) * HX + tx + 1];
+    }
+    const int o0 = (ty + 1) * HX + tx + 1;
+    const float2 pre = mul2(sp2(-gk), f2(s1[o0], s1[HY * HX + o0]));
 #pragma unroll
-        for (int d = 0; d < 3; ++d) F[a][d] = pre * (Gax * ax[d] + Gdi * di[d]);
+    for (int d = 0; d < 3; ++d) {
+        const float2 Fd = mul2(pre, fma2(sp2(Gax), ax[d], mul2(sp2(Gdi), di[d])));
+        F[0][d] = Fd.x;
+        F[1][d] = Fd.y;
     }
 }
 
@@ -151,92 +201,115 @@ __device__ __forceinline__ void collide_store(const float (&rc)[2], const float 
                                               const Dest& D, const float (&m36)[2], uint32_t clk = 0)
 {
     // common velocity u' = sum_a j^a/tau^a / sum_a rho^a/tau^a
-    const float den = rc[0] * itau[0] + rc[1] * itau[1];
+    const float den = fmaf(rc[1], itau[1], rc[0] * itau[0]);
     const float iden = den > 0.f ? __frcp_rn(den) : 0.f;
     float up[3];
 #pragma unroll
-    for (int d = 0; d < 3; ++d) up[d] = (jc[0][d] * itau[0] + jc[1][d] * itau[1]) * iden;
+    for (int d = 0; d < 3; ++d) up[d] = fmaf(jc[1][d], itau[1], jc[0][d] * itau[0]) * iden;
 
-    // per component: equilibrium velocity u' + tau F / rho and the polynomial
-    // coefficients of Eq. Equil with c_s^2 = 1/3:
+    // per component (the two lanes): equilibrium velocity u' + tau F / rho and
+    // the polynomial coefficients of Eq. Equil with c_s^2 = 1/3:
     // n^eq_k = zeta_k rho [1 + P_k],  P = cu (3 - 4.5 u^2 + 4.5 cu (1 + cu)) - 1.5 u^2
-    float u[2][3], A0[2], B0[2], w1[2], w2[2], base[2];
+    float sh[2];
 #pragma unroll
-    for (int a = 0; a < 2; ++a) {
-        const float r = rc[a];
-        const float sh = r > 1e-12f ? tau[a] * __frcp_rn(r) : 0.f;  // shift tau F / rho
+    for (int a = 0; a < 2; ++a) sh[a] = rc[a] > 1e-12f ? tau[a] * __frcp_rn(rc[a]) : 0.f;  // shift tau F / rho
+    float2 u[3];
 #pragma unroll
-        for (int d = 0; d < 3; ++d) u[a][d] = fmaf(sh, F[a][d], up[d]);
-        const float usq = u[a][0] * u[a][0] + u[a][1] * u[a][1] + u[a][2] * u[a][2];
-        A0[a] = fmaf(-4.5f, usq, 3.0f);
-        B0[a] = -1.5f * usq;
-        if constexpr (Codec<S>::kDeviation) {
-            w1[a] = w2[a] = r;          // e* = (rho - rho_ref) + rho P
-            base[a] = r - ref[a];
-        } else {
-            w1[a] = r * (1.0f / 18.0f);  // n* = zeta rho + zeta rho P
-            w2[a] = r * (1.0f / 36.0f);
-            base[a] = 0.f;
-        }
+    for (int d = 0; d < 3; ++d) u[d] = fma2(f2(sh[0], sh[1]), f2(F[0][d], F[1][d]), sp2(up[d]));
+    const float2 usq = fma2(u[2], u[2], fma2(u[1], u[1], mul2(u[0], u[0])));
+    const float2 A0 = fma2(sp2(-4.5f), usq, sp2(3.0f));
+    const float2 B0 = mul2(sp2(-1.5f), usq);
+    const float2 R = f2(rc[0], rc[1]);
+    float2 w1, w2, base;
+    if constexpr (Codec<S>::kDeviation) {
+        w1 = w2 = R;  // e* = (rho - rho_ref) + rho P
+        base = sub2(R, f2(ref[0], ref[1]));
+    } else {
+        w1 = mul2(R, sp2(1.0f / 18.0f));  // n* = zeta rho + zeta rho P
+        w2 = mul2(R, sp2(1.0f / 36.0f));
+        base = sp2(0.f);
     }
     const long long slot = L.slot;
+    const long long cslot = (long long)Q * slot;  // component b's slots follow component r's
     const int self = D.zo[1] + D.ro[1] + D.xo[1];
-    float sum[2] = {0.f, 0.f}, sax[2] = {0.f, 0.f}, sdi[2] = {0.f, 0.f};
+    float2 sum = sp2(0.f), sax = sp2(0.f), sdi = sp2(0.f);
     uint32_t hsh = 0;
     if constexpr (Codec<S>::kDitherMoving) hsh = node_hash((uint32_t)self, clk);
+    // opposite velocities in pairs: c_{k+1} = -c_k (k odd, the first nonzero
+    // component of c_k positive), so c_{k+1}.u = -(c_k.u) exactly
 #pragma unroll
-    for (int k = 1; k < Q; ++k) {
-        bool wall;
-        if constexpr (kGeneral) wall = (D.nb >> k) & 1u;
-        else wall = (cz(k) < 0 && D.bot) || (cz(k) > 0 && D.top);
-        // destination: the neighbour x + c_k, or slot kbar of this node (bounce-back)
-        const int qo = wall ? self : D.zo[cz(k) + 1] + D.ro[cy(k) + 1] + D.xo[cx(k) + 1];
-        if constexpr (kCheckBounds)
-            if (!in_bounds(qo, slot, D.err)) continue;
-        S* q = dst + qo;
-        const long long so = (long long)(wall ? opp(k) : k) * slot;
+    for (int k = 1; k < Q; k += 2) {
+        float2 cuk;
+        if (is_axis(k)) {
+            cuk = u[(k - 1) / 2];
+        } else {
+            const int d1 = cz(k) ? 2 : 1;                    // second nonzero component
+            const int s1 = d1 == 2 ? cz(k) : cy(k);
+            const float2 u0 = cx(k) ? u[0] : u[1];           // first nonzero component (+1)
+            cuk = s1 > 0 ? add2(u0, u[d1]) : sub2(u0, u[d1]);
+        }
 #pragma unroll
-        for (int a = 0; a < 2; ++a) {
-            const float cu = (cx(k) ? cx(k) * u[a][0] : 0.f) + (cy(k) ? cy(k) * u[a][1] : 0.f) +
-                             (cz(k) ? cz(k) * u[a][2] : 0.f);
-            const float P = fmaf(cu, fmaf(cu, fmaf(4.5f, cu, 4.5f), A0[a]), B0[a]);
-            const float w = is_axis(k) ? w1[a] : w2[a];
-            const float qk = fmaf(w, P, Codec<S>::kDeviation ? base[a] : w);  // equilibrium, storage form
-            float s;
-            if constexpr (kTauOne) s = qk;
-            else s = fmaf(qk - vc[a][k], itau[a], vc[a][k]);
-            if constexpr (Codec<S>::kDeviation) {
-                S h;
-                if constexpr (Codec<S>::kDitherMoving) h = Codec<S>::sr(s, rand16(hsh, a * Q + k));
-                else h = Codec<S>::rn(s);
-                if (is_axis(k)) sax[a] += Codec<S>::val(h);
-                else sdi[a] += Codec<S>::val(h);
-                q[so + (long long)a * Q * slot] = h;
+        for (int h = 0; h < 2; ++h) {
+            const int kk = k + h;
+            const float2 cu = h ? neg2(cuk) : cuk;
+            const float2 P = fma2(cu, fma2(cu, fma2(sp2(4.5f), cu, sp2(4.5f)), A0), B0);
+            const float2 w = is_axis(kk) ? w1 : w2;
+            const float2 qk = fma2(w, P, Codec<S>::kDeviation ? base : w);  // equilibrium, storage form
+            float2 s;
+            if constexpr (kTauOne) {
+                s = qk;
             } else {
-                sum[a] += s;
-                Codec<S>::store(q + so + (long long)a * Q * slot, s);
+                const float2 v = f2(vc[0][kk], vc[1][kk]);
+                s = fma2(sub2(qk, v), f2(itau[0], itau[1]), v);
+            }
+            bool wall;
+            if constexpr (kGeneral) wall = (D.nb >> kk) & 1u;
+            else wall = (cz(kk) < 0 && D.bot) || (cz(kk) > 0 && D.top);
+            // destination: the neighbour x + c_k, or slot kbar of this node (bounce-back)
+            const int qo = wall ? self : D.zo[cz(kk) + 1] + D.ro[cy(kk) + 1] + D.xo[cx(kk) + 1];
+            if constexpr (kCheckBounds)
+                if (!in_bounds(qo, slot, D.err)) continue;
+            S* q = dst + qo + (long long)(wall ? opp(kk) : kk) * slot;
+            if constexpr (Codec<S>::kDeviation) {
+                S h0, h1;
+                if constexpr (Codec<S>::kDitherMoving) {
+                    h0 = Codec<S>::sr(s.x, rand16(hsh, kk));
+                    h1 = Codec<S>::sr(s.y, rand16(hsh, Q + kk));
+                } else {
+                    h0 = Codec<S>::rn(s.x);
+                    h1 = Codec<S>::rn(s.y);
+                }
+                const float2 hv = f2(Codec<S>::val(h0), Codec<S>::val(h1));
+                if (is_axis(kk)) sax = add2(sax, hv);
+                else sdi = add2(sdi, hv);
+                q[0] = h0;
+                q[cslot] = h1;
+            } else {
+                sum = add2(sum, s);
+                Codec<S>::store(q, s.x);
+                Codec<S>::store(q + cslot, s.y);
             }
         }
     }
     if constexpr (kCheckBounds)
         if (!in_bounds(self, slot, D.err)) return;
     S* q0 = dst + self;
-    uint32_t hrest = 0;
-    if constexpr (Codec<S>::kDitherMoving) hrest = node_hash(hsh, 0x632BE5ABu);  // a second full mixing round
-    else if constexpr (Codec<S>::kDeviation) hrest = node_hash((uint32_t)self, clk);
-#pragma unroll
-    for (int a = 0; a < 2; ++a) {
-        if constexpr (Codec<S>::kDeviation) {
-            // 12 e_0* = m36 - 2 sum_axis e_k* - sum_diag e_k*, the right side exact in FP32
-            // the residual step makes the quotient round as x/12 itself would;
-            // the rounded reciprocal alone scales every rest value by 1 + 3e-8
-            const float x0 = m36[a] - fmaf(2.0f, sax[a], sdi[a]);
-            float s0 = x0 * (1.0f / 12.0f);
-            s0 = fmaf(fmaf(-12.0f, s0, x0), 1.0f / 12.0f, s0);
-            q0[(long long)a * Q * slot] = Codec<S>::sr(s0, rand16(hrest, a));
-        } else {
-            Codec<S>::store(q0 + (long long)a * Q * slot, rc[a] - sum[a]);
-        }
+    if constexpr (Codec<S>::kDeviation) {
+        uint32_t hrest;
+        if constexpr (Codec<S>::kDitherMoving) hrest = node_hash(hsh, 0x632BE5ABu);  // a second full mixing round
+        else hrest = node_hash((uint32_t)self, clk);
+        // 12 e_0* = m36 - 2 sum_axis e_k* - sum_diag e_k*, the right side exact in FP32
+        // the residual step makes the quotient round as x/12 itself would;
+        // the rounded reciprocal alone scales every rest value by 1 + 3e-8
+        const float2 x0 = sub2(f2(m36[0], m36[1]), fma2(sp2(2.0f), sax, sdi));
+        float2 s0 = mul2(x0, sp2(1.0f / 12.0f));
+        s0 = fma2(fma2(sp2(-12.0f), s0, x0), sp2(1.0f / 12.0f), s0);
+        q0[0] = Codec<S>::sr(s0.x, rand16(hrest, 0));
+        q0[cslot] = Codec<S>::sr(s0.y, rand16(hrest, 1));
+    } else {
+        const float2 r0 = sub2(R, sum);
+        Codec<S>::store(q0, r0.x);
+        Codec<S>::store(q0 + cslot, r0.y);
     }
 }
 

@@ -214,32 +214,37 @@ __global__ void __launch_bounds__(32 * TY, (kTmaCtas<TY, kTauOne>)) step_tma_ker
             const bool solid = zp == 0 || zp == nz - 1;
             if (ok) {
                 const S* st = stages + (size_t)(gi % NS) * G::STAGE_ELEMS;
+                float ps[2] = {eta[0], eta[1]};
+                rho[0] = rho[1] = m[0] = m[1] = 0.f;
 #pragma unroll
-                for (int a = 0; a < 2; ++a) {
-                    float ps = eta[a];
-                    rho[a] = 0.f;
-                    m[a] = 0.f;
-                    j[a][0] = j[a][1] = j[a][2] = 0.f;
-                    if (!solid && own_rd) {
-                        float w[Q];
+                for (int a = 0; a < 2; ++a) j[a][0] = j[a][1] = j[a][2] = 0.f;
+                if (!solid && own_rd) {
+                    float w[2][Q];
+#pragma unroll
+                    for (int a = 0; a < 2; ++a) {
                         if (!own_strip) {
                             const S* so = st + (a * Q * HY + ty + 1) * BX + tx + GX;
 #pragma unroll
-                            for (int k = 0; k < Q; ++k) w[k] = Codec<S>::val(so[k * HY * BX]);
+                            for (int k = 0; k < Q; ++k) w[a][k] = Codec<S>::val(so[k * HY * BX]);
                         } else {
                             const S* so = st + G::MAIN_ELEMS + G::STRIP_ELEMS + (a * Q * HY + ty + 1) * SX + gx - nx;
 #pragma unroll
-                            for (int k = 0; k < Q; ++k) w[k] = Codec<S>::val(so[k * HY * SX]);
-                        }
-                        rho[a] = rho_of<S>(w, ref[a], &m[a]);
-                        mom_of<S>(w, j[a]);
-                        ps = psi_of(rho[a]);
-                        if constexpr (!kTauOne) {
-#pragma unroll
-                            for (int k = 0; k < Q; ++k) v[a][k] = w[k];
+                            for (int k = 0; k < Q; ++k) w[a][k] = Codec<S>::val(so[k * HY * SX]);
                         }
                     }
-                    if (active) spl[(a * HY + ty + 1) * HX + tx + 1] = ps;
+                    moments2<S>(w, ref, rho, j, m);
+                    ps[0] = psi_of(rho[0]);
+                    ps[1] = psi_of(rho[1]);
+                    if constexpr (!kTauOne) {
+#pragma unroll
+                        for (int a = 0; a < 2; ++a)
+#pragma unroll
+                            for (int k = 0; k < Q; ++k) v[a][k] = w[a][k];
+                    }
+                }
+                if (active) {
+                    spl[(ty + 1) * HX + tx + 1] = ps[0];
+                    spl[(HY + ty + 1) * HX + tx + 1] = ps[1];
                 }
 #pragma unroll
                 for (int q = 0; q < NIT; ++q) {
