@@ -43,6 +43,10 @@ WORKLOADS = {
     # 11 wall values in [-0.1, 0.1] on the 128^3 droplet, 20000 steps, as one batch
     "angles": dict(dims=(128, 128, 128), radius=30.0, precision="f32", steps=20000,
                    w=[round(-0.1 + 0.02 * i, 3) for i in range(11)]),
+    # size convergence: cubic lattices of edge 32 .. 256 with the droplet scaled with the box (R = 0.234 L,
+    # the 128^3 droplet's ratio), three wall values, the same fixed step count for every size
+    "sizes": dict(edges=(32, 64, 128, 256), radius_frac=30.0 / 128.0, precision="f32", steps=20000,
+                  w=(0.03, 0.06, 0.09)),
     # adjoint calibration: 64^3, R = 16, 2000 steps, checkpoints every 100
     "adjoint": dict(dims=(64, 64, 64), radius=16.0, precision="f32", steps=2000, ckpt=100),
     # surface tensions (Sec. 4.1-4.2): 8x8x128 periodic lamellae (gamma_LG), 8x8x(64+2) slabs of each
@@ -602,6 +606,96 @@ def run_angles(args):
     print(json.dumps(line), flush=True)
 
 
+def run_sizes(args):
+    """Contact angle against the lattice size (Sec. 4, Fig. 4 left): cubic lattices of edge
+    32, 64, 128 and 256 with the droplet radius scaled with the edge, for three wall values.
+    The lattices up to 128^3 run as one batch, the 256^3 ones one at a time. Every lattice
+    takes the same number of steps; the angle is also taken 10% of the steps before the
+    end, and the change over that last tenth is reported as the convergence indicator."""
+    import torch
+
+    from paper_0910_3915_gb300 import lbsc
+    from paper_0910_3915_gb300 import workloads as W
+
+    torch.cuda.set_device(0)
+    wl = WORKLOADS["sizes"]
+    T = args.steps if args.steps != 20000 else wl["steps"]
+    T1 = T - T // 10
+    ws, edges = wl["w"], wl["edges"]
+    stream = torch.cuda.current_stream()
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    res = {}
+    total_ms, total_lu = 0.0, 0
+
+    def angle_of(obj, L):
+        # reference plane 5 l.u. above the wall; 3 l.u. for the 32^3 droplet (R = 7.5)
+        a = obj.contact_angle(3.0 if L < 64 else 5.0)
+        return a["theta_deg"] if a["ok"] else None
+
+    small = [L for L in edges if L < 256]
+    cases = [(L, w) for L in small for w in ws]
+    fields = [W.droplet_fields(L, L, L, wl["radius_frac"] * L, seed=0) for L, _ in cases]
+    params = [lbsc.Params(**CONTACT, eta_wall_r=W.wall_split(w)[0], eta_wall_b=W.wall_split(w)[1]) for _, w in cases]
+    batch = lbsc.Batch(fields, params, wl["precision"])
+    e0, e1 = ev(), ev()
+    e0.record(stream)
+    batch.step(T1)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    mid = [angle_of(batch.box(i), L) for i, (L, _) in enumerate(cases)]
+    e2, e3 = ev(), ev()
+    e2.record(stream)
+    batch.step(T - T1)
+    e3.record(stream)
+    torch.cuda.synchronize()
+    total_ms += e0.elapsed_time(e1) + e2.elapsed_time(e3)
+    total_lu += sum(L * L * (L - 2) for L, _ in cases) * T
+    for i, (L, w) in enumerate(cases):
+        res[(L, w)] = (angle_of(batch.box(i), L), mid[i])
+    batch.close()
+    for L in [L for L in edges if L >= 256]:
+        for w in ws:
+            rr, rb = W.droplet_fields(L, L, L, wl["radius_frac"] * L, seed=0)
+            er, eb = W.wall_split(w)
+            lat = lbsc.Lattice(rr, rb, wl["precision"]).set_params(**CONTACT, eta_wall_r=er, eta_wall_b=eb)
+            e0, e1 = ev(), ev()
+            e0.record(stream)
+            lat.step(T1)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            th_mid = angle_of(lat, L)
+            e2, e3 = ev(), ev()
+            e2.record(stream)
+            lat.step(T - T1)
+            e3.record(stream)
+            torch.cuda.synchronize()
+            total_ms += e0.elapsed_time(e1) + e2.elapsed_time(e3)
+            total_lu += L * L * (L - 2) * T
+            res[(L, w)] = (angle_of(lat, L), th_mid)
+            lat.close()
+    rows = []
+    for w in ws:
+        row = {"w": w, "theta": {}, "dtheta_last_tenth": {}}
+        for L in edges:
+            th, th_mid = res[(L, w)]
+            row["theta"][str(L)] = round(th, 3) if th is not None else None
+            row["dtheta_last_tenth"][str(L)] = (round(abs(th - th_mid), 3)
+                                                if th is not None and th_mid is not None else None)
+        th128, th256 = res.get((128, w), (None,))[0], res.get((256, w), (None,))[0]
+        if th128 is not None and th256 is not None:
+            row["rel_change_128_to_256"] = round(abs(th256 - th128) / th128, 5)
+        rows.append(row)
+    line = {
+        "metric": METRIC, "value": round(total_lu / (total_ms * 1e-3) / 1e6, 1), "unit": "MLUPS", "n_gpus": 1,
+        "steps": T, "warmup": 0, "ms_per_step": round(total_ms / T, 5), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": wl["precision"], "data": "synthetic",
+        "config": {"workload": "theta vs lattice size: cubic %s, R = %.3f L, w = %s, %d steps each"
+                               % ("/".join(str(L) for L in edges), wl["radius_frac"], list(ws), T)},
+        "sizes": rows,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def run_young(args):
     """Contact angles from surface tensions (Sec. 4.1-4.2): Young's equation with
     planar tensions (Eq. gammaMechDef on lamellae and wall slabs), the radial
@@ -745,6 +839,8 @@ def main():
         run_angles(args)
     elif args.workload == "young":
         run_young(args)
+    elif args.workload == "sizes":
+        run_sizes(args)
     else:
         run_ours(args)
 
