@@ -185,8 +185,9 @@ struct Dest {
 // remainder of the node's mass, which Eq. Equil and BGK leave unchanged, so
 // that rounded lattice weights (1/3 + 6/18 + 12/36 != 1 in FP32) and 16-bit
 // rounding of the stored values do not bias the mass.
-// Loop order: velocity k outer, component inner, so each destination address
-// is formed once and both components' slots are reached by a uniform offset.
+// The two components are the lanes of packed pairs, so each destination
+// address is formed once per velocity and component b's slot is reached by a
+// uniform offset; opposite velocities are taken together (c_kbar.u = -c_k.u).
 // For 16-bit storage the rest value, which balances the node's mass (taken
 // exactly from m36 and the stored moving values), is rounded stochastically:
 // round-to-nearest of nearly equal bulk values would bias the mass of every
