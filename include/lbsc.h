@@ -142,6 +142,20 @@ int lb_sync(lb_ctx* ctx);
  * LB_ERR_BARRIER_TIMEOUT (the expected outcome); the context stays usable. */
 int lb_selftest_bounded_wait(lb_ctx* ctx, unsigned spin_limit);
 
+/* Self-test of the step's pseudopotential psi = 1 - exp(-rho) (Sec. 2; the
+ * library evaluates it by its own range reduction and series, not by a
+ * math-library call). rho: n host floats (1 <= n <= 2^24). out: 4n host
+ * floats, written with
+ *   out[i]        psi as the step computes it for a ring node,
+ *   out[n + i]    psi of rho[i] in the first lane of the packed (two-component)
+ *                 evaluation of the pair (rho[i], rho[n-1-i]),
+ *   out[2n + i]   psi of rho[n-1-i] in the second lane of that evaluation,
+ *   out[3n + i]   -expm1f(-rho[i]) from the CUDA math library, for comparison.
+ * Runs on the current device with temporary device memory (synchronous).
+ * LB_ERR_ARG for NULL arrays or n out of range, LB_ERR_CUDA on a CUDA error
+ * (messages via lb_last_error(NULL)). */
+int lb_selftest_psi(const float* rho, int n, float* out);
+
 /* Read densities and conservation sums (Sec. 2, moments). Any output may be NULL.
  * rho_r, rho_b: nx*ny*nz doubles. u: 3*nx*ny*nz doubles (component-major),
  * the barycentric velocity (sum_a j^a + F/2)/sum_a rho^a with F the total

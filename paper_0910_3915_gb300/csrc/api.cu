@@ -1562,3 +1562,26 @@ extern "C" int lb_huang_theta(double eta_wall_r, double eta_wall_b, double rho_i
     *theta_deg = clamp_acos_deg((eta_wall_r - eta_wall_b) / (0.5 * (rho_in - rho_out)));
     return LB_OK;
 }
+
+// ---------------------------------------------------------------- psi self-test
+extern "C" int lb_selftest_psi(const float* rho, int n, float* out)
+{
+    if (!rho || !out || n < 1 || n > (1 << 24)) {
+        lbsc_set_global_error("lb_selftest_psi: host arrays and 1 <= n <= 2^24 required");
+        return LB_ERR_ARG;
+    }
+    float* d = nullptr;
+    cudaError_t e = cudaMalloc(&d, (size_t)5 * n * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemcpy(d, rho, (size_t)n * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = lbsc::launch_psi_probe(d, n, d + n, nullptr);
+    if (e == cudaSuccess) e = cudaMemcpy(out, d + n, (size_t)4 * n * sizeof(float), cudaMemcpyDeviceToHost);
+    if (d) {
+        const cudaError_t f = cudaFree(d);
+        if (e == cudaSuccess) e = f;
+    }
+    if (e != cudaSuccess) {
+        lbsc_set_global_error(std::string("lb_selftest_psi: ") + cudaGetErrorString(e));
+        return LB_ERR_CUDA;
+    }
+    return LB_OK;
+}

@@ -117,8 +117,9 @@ __device__ __forceinline__ void step_item(const StepArgs<S>& A, int col, int za,
         for (int a = 0; a < 2; ++a) j[a][0] = j[a][1] = j[a][2] = 0.f;
         if (!so_) {
             moments2<S>(ro_, ref, rho, j, m);
-            ps[0] = psi_of(rho[0]);
-            ps[1] = psi_of(rho[1]);
+            const float2 p2 = psi2_of(f2(rho[0], rho[1]));
+            ps[0] = p2.x;
+            ps[1] = p2.y;
             if constexpr (!kTauOne) {
 #pragma unroll
                 for (int a = 0; a < 2; ++a)
@@ -351,6 +352,27 @@ int batch_occupancy(int tile_y, bool tau_one)
                     : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_step_kernel<S, 16, false>, 512, 0);
     }
     return e == cudaSuccess && n > 0 ? n : 1;
+}
+
+// Self-test of psi: out[i] = psi_of(rho[i]); the packed lanes of
+// psi2_of(rho[i], rho[n-1-i]) in out[n + i] and out[2n + i]; and
+// out[3n + i] = -expm1f(-rho[i]) from the CUDA math library.
+__global__ void psi_probe_kernel(const float* __restrict__ rho, int n, float* __restrict__ out)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        out[i] = psi_of(rho[i]);
+        const float2 p = psi2_of(f2(rho[i], rho[n - 1 - i]));
+        out[n + i] = p.x;
+        out[2 * n + i] = p.y;
+        out[3 * n + i] = -expm1f(-rho[i]);
+    }
+}
+
+cudaError_t launch_psi_probe(const float* rho, int n, float* out, cudaStream_t st)
+{
+    const int blocks = (n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024;
+    psi_probe_kernel<<<blocks < 1 ? 1 : blocks, 256, 0, st>>>(rho, n, out);
+    return cudaGetLastError();
 }
 
 #define LBSC_BATCH_INST(S)                                                                                     \

@@ -105,8 +105,60 @@ __device__ __forceinline__ void moments2(const float (&v)[2][Q], const float (&r
     }
 }
 
-// psi = 1 - exp(-rho), evaluated as -expm1(-rho) to keep precision at small rho
-__device__ __forceinline__ float psi_of(float rho) { return -expm1f(-rho); }
+// psi = 1 - exp(-rho) (Sec. 2), evaluated without cancellation at small rho
+// and without a library call. Cody and Waite's reduction: rho = k ln2 + r,
+// k = rint(rho / ln2), |r| <= ln2/2, with ln2 split as kLn2Hi (16 significant
+// bits, so k kLn2Hi is exact for |k| < 2^8) plus kLn2Lo; then
+//   1 - exp(-rho) = (1 - 2^-k) + 2^-k (r + r q(r)),
+// where r + r q(r) = 1 - exp(-r), i.e. q is the Taylor series of
+// (1 - e^-r)/r - 1 = sum_n (-r)^n / (n+1)!, n = 1..6, whose remainder is
+// below 2^-26 relative for |r| <= ln2/2. The leading r is added in the last
+// fused multiply-add, 1 - 2^-k and the scaling by 2^-k are exact, so the
+// result stays within about 1 ulp of -expm1(-rho) (the GPU self-test checks
+// it against the exact value and against expm1f). rho is
+// clamped to [-80, 80] (psi is -5.5e34 .. 1 there); NaN passes through.
+// psi_of and psi2_of (both components in packed lanes) perform the same
+// operations, so a node's psi is the same bits whether it is computed as a
+// tile's own node or as a ring node of the neighbouring tile.
+constexpr float kInvLn2 = 1.44269502162933350f;
+constexpr float kLn2Hi = 0.693145751953125f;
+constexpr float kLn2Lo = 1.42860676533018700e-06f;
+constexpr float kPsiC1 = -0.5f, kPsiC2 = 1.0f / 6.0f, kPsiC3 = -1.0f / 24.0f, kPsiC4 = 1.0f / 120.0f,
+                kPsiC5 = -1.0f / 720.0f, kPsiC6 = 1.0f / 5040.0f;
+
+__device__ __forceinline__ float psi_clamp(float rho) { return rho > 80.0f ? 80.0f : (rho < -80.0f ? -80.0f : rho); }
+__device__ __forceinline__ float pow2_neg(float kf) { return __int_as_float((127 - (int)kf) << 23); }  // 2^-k
+
+__device__ __forceinline__ float psi_of(float rho)
+{
+    const float x = psi_clamp(rho);
+    const float kf = rintf(x * kInvLn2);
+    const float r = fmaf(kf, -kLn2Lo, fmaf(kf, -kLn2Hi, x));
+    float t = fmaf(kPsiC6, r, kPsiC5);
+    t = fmaf(t, r, kPsiC4);
+    t = fmaf(t, r, kPsiC3);
+    t = fmaf(t, r, kPsiC2);
+    t = fmaf(t, r, kPsiC1);
+    const float q = r * t;
+    const float sc = pow2_neg(kf);
+    return fmaf(sc, fmaf(r, q, r), 1.0f - sc);
+}
+
+__device__ __forceinline__ float2 psi2_of(float2 rho)
+{
+    const float2 x = f2(psi_clamp(rho.x), psi_clamp(rho.y));
+    const float2 xk = mul2(x, sp2(kInvLn2));
+    const float2 kf = f2(rintf(xk.x), rintf(xk.y));
+    const float2 r = fma2(kf, sp2(-kLn2Lo), fma2(kf, sp2(-kLn2Hi), x));
+    float2 t = fma2(sp2(kPsiC6), r, sp2(kPsiC5));
+    t = fma2(t, r, sp2(kPsiC4));
+    t = fma2(t, r, sp2(kPsiC3));
+    t = fma2(t, r, sp2(kPsiC2));
+    t = fma2(t, r, sp2(kPsiC1));
+    const float2 q = mul2(r, t);
+    const float2 sc = f2(pow2_neg(kf.x), pow2_neg(kf.y));
+    return fma2(sc, fma2(r, q, r), sub2(sp2(1.0f), sc));
+}
 
 // Eq. SCforce on the psi ring: s0, s1, s2 are the planes z-1, z, z+1 of a
 // [2][HY][HX] psi array, the node at row ty+1, column tx+1.

@@ -233,8 +233,9 @@ __global__ void __launch_bounds__(32 * TY, (kTmaCtas<TY, kTauOne>)) step_tma_ker
                         }
                     }
                     moments2<S>(w, ref, rho, j, m);
-                    ps[0] = psi_of(rho[0]);
-                    ps[1] = psi_of(rho[1]);
+                    const float2 p2 = psi2_of(f2(rho[0], rho[1]));
+                    ps[0] = p2.x;
+                    ps[1] = p2.y;
                     if constexpr (!kTauOne) {
 #pragma unroll
                         for (int a = 0; a < 2; ++a)

@@ -88,6 +88,7 @@ SIGNATURES = [
     ("lb_step", _I, [_VP, _I]),
     ("lb_sync", _I, [_VP]),
     ("lb_selftest_bounded_wait", _I, [_VP, ctypes.c_uint]),
+    ("lb_selftest_psi", _I, [ctypes.POINTER(ctypes.c_float), _I, ctypes.POINTER(ctypes.c_float)]),
     ("lb_moments", _I, [_VP, _DP, _DP, _DP, _DP]),
     ("lb_conservation", _I, [_VP, _DP]),
     ("lb_contact_angle", _I, [_VP, ctypes.c_double, ctypes.POINTER(lb_droplet)]),

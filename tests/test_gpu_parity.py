@@ -435,3 +435,30 @@ def test_bounded_wait_reports_timeout_and_context_survives(lbsc):
     cons = lat.conservation()  # the status word was cleared: no error now
     assert cons[7] == 10 and cons[5] == 0
     lat.close()
+
+
+def test_psi_series_within_two_ulp_and_packed_lanes_identical(lbsc):
+    """psi = 1 - exp(-rho) as the step evaluates it (its own ln2 range
+    reduction and Taylor series, Sec. 2's pseudopotential) is within 1 ulp of
+    the exact value over the densities the method meets and beyond, no worse
+    than CUDA's expm1f plus a quarter ulp, and the packed two-component evaluation
+    gives the scalar evaluation's bits in both lanes (own and ring nodes must
+    agree bit for bit)."""
+    import ctypes
+    rho = np.concatenate([np.linspace(0.0, 4.0, 40001), np.geomspace(1e-9, 1.0, 4001),
+                          np.linspace(4.0, 80.0, 2001), -np.geomspace(1e-9, 0.3, 1001),
+                          [0.0, 1e-30, 90.0]]).astype(np.float32)
+    n = rho.size
+    out = np.empty(4 * n, np.float32)
+    P = ctypes.POINTER(ctypes.c_float)
+    lib = lbsc.load()
+    assert lib.lb_selftest_psi(rho.ctypes.data_as(P), n, out.ctypes.data_as(P)) == lbsc.LB_OK
+    psi, lane0, lane1, lib_ref = out[:n], out[n:2 * n], out[2 * n:3 * n], out[3 * n:]
+    assert np.array_equal(psi.view(np.uint32), lane0.view(np.uint32))
+    assert np.array_equal(psi[::-1].view(np.uint32), lane1.view(np.uint32))
+    exact = -np.expm1(-rho.astype(np.float64))
+    ulp = np.spacing(np.abs(exact).astype(np.float32)).astype(np.float64)
+    err = np.abs(psi.astype(np.float64) - exact) / ulp
+    lib_err = np.abs(lib_ref.astype(np.float64) - exact) / ulp
+    assert err.max() <= 1.0, (err.max(), rho[np.argmax(err)])
+    assert err.max() <= lib_err.max() + 0.25, (err.max(), lib_err.max())
