@@ -437,7 +437,7 @@ def test_bounded_wait_reports_timeout_and_context_survives(lbsc):
     lat.close()
 
 
-def test_psi_series_within_two_ulp_and_packed_lanes_identical(lbsc):
+def test_psi_series_within_one_ulp_and_packed_lanes_identical(lbsc):
     """psi = 1 - exp(-rho) as the step evaluates it (its own ln2 range
     reduction and Taylor series, Sec. 2's pseudopotential) is within 1 ulp of
     the exact value over the densities the method meets and beyond, no worse
