@@ -200,7 +200,7 @@ __device__ __forceinline__ void sc_force(const float* s0, const float* s1, const
 // Where the node's populations go: neighbours (wrapped), the planes of z-1,
 // z, z+1, and which links end on a wall.
 // Ghost images are not written here: the TMA path refreshes them in a
-// separate pass (ghost_kernel) after each step. Addresses are a warp-uniform
+// separate pass (ghost_rows_kernel) after each step. Addresses are a warp-uniform
 // slot base plus a 32-bit per-thread offset.
 struct Dest {
     int xo[3], yo[3];  // x-1, x, x+1 and y-1, y, y+1, wrapped
