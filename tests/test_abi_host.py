@@ -131,3 +131,22 @@ def test_closed_form_angles_host(lib):
     assert lbsc.huang_theta(-w, w, 0.7, 0.04) > 90.0 > lbsc.huang_theta(w, -w, 0.7, 0.04)
     with pytest.raises(lbsc.LBError):
         lbsc.huang_theta(0.0, 0.0, 0.04, 0.7)
+
+
+def test_huang_theta_hand_worked_values(lib):
+    """Eq. huangSigmaLG against values worked by hand as exact fractions
+    (tests/golden/paper_values.json), including the clamp at |cos| > 1."""
+    import json
+    import math
+    import os
+    from paper_0910_3915_gb300 import lbsc
+    with open(os.path.join(os.path.dirname(__file__), "golden", "paper_values.json")) as f:
+        ex = json.load(f)["huang_examples"]
+    assert len(ex) >= 4
+    for e in ex:
+        num, den = (int(t) for t in e["cos_theta"].split("/"))
+        c = num / den
+        assert math.isclose(c, (e["eta_wall_r"] - e["eta_wall_b"]) / ((e["rho_in"] - e["rho_out"]) / 2),
+                            rel_tol=1e-12, abs_tol=1e-15)
+        th = lbsc.huang_theta(e["eta_wall_r"], e["eta_wall_b"], e["rho_in"], e["rho_out"])
+        assert math.isclose(th, e["theta_deg"], rel_tol=0, abs_tol=1e-9), e

@@ -306,6 +306,27 @@ def test_contact_angle_small_cap_with_small_offset():
     assert ca["ok"] == 1 and abs(ca["theta_deg"] - 30.0) < 1.0
 
 
+@pytest.mark.parametrize("theta", [60.0, 120.0])
+@pytest.mark.parametrize("frac", [-0.5, 0.5])
+def test_contact_angle_at_level_on_analytic_caps(theta, frac):
+    """Sec. 3 construction at phi = level (Fig. 4's half-max error bars): on the
+    cap phi = A tanh((R - d)/w) the level set phi = c is the sphere of radius
+    R - w atanh(c/A) about the same centre, so the angle at that level is
+    acos((0.5 - z_c)/R_c). The two signs of c give angles about 3.6 deg apart,
+    so taking the level with the wrong sign fails."""
+    R, width, A = 20.0, 2.0, 0.66
+    rr, rb, solid, zc = _cap_field(theta, R=R, width=width)
+    level = frac * A
+    R_c = R - width * math.atanh(frac)
+    theta_c = math.degrees(math.acos((0.5 - zc) / R_c))
+    ca = oracle.contact_angle(rr, rb, solid, offset=5.0, level=level)
+    assert ca["ok"] == 1
+    assert abs(ca["theta_deg"] - theta_c) < 0.5
+    assert abs(ca["r_fit"] - R_c) < 0.1
+    assert abs(ca["zc"] - zc) < 0.2
+    assert abs(theta_c - theta) > 1.5  # the level moves the angle by more than the tolerance
+
+
 def test_cap_relation_worked_example():
     """Fig. 2 caption: r = (4h^2 + b^2)/(8h); hand-worked values in the golden file."""
     for ex in golden("paper_values.json")["cap_relation_examples"]:
@@ -316,6 +337,54 @@ def test_cap_relation_worked_example():
 
 
 # ---------------------------------------------------------------- surface tension reductions
+@pytest.mark.parametrize("plane", ["xy", "xz", "yz"])
+def test_pressure_tensor_off_diagonal_on_tilted_lamella(plane):
+    """Sec. 4.1 pressure tensor, off-diagonal entries. Lamellae whose normal
+    n = (e_i + e_j)/sqrt(2) lies on a face diagonal of the lattice (periodic
+    N x N box, densities a function of s = x_i + x_j only). With the W36
+    weights (G_k = 36 zeta_k) and tau = 1, every population, weight and
+    neighbour psi depends on a velocity only through c.n and zeta_k, and within
+    each group of equal c.n the D3Q19 sums of (c.t)^2 and c_k^2 coincide for the
+    in-plane tangent t = (e_i - e_j)/sqrt(2) and the third axis e_k. So:
+    P_ii = P_jj (the i <-> j mirror), P_ik = P_jk = 0 (the k mirror), and the
+    in-plane tangential stress t.P.t = (P_ii + P_jj)/2 - P_ij equals P_kk
+    exactly. A wrong index, sign or factor in P_ij breaks the last identity.
+    The normal-minus-tangential excess integrated along n is the lamella's
+    surface tension (Eq. gammaMechDef), within the lattice's anisotropy of the
+    axis-aligned value."""
+    N, steps = 48, 2000
+    i, j = {"xy": (0, 1), "xz": (0, 2), "yz": (1, 2)}[plane]
+    k = 3 - i - j
+    dims = [1, 1, 1]
+    dims[i] = dims[j] = N
+    nx, ny, nz = dims
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    c = (x, y, z)
+    s = (c[i] + c[j]) % N
+    inside = s < N // 2
+    rr, rb = np.where(inside, 0.7, 0.04), np.where(inside, 0.04, 0.7)
+    st = oracle.State(rr, rb, W.periodic_mask(nx, ny, nz), CONTACT)
+    st.step(steps)
+    P = st.pressure_tensor()
+    comp = {(0, 0): 0, (1, 1): 1, (2, 2): 2, (0, 1): 3, (0, 2): 4, (1, 2): 5}
+    Pii, Pjj, Pkk = P[comp[(i, i)]], P[comp[(j, j)]], P[comp[(k, k)]]
+    Pij = P[comp[(i, j)]]
+    Pik, Pjk = P[comp[tuple(sorted((i, k)))]], P[comp[tuple(sorted((j, k)))]]
+    scale = np.abs(Pii).max()
+    assert np.abs(Pij).max() > 1e-3 * scale  # the shear entry is far from zero across the interfaces
+    assert np.abs(Pii - Pjj).max() < 1e-13 * scale
+    assert np.abs(Pik).max() < 1e-13 * scale and np.abs(Pjk).max() < 1e-13 * scale
+    PT = 0.5 * (Pii + Pjj) - Pij
+    PN = 0.5 * (Pii + Pjj) + Pij
+    assert np.abs(PT - Pkk).max() < 1e-13 * scale
+    # Eq. gammaMechDef along n: one unit of s is 1/sqrt(2) along the normal; two interfaces
+    sf = s.ravel()
+    excess = np.array([(PN - PT).ravel()[sf == v].mean() for v in range(N)])
+    gamma_tilted = 0.5 * excess.sum() / math.sqrt(2)
+    gamma_axis = _surface_tension_flat(_lamella())
+    assert math.isclose(gamma_tilted, gamma_axis, rel_tol=0.1)
+
+
 def test_pressure_profile_on_analytic_planar_field():
     """Eq. gammaMechDef on a synthetic tensor field whose P_N - P_T along z is a
     Gaussian of known integral: the plane means drop in-plane variations of
