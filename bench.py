@@ -45,6 +45,10 @@ WORKLOADS = {
                    w=[round(-0.1 + 0.02 * i, 3) for i in range(11)]),
     # size convergence: cubic lattices of edge 32 .. 256 with the droplet scaled with the box (R = 0.234 L,
     # the 128^3 droplet's ratio), three wall values, the same fixed step count for every size
+    # z-slab decomposition with a halo exchange every step. One process: the 128^3 droplet as 2 slabs on one
+    # GPU (the exchange's cost against the single lattice). Under torchrun: one slab of 126 fluid planes per
+    # rank, a 128 x 128 x (126 N + 2) lattice with the droplet on its bottom wall (NCCL messages, weak scaling)
+    "slabs": dict(dims=(128, 128, 128), radius=30.0, precision="f32", w=0.05, nslab=2, schedule=(8, 19, 4)),
     "sizes": dict(edges=(32, 64, 128, 256), radius_frac=30.0 / 128.0, precision="f32", steps=20000,
                   w=(0.03, 0.06, 0.09)),
     # adjoint calibration: 64^3, R = 16, 2000 steps, checkpoints every 100
@@ -69,6 +73,8 @@ def parse():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="single")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--no-samples", action="store_true",
+                    help="default workload: skip the 16-bit storage and batched-sweep throughput samples")
     ap.add_argument("--no-accuracy", action="store_true",
                     help="precision workloads: skip the accuracy runs against FP32 and the oracle")
     ap.add_argument("--schedule", default=None,
@@ -252,6 +258,7 @@ def run_ours(args):
     elif not args.no_tune:
         schedule, _ = tune.tune(lat)
     lat.step(Wm)
+    lat.contact_angle(5.0)  # warm-up of the measurement kernels too (their first launch loads them)
     lat.sync()
 
     try:
@@ -294,27 +301,34 @@ def run_ours(args):
     cons = lat.conservation()
     lat.close()
 
-    # end to end through the C ABI with host buffers: init (H2D), steps, readback (D2H)
+    # End to end through the C ABI with host buffers. The context is allocated before the timed region
+    # (the allocation is not a copy); timed are: the initial densities from pinned host memory into it
+    # (lb_reset: host-to-device copy, initialisation kernel and its input check), the same steps and
+    # reductions as above, and the results back on the host (the conservation sums and the contact angle).
     rr_p = torch.from_numpy(rr).pin_memory().numpy()
     rb_p = torch.from_numpy(rb).pin_memory().numpy()
+    lat2 = lbsc.Lattice(rr, rb, prec).set_params(**prm)
+    if schedule:
+        tune.apply(lat2, schedule)
+    lat2.step(Wm)
+    lat2.contact_angle(5.0)
     torch.cuda.synchronize()
     replicas.barrier()
     te = time.perf_counter()
-    lat2 = lbsc.Lattice(rr_p, rb_p, prec).set_params(**prm)
-    if schedule:
-        tune.apply(lat2, schedule)
-    done = 0
+    lat2.reset(rr_p, rb_p)
+    done, n_cons = 0, 0
     while done < K:
         m = min(CONS_EVERY, K - done)
         lat2.step(m)
         lat2.conservation()
+        n_cons += 1
         done += m
-    out_r, out_b, _, _ = lat2.moments()
+    lat2.contact_angle(5.0)
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - te
     lat2.close()
     h2d = 2 * rr.size * 8
-    d2h = 2 * rr.size * 4 + (K // CONS_EVERY + 2) * 64
+    d2h = n_cons * 8 * 8 + 19 * 8
     e_units, e_secs = replicas.whole_job(nf * K, e2e_s, device="cuda")
     e2e = e_units / e_secs / 1e6
 
@@ -367,6 +381,8 @@ def run_ours(args):
     line["load_mass_rel_err"] = [float(cons_load[k] / m0[k] - 1) for k in (0, 1)]
     if args.workload.startswith("precision") and ws == 1 and not args.no_accuracy:
         line["accuracy"] = precision_accuracy(prec, 10000)
+    if args.workload == "single" and not args.no_samples:
+        line["samples"] = throughput_samples(K, Wm, peak)
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
@@ -384,8 +400,15 @@ def run_sweep(args):
 
     ws, rank, local = replicas.world()
     torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
     wl = WORKLOADS["sweep"]
-    boxes = W.sweep_boxes(wl["boxes"], seed=wl["seed"])
+    all_boxes = W.sweep_boxes(wl["boxes"], seed=wl["seed"])
+    # under torchrun each rank advances its round-robin share of the boxes (no data-path exchange)
+    idx = replicas.shard(range(len(all_boxes)), rank, ws)
+    boxes = [all_boxes[i] for i in idx]
     fields, params = [], []
     for bx in boxes:
         fields.append(W.droplet_fields(bx.edge, bx.edge, bx.edge, bx.radius, seed=bx.seed))
@@ -403,12 +426,15 @@ def run_sweep(args):
     best = (None, b_ty, b_planes)
     batch.step(Wm)
     torch.cuda.synchronize()
+    replicas.barrier()
     t0, t1 = ev(), ev()
     t0.record(stream)
     batch.step(K)
     t1.record(stream)
     torch.cuda.synchronize()
-    ms_batch = t0.elapsed_time(t1)
+    replicas.barrier()
+    units, secs = replicas.whole_job(nf * K, t0.elapsed_time(t1) * 1e-3, device="cuda")
+    ms_batch = secs * 1e3
     angles = batch.contact_angles(5.0)
     batch.close()
 
@@ -416,31 +442,147 @@ def run_sweep(args):
     for lat in lats:
         lat.step(Wm)
     torch.cuda.synchronize()
+    replicas.barrier()
     t0.record(stream)
     for lat in lats:
         lat.step(K)
     t1.record(stream)
     torch.cuda.synchronize()
-    ms_seq = t0.elapsed_time(t1)
+    replicas.barrier()
+    _, seq_secs = replicas.whole_job(nf * K, t0.elapsed_time(t1) * 1e-3, device="cuda")
+    ms_seq = seq_secs * 1e3
     for lat in lats:
         lat.close()
+    if dist:
+        got = [None] * ws
+        dist.all_gather_object(got, (idx, angles))
+        order = {}
+        for ix, an in got:
+            order.update(zip(ix, an))
+        angles = [order[i] for i in range(len(all_boxes))]
+        dist.destroy_process_group()
+    boxes = all_boxes
+    nf = sum(bx.edge * bx.edge * (bx.edge - 2) for bx in boxes)
     if rank != 0:
         return
-    value = nf * K / (ms_batch * 1e-3) / 1e6
+    value = units / secs / 1e6
     line = {
         "metric": METRIC, "value": round(value, 1), "unit": "MLUPS", "n_gpus": ws, "steps": K, "warmup": Wm,
-        "ms_per_step": round(ms_batch / K, 5), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "ms_per_step": round(ms_batch / K, 5), "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
         "dtype": wl["precision"], "data": "synthetic",
-        "config": {"workload": f"batched sweep: {len(boxes)} cubic boxes, edges from 48/64/80/96, R = 0.3 edge",
+        "config": {"workload": f"batched sweep: {len(boxes)} cubic boxes, edges from 48/64/80/96, R = 0.3 edge"
+                               + (f", round-robin over {ws} ranks" if ws > 1 else ""),
                    "fluid_nodes": nf, "schedule": {"tile": f"32x{best[1]}", "planes_per_item": best[2]},
                    "l2": "inputs larger than L2"},
         "sequential_mlups": round(nf * K / (ms_seq * 1e-3) / 1e6, 1),
         "speedup_vs_sequential": round(ms_seq / ms_batch, 3),
-        "roofline": {"bound": "hbm", "achieved": round(nf * 304 / (ms_batch / K * 1e-3) / 1e9, 1),
+        "roofline": {"bound": "hbm", "achieved": round(nf * 304 / (ms_batch / K * 1e-3) / 1e9 / ws, 1),
                      "peak": peaks()[0], "unit": "GB/s",
-                     "frac": round(nf * 304 / (ms_batch / K * 1e-3) / 1e9 / peaks()[0], 4)},
+                     "frac": round(nf * 304 / (ms_batch / K * 1e-3) / 1e9 / ws / peaks()[0], 4),
+                     "note": "per GPU" if ws > 1 else None},
         "theta_deg": [round(a["theta_deg"], 2) if a["ok"] else None for a in angles],
+        "droplets": droplet_validity(boxes, angles),
     }
+    print(json.dumps(line), flush=True)
+
+
+# a measured droplet whose phase contrast max(rho_r - rho_b) fell below this (from 0.66 initially) is a
+# diffuse, partly dissolved drop: its angle is reported but flagged
+CONTRAST_MIN = 0.3
+
+
+def droplet_validity(boxes, angles):
+    """Per-box validity of the sweep's angles: the library's status (why an angle
+    is missing) and a contrast check, with each invalid box's parameters."""
+    from paper_0910_3915_gb300 import lbsc
+    bad = []
+    for i, (bx, a) in enumerate(zip(boxes, angles)):
+        reason = None
+        if a["status"] != lbsc.LB_DROP_OK:
+            reason = lbsc.DROP_STATUS.get(a["status"], "status %d" % a["status"])
+        elif a["phi_max"] < CONTRAST_MIN:
+            reason = "diffuse: max(rho_r - rho_b) = %.3f < %.2f" % (a["phi_max"], CONTRAST_MIN)
+        if reason:
+            bad.append({"box": i, "edge": bx.edge, "g_br": round(bx.g_br, 4), "w": round(bx.w, 4), "reason": reason,
+                        "phi_max": round(a["phi_max"], 4),
+                        "theta_deg": round(a["theta_deg"], 2) if a["ok"] else None})
+    return {"valid": len(boxes) - len(bad), "total": len(boxes), "contrast_min": CONTRAST_MIN, "invalid": bad}
+
+
+def run_slabs(args):
+    """The lattice split into z slabs, one exchange of face messages per step."""
+    import torch
+
+    from paper_0910_3915_gb300 import lbsc, replicas, slabs
+    from paper_0910_3915_gb300 import workloads as W
+
+    ws, rank, local = replicas.world()
+    torch.cuda.set_device(local)
+    dist = None
+    wl = WORKLOADS["slabs"]
+    nx, ny, nz = wl["dims"]
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+        nz = (nz - 2) * ws + 2
+    prec = wl["precision"]
+    nf = nx * ny * (nz - 2)
+    er, eb = W.wall_split(wl["w"])
+    prm = dict(CONTACT, eta_wall_r=er, eta_wall_b=eb)
+    rr, rb = W.droplet_fields(nx, ny, nz, wl["radius"], seed=0)
+    K, Wm = args.steps, max(3, args.warmup)
+    stream = torch.cuda.current_stream()
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    ty, nty, seg = wl["schedule"]
+    if ws == 1:
+        dec = slabs.Slabs(rr, rb, wl["nslab"], prec).set_params(**prm).set_tiling(ty, nty, seg)
+    else:
+        dec = slabs.DistributedSlab(rr, rb, prec).set_params(**prm)
+        dec.lat.set_tiling(ty, nty, seg)
+    dec.step(Wm)
+    torch.cuda.synchronize()
+    replicas.barrier()
+    t0, t1 = ev(), ev()
+    t0.record(stream)
+    dec.step(K)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    replicas.barrier()
+    units, secs = replicas.whole_job(nx * ny * (dec.bounds[rank][1] - dec.bounds[rank][0]) * K if ws > 1 else nf * K,
+                                     t0.elapsed_time(t1) * 1e-3, device="cuda")
+    cons = dec.conservation()
+    single = None
+    if ws == 1:
+        dec.close()
+        lat = lbsc.Lattice(rr, rb, prec).set_params(**prm).set_tiling(ty, nty, seg)
+        lat.step(Wm)
+        torch.cuda.synchronize()
+        t0.record(stream)
+        lat.step(K)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        single = nf * K / (t0.elapsed_time(t1) * 1e-3) / 1e6
+        lat.close()
+    else:
+        dec.close()
+        dist.destroy_process_group()
+    if rank != 0:
+        return
+    value = units / secs / 1e6
+    line = {
+        "metric": METRIC, "value": round(value, 1), "unit": "MLUPS", "n_gpus": ws, "steps": K, "warmup": Wm,
+        "ms_per_step": round(secs * 1e3 / K, 5), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": prec, "data": "synthetic",
+        "config": {"workload": f"droplet {nx}x{ny}x{nz} R={wl['radius']:g} {prec.upper()} in "
+                               f"{wl['nslab'] if ws == 1 else ws} z slabs" + (" on one GPU" if ws == 1 else ", one per GPU"),
+                   "lattice": [nx, ny, nz], "fluid_nodes": nf,
+                   "schedule": {"tile": f"32x{ty}", "y_tiles": nty, "z_segments": seg},
+                   "exchange": "lattice to lattice (lb_halo_exchange)" if ws == 1 else "NCCL send/recv of face messages"},
+        "mass": [float(cons[0]), float(cons[1])],
+    }
+    if single is not None:
+        line["single_lattice_mlups"] = round(single, 1)
+        line["vs_single_lattice"] = round(value / single, 4)
     print(json.dumps(line), flush=True)
 
 
@@ -798,6 +940,75 @@ def run_young(args):
     print(json.dumps(line), flush=True)
 
 
+def throughput_samples(K: int, Wm: int, peak: float):
+    """Throughput of the 16-bit storage workload (256x256x128, R = 60, BF16 and
+    FP16) and of the batched sweep (64 boxes), the same K steps after Wm
+    warm-up steps, each tuned on itself and timed with CUDA events on its
+    stream. The roofline's achieved bandwidth counts the algorithmic bytes per
+    fluid-node update over the whole step (every kernel the step launches)."""
+    import torch
+
+    from paper_0910_3915_gb300 import lbsc, tune
+    from paper_0910_3915_gb300 import workloads as W
+
+    stream = torch.cuda.current_stream()
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    out = {}
+    for prec in ("bf16", "f16"):
+        wl = WORKLOADS["precision-" + prec]
+        nx, ny, nz = wl["dims"]
+        nf = nx * ny * (nz - 2)
+        er, eb = W.wall_split(wl["w"])
+        rr, rb = W.droplet_fields(nx, ny, nz, wl["radius"], seed=0)
+        lat = lbsc.Lattice(rr, rb, prec).set_params(**dict(CONTACT, eta_wall_r=er, eta_wall_b=eb))
+        sched, _ = tune.tune(lat, steps=32)
+        lat.step(Wm)
+        torch.cuda.synchronize()
+        a, b = ev(), ev()
+        a.record(stream)
+        lat.step(K)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / K
+        lat.close()
+        ach = nf * BYTES_PER_LU[prec] / (ms * 1e-3) / 1e9
+        out["precision_" + prec] = {
+            "workload": f"droplet {nx}x{ny}x{nz} R={wl['radius']:g} {prec.upper()} storage, FP32 arithmetic",
+            "value": round(nf / (ms * 1e-3) / 1e6, 1), "unit": "MLUPS", "steps": K, "ms_per_step": round(ms, 5),
+            "schedule": tune.name(sched),
+            "roofline": {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
+                         "frac": round(ach / peak, 4), "bytes_per_lu": BYTES_PER_LU[prec],
+                         "kernel": "whole step (TMA step kernel and ghost-row refresh)" if sched[0] == "tma"
+                         else "step_kernel"}}
+    wl = WORKLOADS["sweep"]
+    boxes = W.sweep_boxes(wl["boxes"], seed=wl["seed"])
+    fields, params = [], []
+    for bx in boxes:
+        fields.append(W.droplet_fields(bx.edge, bx.edge, bx.edge, bx.radius, seed=bx.seed))
+        er, eb = W.wall_split(bx.w)
+        params.append(lbsc.Params(g_br=bx.g_br, eta_wall_r=er, eta_wall_b=eb, force_weights=1, force_scale=1.25))
+    nf = sum(bx.edge * bx.edge * (bx.edge - 2) for bx in boxes)
+    batch = lbsc.Batch(fields, params, wl["precision"])
+    (b_ty, b_planes), _ = tune.tune_batch(batch, steps=32)
+    batch.step(Wm)
+    torch.cuda.synchronize()
+    a, b = ev(), ev()
+    a.record(stream)
+    batch.step(K)
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / K
+    batch.close()
+    ach = nf * 304 / (ms * 1e-3) / 1e9
+    out["sweep"] = {
+        "workload": f"batched sweep: {len(boxes)} cubic boxes, edges from 48/64/80/96, R = 0.3 edge, one launch a step",
+        "value": round(nf / (ms * 1e-3) / 1e6, 1), "unit": "MLUPS", "steps": K, "ms_per_step": round(ms, 5),
+        "schedule": {"tile": f"32x{b_ty}", "planes_per_item": b_planes},
+        "roofline": {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(ach / peak, 4), "bytes_per_lu": 304, "kernel": "batch_step_kernel"}}
+    return out
+
+
 def precision_accuracy(prec: str, steps: int):
     """16-bit storage against FP32 on the full lattice (the comparison with the
     FP64 oracle on the 64x64x32 copy is a test: tests/test_gpu_parity.py)."""
@@ -837,6 +1048,8 @@ def main():
         run_reference(args)
     elif args.workload == "sweep":
         run_sweep(args)
+    elif args.workload == "slabs":
+        run_slabs(args)
     elif args.workload == "adjoint":
         run_adjoint(args)
     elif args.workload == "angles":

@@ -87,9 +87,20 @@ typedef struct {
     double base_ref;      /* equivalent-circle diameter of {phi > 0} at the reference plane */
     double xc, yc, zc;    /* fitted sphere centre */
     double r_fit;         /* fitted sphere radius */
-    int ok;               /* 1 if theta_deg, h, b, r are defined */
+    int ok;               /* 1 if theta_deg, h, b, r are defined (status == LB_DROP_OK) */
     int n_points;         /* interface points in the sphere fit */
+    double phi_max;       /* max of rho_r - rho_b over fluid nodes (the droplet phase's contrast) */
+    double phi_min;       /* min of rho_r - rho_b over fluid nodes */
+    int status;           /* LB_DROP_*: why theta is missing, checked in this order */
 } lb_droplet;
+
+/* lb_droplet.status (the interface is phi = rho_r - rho_b = level) */
+#define LB_DROP_OK 0         /* a cap with its apex above the reference plane and a base there */
+#define LB_DROP_BAD_PLANE 1  /* the reference plane wall + offset (and the plane above it) is outside the lattice */
+#define LB_DROP_NO_PHASE 2   /* no fluid node has phi > level: the droplet phase has dissolved */
+#define LB_DROP_NO_APEX 3    /* phi > level somewhere, but never below a node with phi <= level */
+#define LB_DROP_LOW_APEX 4   /* the apex is not above the reference plane: a cap flatter than the offset */
+#define LB_DROP_NO_BASE 5    /* no phi > level area at the reference plane: the drop is detached */
 
 /* Create a context on the current CUDA device.
  * nx, ny, nz >= 1 (nz >= 3 with the default walls), and one population plane
@@ -104,6 +115,70 @@ typedef struct {
  * force, unit weights, force_scale 1. On error *out is NULL. */
 int lb_init(lb_ctx** out, int nx, int ny, int nz, int precision,
             const double* rho_r, const double* rho_b, void* cuda_stream);
+
+/* Re-initialise an existing context from new initial densities (host arrays
+ * of nx*ny*nz doubles, as lb_init), without allocating: populations at rest
+ * equilibrium, step count and device step counter back to 0. Geometry,
+ * parameters, schedule and (16-bit storage) the deviation references of
+ * lb_init stay. The densities are checked on the GPU: LB_ERR_ARG if one is
+ * negative or not finite (the populations are then undefined until the next
+ * successful reset). Host arrays in pinned memory copy asynchronously; the
+ * call synchronises the context's stream before it returns. */
+int lb_reset(lb_ctx* ctx, const double* rho_r, const double* rho_b);
+
+/* ------------------------------------------------------------ z-slab decomposition
+ * The update of a node needs only its nearest neighbours (Sec. 2), so a
+ * lattice splits into slabs of whole z planes with one exchange per step.
+ * A slab is a context of nx x ny x nz planes whose planes 1..nz-2 it owns.
+ * Plane 0 and plane nz-1 are either the solid wall layers of the whole
+ * lattice or halo planes: copies of the neighbouring slab's boundary plane,
+ * read for psi (the force at the owned boundary plane) and pushed into like
+ * fluid nodes, never updated by the slab's own step. After every step the
+ * two slabs of a face exchange one message each way (lb_halo_pack /
+ * lb_halo_unpack, or lb_halo_exchange lattice to lattice): the 5 crossing
+ * populations per component per face node and the 28 boundary-plane values
+ * the neighbour's halo plane takes; then the slabs' owned planes hold exactly
+ * what the whole lattice holds (bitwise: each node's arithmetic is the same).
+ * Stepping a slab further without the exchange leaves its boundary planes
+ * stale. Slabs always use the load-from-global step kernel and planar walls. */
+#define LB_HALO_BELOW 1 /* plane 0 is a halo plane (a neighbour below) */
+#define LB_HALO_ABOVE 2 /* plane nz-1 is a halo plane (a neighbour above) */
+
+/* Create a slab: as lb_init on the slab's nz planes (rho_r, rho_b: host,
+ * nx*ny*nz doubles, including the halo planes' initial densities, i.e. the
+ * neighbours' boundary planes). halo: LB_HALO_BELOW | LB_HALO_ABOVE as the
+ * slab has neighbours. zbase: index in the whole lattice of the slab's plane
+ * 0 (it keys 16-bit storage's rounding dither by the node's position in the
+ * whole lattice). ref: NULL, or the whole lattice's 16-bit deviation
+ * references {rho_ref_r, rho_ref_b} (its mean initial densities over fluid
+ * nodes), which every slab must share. */
+int lb_init_slab(lb_ctx** out, int nx, int ny, int nz, int precision, const double* rho_r, const double* rho_b,
+                 void* cuda_stream, int halo, int zbase, const double* ref);
+
+/* Bytes of one face message: 38 * nx * ny values in the storage format. */
+int lb_halo_bytes(lb_ctx* ctx, size_t* bytes);
+
+/* Enqueue (on the context's stream) the copy of this slab's outgoing message
+ * for face 0 (below) or 1 (above) into msg (device memory of lb_halo_bytes
+ * bytes): entries 0..9 the crossing populations (component a, i-th of the
+ * crossing velocities: entry 5a + i), entries 10..37 the boundary plane's
+ * values with c_z of that direction or 0 (entry 10 + 14a + i), x fastest.
+ * LB_ERR_STATE if the slab has no halo plane on that face. */
+int lb_halo_pack(lb_ctx* ctx, int face, void* msg);
+
+/* Enqueue the application of the neighbour's message (its lb_halo_pack of
+ * the facing side) on face 0 (below) or 1 (above). */
+int lb_halo_unpack(lb_ctx* ctx, int face, const void* msg);
+
+/* Both messages of one face, lattice to lattice, in one kernel: `below` has
+ * a halo plane above, `above` one below; same nx, ny, precision and stream
+ * (the same device, or devices with peer access to each other's memory). */
+int lb_halo_exchange(lb_ctx* below, lb_ctx* above);
+
+/* nsteps steps of a lattice split into nslab slabs (ordered bottom to top,
+ * halo planes exactly on their inner faces, one stream): each step steps
+ * every slab and then exchanges every face. */
+int lb_slabs_step(lb_ctx* const* slabs, int nslab, int nsteps);
 
 /* Bytes of device memory lb_init_external needs for this lattice. */
 int lb_required_bytes(int nx, int ny, int nz, int precision, size_t* bytes);

@@ -50,6 +50,8 @@ struct lb_ctx {
     int* dev_err = nullptr;                  // device status word of the step kernels
     uint32_t* clock = nullptr;               // device step counter {steps mod 2^32, done-ticket}
     bool ghost_ok = true;                    // ghost images of the current buffer are current
+    int halo = 0;                            // z slab: bit 0 plane 0, bit 1 plane nz-1 is a halo plane
+    uint32_t hkey = 0;                       // z slab: its planes' offset in the whole lattice (dither key)
     static constexpr int kGraphSteps = 32;
     std::string err;
 };
@@ -218,7 +220,8 @@ static cudaError_t tma_prepare(lb_ctx* c)
 // stages used by the TMA kernel for the current schedule, 0 if not available
 static int tma_stages(lb_ctx* c)
 {
-    if (c->general || c->variant != LB_STEP_TMA) return 0;  // AUTO: load-from-global (measured faster)
+    // AUTO: load-from-global (measured faster); z slabs always load from global
+    if (c->general || c->halo || c->variant != LB_STEP_TMA) return 0;
     const int want[2] = {c->stages ? c->stages : 3, c->stages ? c->stages : 2};
     for (int ns : want) {
         // occupancy 0: the pair is not built for this precision (or does not fit)
@@ -293,6 +296,8 @@ static StepArgs<S> step_args(lb_ctx* c, int src)
     A.zlo = c->zlo;
     A.zhi = c->zhi;
     A.nseg = nseg_for(c, A.tiles_x * A.tiles_y);
+    A.halo = c->halo;
+    A.hkey = c->hkey;
     return A;
 }
 
@@ -355,9 +360,9 @@ static cudaError_t launch_steps(lb_ctx* c, int n, int& parity, cudaStream_t st)
 }
 
 template <class S>
-static cudaError_t run_init(lb_ctx* c, const double* drr, const double* drb)
+static cudaError_t run_init(lb_ctx* c, const double* drr, const double* drb, int* err = nullptr)
 {
-    return launch_init<S>(field_args(c), (S*)c->f[0], drr, drb, c->stream);
+    return launch_init<S>(field_args(c), (S*)c->f[0], drr, drb, c->stream, err);
 }
 
 static int planar_default(lb_ctx* c)
@@ -378,8 +383,13 @@ static int planar_default(lb_ctx* c)
     return LB_OK;
 }
 
+extern "C" {
+static int check_device_status(lb_ctx* c);
+}
+
 static int init_common(lb_ctx** out, int nx, int ny, int nz, int precision, const double* rho_r,
-                       const double* rho_b, void* stream, void* ext, size_t ext_bytes)
+                       const double* rho_b, void* stream, void* ext, size_t ext_bytes, int halo = 0, int zbase = 0,
+                       const double* ref = nullptr)
 {
     if (!out) return fail(nullptr, LB_ERR_ARG, "lb_init: out is NULL");
     *out = nullptr;
@@ -459,8 +469,10 @@ static int init_common(lb_ctx** out, int nx, int ny, int nz, int precision, cons
             sum[1] += rho_b[i];
             ++cnt;
         }
-    c->kp.ref[0] = precision == LB_F32 ? 0.f : (float)(sum[0] / (double)cnt);
-    c->kp.ref[1] = precision == LB_F32 ? 0.f : (float)(sum[1] / (double)cnt);
+    c->kp.ref[0] = precision == LB_F32 ? 0.f : (float)(ref ? ref[0] : sum[0] / (double)cnt);
+    c->kp.ref[1] = precision == LB_F32 ? 0.f : (float)(ref ? ref[1] : sum[1] / (double)cnt);
+    c->halo = halo;
+    c->hkey = (uint32_t)((uint64_t)zbase * (uint64_t)c->L.plane);
     c->prm = lb_params{1.0, 1.0, 0.0, 0.0, 0.0, LB_WEIGHTS_UNIT, 1.0};
     set_kparams(c);
 
@@ -506,9 +518,116 @@ int lb_init_external(lb_ctx** out, int nx, int ny, int nz, int precision, const 
     return init_common(out, nx, ny, nz, precision, rho_r, rho_b, cuda_stream, device_buffer, buffer_bytes);
 }
 
+int lb_init_slab(lb_ctx** out, int nx, int ny, int nz, int precision, const double* rho_r, const double* rho_b,
+                 void* cuda_stream, int halo, int zbase, const double* ref)
+{
+    if (halo < 0 || halo > (LB_HALO_BELOW | LB_HALO_ABOVE))
+        return fail(nullptr, LB_ERR_ARG, "lb_init_slab: halo must be a combination of LB_HALO_BELOW and LB_HALO_ABOVE");
+    if (nz < 3 || zbase < 0) return fail(nullptr, LB_ERR_ARG, "lb_init_slab: a slab needs nz >= 3 and zbase >= 0");
+    if (ref && !(std::isfinite(ref[0]) && std::isfinite(ref[1])))
+        return fail(nullptr, LB_ERR_ARG, "lb_init_slab: reference densities must be finite");
+    return init_common(out, nx, ny, nz, precision, rho_r, rho_b, cuda_stream, nullptr, 0, halo, zbase, ref);
+}
+
+int lb_halo_bytes(lb_ctx* c, size_t* bytes)
+{
+    if (!c || !bytes) return fail(c, LB_ERR_ARG, "lb_halo_bytes: NULL argument");
+    *bytes = (size_t)kHaloEntries * c->nx * c->ny * elem_size(c->prec);
+    return LB_OK;
+}
+
+static int halo_copy(lb_ctx* c, int face, void* msg, int unpack, const char* who)
+{
+    if (!c || !msg || (face != 0 && face != 1)) return fail(c, LB_ERR_ARG, std::string(who) + ": bad argument");
+    if (!(c->halo & (1 << face))) return fail(c, LB_ERR_STATE, std::string(who) + ": no halo plane on that face");
+    LB_CUDA(c, launch_halo_copy(c->L, c->f[c->cur], elem_size(c->prec), msg, face, unpack, c->stream));
+    return LB_OK;
+}
+
+int lb_halo_pack(lb_ctx* c, int face, void* msg) { return halo_copy(c, face, msg, 0, "lb_halo_pack"); }
+
+int lb_halo_unpack(lb_ctx* c, int face, const void* msg)
+{
+    return halo_copy(c, face, const_cast<void*>(msg), 1, "lb_halo_unpack");
+}
+
+static bool slab_pair_ok(const lb_ctx* a, const lb_ctx* b)
+{
+    return a && b && a != b && a->nx == b->nx && a->ny == b->ny && a->prec == b->prec && a->L.px == b->L.px &&
+           (a->halo & LB_HALO_ABOVE) && (b->halo & LB_HALO_BELOW);
+}
+
+int lb_halo_exchange(lb_ctx* below, lb_ctx* above)
+{
+    if (!slab_pair_ok(below, above))
+        return fail(below, LB_ERR_ARG, "lb_halo_exchange: need a slab with a halo above and one with a halo below, "
+                                       "same nx, ny and precision");
+    if (below->stream != above->stream)
+        return fail(below, LB_ERR_ARG, "lb_halo_exchange: the two slabs must share one stream");
+    LB_CUDA(below, launch_halo_exchange(below->L, below->f[below->cur], above->L, above->f[above->cur],
+                                        elem_size(below->prec), below->stream));
+    return LB_OK;
+}
+
+int lb_slabs_step(lb_ctx* const* slabs, int nslab, int nsteps)
+{
+    if (!slabs || nslab < 1 || nsteps < 0) return fail(nullptr, LB_ERR_ARG, "lb_slabs_step: bad argument");
+    for (int i = 0; i < nslab; ++i) {
+        if (!slabs[i]) return fail(nullptr, LB_ERR_ARG, "lb_slabs_step: NULL slab");
+        const int want = (i > 0 ? LB_HALO_BELOW : 0) | (i + 1 < nslab ? LB_HALO_ABOVE : 0);
+        if (slabs[i]->halo != want || slabs[i]->stream != slabs[0]->stream)
+            return fail(slabs[i], LB_ERR_ARG, "lb_slabs_step: slabs must be ordered bottom to top, with halo planes "
+                                              "exactly on their inner faces, on one stream");
+        if (i > 0 && !slab_pair_ok(slabs[i - 1], slabs[i]))
+            return fail(slabs[i], LB_ERR_ARG, "lb_slabs_step: neighbouring slabs differ in nx, ny or precision");
+    }
+    for (int t = 0; t < nsteps; ++t) {
+        for (int i = 0; i < nslab; ++i) {
+            const int rc = lb_step(slabs[i], 1);
+            if (rc != LB_OK) return rc;
+        }
+        for (int i = 0; i + 1 < nslab; ++i) {
+            const int rc = lb_halo_exchange(slabs[i], slabs[i + 1]);
+            if (rc != LB_OK) return rc;
+        }
+    }
+    return LB_OK;
+}
+
+int lb_reset(lb_ctx* c, const double* rho_r, const double* rho_b)
+{
+    if (!c || !rho_r || !rho_b) return fail(c, LB_ERR_ARG, "lb_reset: NULL argument");
+    const long long N = (long long)c->nx * c->ny * c->nz;
+    // stage the densities in the scratch fields (FP64: 2 N doubles fit in 10 N floats)
+    double* drr = (double*)c->W.rho[0];
+    double* drb = drr + N;
+    LB_CUDA(c, cudaMemcpyAsync(drr, rho_r, N * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    LB_CUDA(c, cudaMemcpyAsync(drb, rho_b, N * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    cudaError_t e;
+    switch (c->prec) {
+    case LB_F32: e = run_init<float>(c, drr, drb, c->dev_err); break;
+    case LB_F16: e = run_init<__half>(c, drr, drb, c->dev_err); break;
+    default: e = run_init<__nv_bfloat16>(c, drr, drb, c->dev_err); break;
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "lb_reset: init");
+    LB_CUDA(c, launch_clock_set(c->clock, 0, c->stream));
+    LB_CUDA(c, cudaStreamSynchronize(c->stream));
+    c->cur = 0;
+    c->steps = 0;
+    c->ghost_ok = true;  // the initial populations fill the ghost images
+    int h = 0;
+    LB_CUDA(c, cudaMemcpy(&h, c->dev_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (h & kErrInput) {
+        LB_CUDA(c, cudaMemset(c->dev_err, 0, sizeof(int)));
+        return fail(c, LB_ERR_ARG, "lb_reset: densities must be finite and non-negative");
+    }
+    return check_device_status(c);
+}
+
 int lb_set_geometry(lb_ctx* c, const uint8_t* solid)
 {
     if (!c || !solid) return fail(c, LB_ERR_ARG, "lb_set_geometry: NULL argument");
+    if (c->halo) return fail(c, LB_ERR_UNSUPPORTED, "lb_set_geometry: a z slab keeps the planar walls");
     const int nx = c->nx, ny = c->ny, nz = c->nz;
     const long long N = (long long)nx * ny * nz, NP = (long long)nx * ny;
     long long fluid = 0;
@@ -648,8 +767,6 @@ int lb_step(lb_ctx* c, int nsteps)
     return LB_OK;
 }
 
-static int check_device_status(lb_ctx* c);
-
 int lb_sync(lb_ctx* c)
 {
     if (!c) return fail(c, LB_ERR_ARG, "lb_sync: NULL context");
@@ -677,6 +794,19 @@ static cudaError_t dispatch_cons(lb_ctx* c)
     case LB_F32: return run_cons<float>(c);
     case LB_F16: return run_cons<__half>(c);
     default: return run_cons<__nv_bfloat16>(c);
+    }
+}
+template <class S>
+static cudaError_t run_rho(lb_ctx* c)
+{
+    return launch_rho<S>(field_args(c), (const S*)c->f[c->cur], c->W, c->stream);
+}
+static cudaError_t dispatch_rho(lb_ctx* c)
+{
+    switch (c->prec) {
+    case LB_F32: return run_rho<float>(c);
+    case LB_F16: return run_rho<__half>(c);
+    default: return run_rho<__nv_bfloat16>(c);
     }
 }
 static cudaError_t dispatch_fields(lb_ctx* c, bool vel)
@@ -763,7 +893,7 @@ int lb_contact_angle_at(lb_ctx* c, double offset, double level, lb_droplet* out)
         return fail(c, LB_ERR_ARG, "lb_contact_angle: bad argument");
     memset(out, 0, sizeof(*out));
     const double zw = 0.5, zref = zw + offset;
-    LB_CUDA(c, dispatch_fields(c, false));
+    LB_CUDA(c, dispatch_rho(c));
     LB_CUDA(c, launch_angle(field_args(c), c->W, zref, level, c->part, c->red, c->stream));
     LB_CUDA(c, cudaMemcpyAsync(c->h_red, c->red, kAngleVals * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     LB_CUDA(c, cudaStreamSynchronize(c->stream));
@@ -775,8 +905,16 @@ int lb_contact_angle_at(lb_ctx* c, double offset, double level, lb_droplet* out)
     const double bref = 2.0 * std::sqrt(area / pi), hp = h - offset;
     out->h = h;
     out->base_ref = bref;
+    out->phi_max = v[17];
+    out->phi_min = -v[18];
     const int z0 = (int)std::floor(zref);
-    if (top > -1e299 && z0 >= 0 && z0 + 1 < c->nz && hp > 0 && bref > 0) {
+    if (!(z0 >= 0 && z0 + 1 < c->nz)) out->status = LB_DROP_BAD_PLANE;
+    else if (!(v[17] > -1e299) || !((double)v[17] - level > 0)) out->status = LB_DROP_NO_PHASE;
+    else if (!(top > -1e299)) out->status = LB_DROP_NO_APEX;
+    else if (!(hp > 0)) out->status = LB_DROP_LOW_APEX;
+    else if (!(bref > 0)) out->status = LB_DROP_NO_BASE;
+    else out->status = LB_DROP_OK;
+    if (out->status == LB_DROP_OK) {
         // cap above the reference plane: height hp, base bref -> sphere radius (Fig. 2 relation)
         const double r = (0.25 * bref * bref + hp * hp) / (2.0 * hp);
         const double arg = r * r - (r - h) * (r - h);

@@ -82,15 +82,19 @@ __device__ __forceinline__ bool node_solid(const FieldArgs& F, int x, int y, int
 }
 
 // ---------------------------------------------------------------- init
-// populations at rest: n_k = zeta_k rho (Eq. Equil at u = 0)
+// populations at rest: n_k = zeta_k rho (Eq. Equil at u = 0). err (may be
+// NULL): kErrInput is set for a density that is negative or not finite.
 template <class S>
-__global__ void init_kernel(FieldArgs F, S* __restrict__ f, const double* __restrict__ rr, const double* __restrict__ rb)
+__global__ void init_kernel(FieldArgs F, S* __restrict__ f, const double* __restrict__ rr, const double* __restrict__ rb,
+                            int* err)
 {
     const long long N = (long long)F.L.nx * F.L.ny * F.L.nz;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
         const int x = (int)(i % F.L.nx), y = (int)((i / F.L.nx) % F.L.ny), z = (int)(i / ((long long)F.L.nx * F.L.ny));
         for (int a = 0; a < 2; ++a) {
-            const float rho = (float)(a == 0 ? rr[i] : rb[i]);
+            const double d = a == 0 ? rr[i] : rb[i];
+            if (err && !(isfinite(d) && d >= 0.0)) atomicOr(err, kErrInput);
+            const float rho = (float)d;
             for (int k = 0; k < Q; ++k) {
                 float v;
                 if constexpr (Codec<S>::kDeviation) v = rho - F.P.ref[a];
@@ -103,45 +107,56 @@ __global__ void init_kernel(FieldArgs F, S* __restrict__ f, const double* __rest
 
 // ---------------------------------------------------------------- conservation
 // cons = {M_r, M_b, Px, Py, Pz, non-finite count, fluid nodes, -}
-// Warp w of the fixed grid takes lattice rows (y, z) = w, w + nwarps, ...;
-// its lanes step along x. A node's mass and momentum are summed in FP32 over
-// its 19 values, then added into per-thread FP64 sums (two masses and the
-// total momentum: five FP64 additions a node); the counts stay integers.
+// A grid-stride walk over the nodes of the fluid planes, x fastest, so that a
+// warp's load of one population slot covers consecutive addresses; every
+// thread of the fixed grid takes nodes t, t + T, t + 2T, ... (T threads), with
+// its 38 loads of a node independent of each other. A node's mass and
+// momentum are summed in FP32 over its 19 values per component, then added
+// into per-thread FP64 sums (two masses and the total momentum: five FP64
+// additions a node); the counts stay integers. Fixed grid, fixed per-thread
+// order, fixed block tree and final pass: the sums do not depend on scheduling.
 template <class S>
 __global__ void __launch_bounds__(kRedThreads) cons_kernel(FieldArgs F, const S* __restrict__ f, double* __restrict__ part)
 {
     double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     int bad = 0, fluid = 0;
-    const int nx = F.L.nx, ny = F.L.ny, rows = F.L.ny * F.L.nz;
-    const int lane = threadIdx.x & 31;
-    const int nwarps = gridDim.x * (kRedThreads / 32);
-    for (int r = blockIdx.x * (kRedThreads / 32) + (threadIdx.x >> 5); r < rows; r += nwarps) {
-        const int y = r % ny, z = r / ny;
-        for (int x = lane; x < nx; x += 32) {
-            const long long off = F.L.off(x, y, z);
-            if (node_solid(F, x, y, z, off)) continue;
-            ++fluid;
-            float rho[2], j[3] = {0.f, 0.f, 0.f};
+    const int nx = F.L.nx, ny = F.L.ny;
+    const int zlo = F.general ? 0 : 1, zhi = F.general ? F.L.nz : F.L.nz - 1;
+    const unsigned nxy = (unsigned)nx * (unsigned)ny;
+    const unsigned n = nxy * (unsigned)(zhi - zlo);  // below 2^31 (the layout's limit)
+    const unsigned T = gridDim.x * blockDim.x;
+    const long long slot = F.L.slot;
+    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += T) {
+        const unsigned zr = i / nxy, rem = i - zr * nxy;
+        const int y = (int)(rem / (unsigned)nx), x = (int)(rem - (unsigned)y * nx), z = zlo + (int)zr;
+        const long long off = F.L.off(x, y, z);
+        if (F.general && (F.nbmask[off] & kSelfSolid)) continue;
+        ++fluid;
+        float v[2][Q];
 #pragma unroll
-            for (int a = 0; a < 2; ++a) {
-                float m = 0.f;
+        for (int a = 0; a < 2; ++a)
 #pragma unroll
-                for (int k = 0; k < Q; ++k) {
-                    const float n = decode<S>(f + (long long)(a * Q + k) * F.L.slot + off, k, F.P.ref[a]);
-                    bad += isfinite(n) ? 0 : 1;
-                    m += n;
-                    if (cx(k)) j[0] += cx(k) * n;
-                    if (cy(k)) j[1] += cy(k) * n;
-                    if (cz(k)) j[2] += cz(k) * n;
-                }
-                rho[a] = m;
+            for (int k = 0; k < Q; ++k) v[a][k] = decode<S>(f + (long long)(a * Q + k) * slot + off, k, F.P.ref[a]);
+        float rho[2], j[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+        for (int a = 0; a < 2; ++a) {
+            float m = 0.f;
+#pragma unroll
+            for (int k = 0; k < Q; ++k) {
+                const float nk = v[a][k];
+                bad += isfinite(nk) ? 0 : 1;
+                m += nk;
+                if (cx(k)) j[0] += cx(k) * nk;
+                if (cy(k)) j[1] += cy(k) * nk;
+                if (cz(k)) j[2] += cz(k) * nk;
             }
-            acc[0] += rho[0];
-            acc[1] += rho[1];
-            acc[2] += j[0];
-            acc[3] += j[1];
-            acc[4] += j[2];
+            rho[a] = m;
         }
+        acc[0] += rho[0];
+        acc[1] += rho[1];
+        acc[2] += j[0];
+        acc[3] += j[1];
+        acc[4] += j[2];
     }
     acc[5] = bad;
     acc[6] = fluid;
@@ -208,39 +223,94 @@ __global__ void velocity_kernel(FieldArgs F, Scratch W)
     }
 }
 
+// rho^r and rho^b of every node into the scratch fields (0 on solid nodes):
+// the contact angle needs phi = rho_r - rho_b only
+template <class S>
+__global__ void rho_kernel(FieldArgs F, const S* __restrict__ f, Scratch W)
+{
+    const int nx = F.L.nx, ny = F.L.ny;
+    const unsigned nxy = (unsigned)nx * (unsigned)ny;
+    const unsigned N = nxy * (unsigned)F.L.nz;
+    const unsigned T = gridDim.x * blockDim.x;
+    const long long slot = F.L.slot;
+    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += T) {
+        const unsigned z = i / nxy, rem = i - z * nxy;
+        const int y = (int)(rem / (unsigned)nx), x = (int)(rem - (unsigned)y * nx);
+        const long long off = F.L.off(x, y, (int)z);
+        float rho[2] = {0.f, 0.f};
+        if (!node_solid(F, x, y, (int)z, off)) {
+            float v[2][Q];
+#pragma unroll
+            for (int a = 0; a < 2; ++a)
+#pragma unroll
+                for (int k = 0; k < Q; ++k) v[a][k] = decode<S>(f + (long long)(a * Q + k) * slot + off, k, F.P.ref[a]);
+#pragma unroll
+            for (int a = 0; a < 2; ++a)
+#pragma unroll
+                for (int k = 0; k < Q; ++k) rho[a] += v[a][k];
+        }
+        W.rho[0][i] = rho[0];
+        W.rho[1][i] = rho[1];
+    }
+}
+
 // ---------------------------------------------------------------- contact angle
-// Per column (x, y): top phi = 0 crossing (max), positive length of the
-// reference-plane interpolant along x, and sphere-fit sums of interface points.
-// acc = {top, area, npts, M00, M01, M02, M03, M11, M12, M13, M22, M23, M33, v0, v1, v2, v3}
+// phi - level at a node, in FP64 from the FP32 densities (as the host finish uses it)
+__device__ __forceinline__ double phi_at(float r, float b, double level) { return (double)r - (double)b - level; }
+
+// phi - level > 0, decided in FP32 where the margin is far above FP32's
+// rounding, else in FP64 exactly as phi_at: (double)r - (double)b - level > 0
+// holds iff the exact r - b exceeds level, and the FP32 difference is within
+// about 2^-23 (|r - b| + |level|) of it, far inside the 1e-5 margin. Bulk nodes
+// therefore need no FP64 arithmetic (slow on this GPU); the decisions are the
+// ones the FP64 expression takes.
+__device__ __forceinline__ bool phi_pos(float r, float b, float lf, double level)
+{
+    const float d = r - b;
+    const float m = d - lf;
+    if (fabsf(m) > 1e-5f * (fabsf(d) + fabsf(lf)) + 1e-30f) return m > 0.f;
+    return phi_at(r, b, level) > 0.0;
+}
+
+// One thread per node (grid-stride, x fastest), reading rho^r, rho^b of the
+// node and of its +x, +y, +z neighbours:
+//  acc[0]  (max) top phi = level crossing: z + p0/(p0 - p1) where phi > level
+//          below and <= level above (both nodes fluid);
+//  acc[1]  positive length along x of the reference-plane interpolant of
+//          phi (the node at z0 adds its segment to x + 1, periodic);
+//  acc[2..16] sphere-fit sums over crossings along +x, +y, +z at or above
+//          the reference plane: count, the 10 upper entries of M = sum row row^T
+//          and the 4 of v = sum row |p|^2, row = (2p, 1);
+//  acc[17] (max) max of rho_r - rho_b over fluid nodes, acc[18] (max) of
+//          rho_b - rho_r (the phase contrast, a validity check).
 __global__ void __launch_bounds__(kRedThreads) angle_kernel(FieldArgs F, Scratch W, double zref, double level,
                                                             double* __restrict__ part)
 {
     const int nx = F.L.nx, ny = F.L.ny, nz = F.L.nz;
     double acc[kAngleVals];
+#pragma unroll
     for (int i = 0; i < kAngleVals; ++i) acc[i] = 0.0;
     acc[0] = -1e300;
+    float dmax = -3.0e38f, dmin = 3.0e38f;
     const int z0 = (int)floor(zref);
     const double fz = zref - z0;
-    auto phi = [&](int x, int y, int z) -> double {
-        const long long i = (long long)x + (long long)nx * (y + (long long)ny * z);
-        return (double)W.rho[0][i] - (double)W.rho[1][i] - level;
-    };
-    auto solid = [&](int x, int y, int z) -> bool {
-        const long long off = F.L.off(x, y, z);
-        return node_solid(F, x, y, z, off);
-    };
-    const long long ncols = (long long)nx * ny;
-    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncols; c += (long long)gridDim.x * blockDim.x) {
-        const int x = (int)(c % nx), y = (int)(c / nx);
-        for (int z = 0; z + 1 < nz; ++z) {
-            if (solid(x, y, z) || solid(x, y, z + 1)) continue;
-            const double p0 = phi(x, y, z), p1 = phi(x, y, z + 1);
-            if (p0 > 0 && p1 <= 0) acc[0] = fmax(acc[0], z + p0 / (p0 - p1));
-        }
-        if (z0 >= 0 && z0 + 1 < nz) {
-            const int x1 = (x + 1) % nx;
-            const double a0 = (1 - fz) * phi(x, y, z0) + fz * phi(x, y, z0 + 1);
-            const double a1 = (1 - fz) * phi(x1, y, z0) + fz * phi(x1, y, z0 + 1);
+    const float lf = (float)level;
+    const float* __restrict__ R = W.rho[0];
+    const float* __restrict__ B = W.rho[1];
+    const unsigned nxy = (unsigned)nx * (unsigned)ny;
+    const unsigned N = nxy * (unsigned)nz;
+    const unsigned T = gridDim.x * blockDim.x;
+    auto solid = [&](int x, int y, int z) -> bool { return node_solid(F, x, y, z, F.L.off(x, y, z)); };
+    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += T) {
+        const int z = (int)(i / nxy);
+        const unsigned rem = i - (unsigned)z * nxy;
+        const int y = (int)(rem / (unsigned)nx), x = (int)(rem - (unsigned)y * nx);
+        const float r0 = R[i], b0 = B[i];
+        if (z == z0 && z0 + 1 < nz) {  // reference plane: every column, solid or not
+            const int x1 = x + 1 < nx ? x + 1 : 0;
+            const unsigned i1 = i - x + x1;
+            const double a0 = (1 - fz) * phi_at(r0, b0, level) + fz * phi_at(R[i + nxy], B[i + nxy], level);
+            const double a1 = (1 - fz) * phi_at(R[i1], B[i1], level) + fz * phi_at(R[i1 + nxy], B[i1 + nxy], level);
             double len;
             if (a0 > 0 && a1 > 0) len = 1.0;
             else if (a0 <= 0 && a1 <= 0) len = 0.0;
@@ -248,28 +318,39 @@ __global__ void __launch_bounds__(kRedThreads) angle_kernel(FieldArgs F, Scratch
             else len = a1 / (a1 - a0);
             acc[1] += len;
         }
-        for (int z = 0; z < nz; ++z) {
-            if (solid(x, y, z)) continue;
-            const double p0 = phi(x, y, z);
-            for (int d = 0; d < 3; ++d) {
-                const int x1 = x + (d == 0), y1 = y + (d == 1), z1 = z + (d == 2);
-                if (x1 >= nx || y1 >= ny || z1 >= nz || solid(x1, y1, z1)) continue;
-                const double p1 = phi(x1, y1, z1);
-                if ((p0 > 0) == (p1 > 0)) continue;
-                const double t = p0 / (p0 - p1);
-                const double pxv = x + t * (d == 0), pyv = y + t * (d == 1), pzv = z + t * (d == 2);
-                if (pzv < zref) continue;
-                const double row[4] = {2 * pxv, 2 * pyv, 2 * pzv, 1.0};
-                const double rhs = pxv * pxv + pyv * pyv + pzv * pzv;
-                acc[2] += 1.0;
-                int m = 3;
-                for (int r = 0; r < 4; ++r)
-                    for (int q = r; q < 4; ++q) acc[m++] += row[r] * row[q];
-                for (int r = 0; r < 4; ++r) acc[13 + r] += row[r] * rhs;
-            }
+        if (solid(x, y, z)) continue;
+        const float d0 = r0 - b0;
+        dmax = fmaxf(dmax, d0);
+        dmin = fminf(dmin, d0);
+        const bool s0 = phi_pos(r0, b0, lf, level);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const int x1 = x + (d == 0), y1 = y + (d == 1), z1 = z + (d == 2);
+            if (x1 >= nx || y1 >= ny || z1 >= nz || solid(x1, y1, z1)) continue;
+            const unsigned j = d == 0 ? i + 1 : (d == 1 ? i + nx : i + nxy);
+            const float r1 = R[j], b1 = B[j];
+            const bool s1 = phi_pos(r1, b1, lf, level);
+            if (s0 == s1) continue;
+            const double p0 = phi_at(r0, b0, level), p1 = phi_at(r1, b1, level);
+            const double t = p0 / (p0 - p1);
+            if (d == 2 && s0) acc[0] = fmax(acc[0], z + t);  // phi > level below, <= level above
+            const double pxv = x + t * (d == 0), pyv = y + t * (d == 1), pzv = z + t * (d == 2);
+            if (pzv < zref) continue;
+            const double row[4] = {2 * pxv, 2 * pyv, 2 * pzv, 1.0};
+            const double rhs = pxv * pxv + pyv * pyv + pzv * pzv;
+            acc[2] += 1.0;
+            int m = 3;
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int q = r; q < 4; ++q) acc[m++] += row[r] * row[q];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) acc[13 + r] += row[r] * rhs;
         }
     }
-    block_reduce<kAngleVals>(acc, 1u, part);
+    acc[17] = dmax > -3.0e38f ? (double)dmax : -1e300;
+    acc[18] = dmin < 3.0e38f ? -(double)dmin : -1e300;
+    block_reduce<kAngleVals>(acc, kAngleMaxMask, part);
 }
 
 // ---------------------------------------------------------------- pressure tensor
@@ -480,10 +561,10 @@ cudaError_t launch_clock_set(uint32_t* clk, uint32_t v, cudaStream_t st)
 }
 
 template <class S>
-cudaError_t launch_init(const FieldArgs& F, S* f, const double* rr, const double* rb, cudaStream_t st)
+cudaError_t launch_init(const FieldArgs& F, S* f, const double* rr, const double* rb, cudaStream_t st, int* err)
 {
     const long long N = (long long)F.L.nx * F.L.ny * F.L.nz;
-    init_kernel<S><<<grid_for(N, 256, 65536), 256, 0, st>>>(F, f, rr, rb);
+    init_kernel<S><<<grid_for(N, 256, 65536), 256, 0, st>>>(F, f, rr, rb, err);
     return cudaGetLastError();
 }
 
@@ -504,11 +585,19 @@ cudaError_t launch_fields(const FieldArgs& F, const S* f, const Scratch& W, bool
     return cudaGetLastError();
 }
 
+template <class S>
+cudaError_t launch_rho(const FieldArgs& F, const S* f, const Scratch& W, cudaStream_t st)
+{
+    const long long N = (long long)F.L.nx * F.L.ny * F.L.nz;
+    rho_kernel<S><<<grid_for(N, 256, 65536), 256, 0, st>>>(F, f, W);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_angle(const FieldArgs& F, const Scratch& W, double zref, double level, double* part, double* out,
                          cudaStream_t st)
 {
     angle_kernel<<<kRedBlocks, kRedThreads, 0, st>>>(F, W, zref, level, part);
-    finish_kernel<kAngleVals><<<1, kRedThreads, 0, st>>>(part, kRedBlocks, 1u, out);
+    finish_kernel<kAngleVals><<<1, kRedThreads, 0, st>>>(part, kRedBlocks, kAngleMaxMask, out);
     return cudaGetLastError();
 }
 
@@ -555,9 +644,10 @@ cudaError_t launch_pressure_radial(const FieldArgs& F, const void* f, int prec, 
 }
 
 #define LBSC_INST(S)                                                                                  \
-    template cudaError_t launch_init<S>(const FieldArgs&, S*, const double*, const double*, cudaStream_t); \
+    template cudaError_t launch_init<S>(const FieldArgs&, S*, const double*, const double*, cudaStream_t, int*); \
     template cudaError_t launch_conservation<S>(const FieldArgs&, const S*, double*, double*, cudaStream_t); \
     template cudaError_t launch_fields<S>(const FieldArgs&, const S*, const Scratch&, bool, cudaStream_t); \
+    template cudaError_t launch_rho<S>(const FieldArgs&, const S*, const Scratch&, cudaStream_t);      \
     template cudaError_t launch_get_pop<S>(const FieldArgs&, const S*, double*, cudaStream_t);       \
     template cudaError_t launch_set_pop<S>(const FieldArgs&, S*, const double*, cudaStream_t);   \
     template cudaError_t launch_ghosts<S>(const Layout&, S*, int, int, cudaStream_t);                 \

@@ -9,7 +9,8 @@ namespace lbsc {
 
 constexpr int kRedThreads = 256;  // threads per reduction block
 constexpr int kRedBlocks = 512;   // fixed grid of the reductions: fixed summation order
-constexpr int kAngleVals = 17;    // contact-angle partial sums per block
+constexpr int kAngleVals = 19;    // contact-angle partial sums per block
+constexpr uint32_t kAngleMaxMask = (1u << 0) | (1u << 17) | (1u << 18);  // max-reduced entries of the 19
 
 // Geometry and parameters for the non-step kernels.
 struct FieldArgs {
@@ -72,11 +73,15 @@ cudaError_t launch_clock_set(uint32_t* clk, uint32_t v, cudaStream_t st);
 template <class S>
 cudaError_t launch_ghosts(const Layout& L, S* f, int z0, int z1, cudaStream_t st);
 template <class S>
-cudaError_t launch_init(const FieldArgs& F, S* f, const double* rr, const double* rb, cudaStream_t st);
+cudaError_t launch_init(const FieldArgs& F, S* f, const double* rr, const double* rb, cudaStream_t st,
+                        int* err = nullptr);
 template <class S>
 cudaError_t launch_conservation(const FieldArgs& F, const S* f, double* part, double* out, cudaStream_t st);
 template <class S>
 cudaError_t launch_fields(const FieldArgs& F, const S* f, const Scratch& W, bool velocity, cudaStream_t st);
+// rho^r, rho^b of every node into W.rho (the contact angle's input)
+template <class S>
+cudaError_t launch_rho(const FieldArgs& F, const S* f, const Scratch& W, cudaStream_t st);
 cudaError_t launch_angle(const FieldArgs& F, const Scratch& W, double zref, double level, double* part, double* out,
                          cudaStream_t st);
 // pressure tensor of Sec. 4.1 (after launch_fields with velocity): every node,
@@ -89,6 +94,13 @@ constexpr int kRadialBinsMax = 1024;
 constexpr double kRadialFix = 1073741824.0;  // fixed-point unit of the radial sums: 2^-30
 cudaError_t launch_pressure_radial(const FieldArgs& F, const void* f, int prec, const Scratch& W, const double* centre,
                                    double dr, int nbins, double zmin, unsigned long long* out, cudaStream_t st);
+// z-slab face messages (halo.cu): 38 entries of nx*ny values per face
+constexpr int kHaloEntries = 38;
+// face 0 = below (planes 0, 1), 1 = above (planes nz-2, nz-1); unpack 0 packs
+// the lattice's outgoing message into msg, 1 applies the neighbour's message
+cudaError_t launch_halo_copy(const Layout& L, void* f, size_t elem, void* msg, int face, int unpack, cudaStream_t st);
+// both messages of the face between slab A (below) and B (above), lattice to lattice
+cudaError_t launch_halo_exchange(const Layout& LA, void* fa, const Layout& LB, void* fb, size_t elem, cudaStream_t st);
 template <class S>
 cudaError_t launch_get_pop(const FieldArgs& F, const S* f, double* out, cudaStream_t st);
 template <class S>

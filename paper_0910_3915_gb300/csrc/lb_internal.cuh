@@ -193,14 +193,18 @@ struct StepArgs {
     int tiles_x, tiles_y;  // tile columns: 32-node rows in x; tiles_y even row splits of ny in y
     int zlo, zhi;  // fluid plane range [zlo, zhi)
     int nseg;      // z segments per tile column
+    int halo;      // planar walls: bit 0 = plane 0, bit 1 = plane nz-1 is a halo plane of a z slab, not a wall
+    uint32_t hkey; // added to a node's offset in the rounding dither's hash (a slab's offset in its lattice)
 };
 
 constexpr uint32_t kSelfSolid = 1u << 31;
 
 // Device status word bits (StepArgs::err): a bounded wait gave up; an index
-// fell outside its buffer (only a build with LBSC_DEBUG_BOUNDS checks indices).
+// fell outside its buffer (only a build with LBSC_DEBUG_BOUNDS checks indices);
+// an input density failed the re-initialisation's check.
 constexpr int kErrWait = 1;
 constexpr int kErrBounds = 2;
+constexpr int kErrInput = 4;  // lb_reset: a density was negative or not finite
 #ifdef LBSC_DEBUG_BOUNDS
 constexpr bool kCheckBounds = true;
 #else

@@ -15,8 +15,9 @@
 namespace lbsc {
 
 constexpr int kStaticMaxBlocks = 1024;                // rows of partial sums in the static array
-constexpr long long kStaticNodesPerBlock = 65536;     // nodes reduced by one block
-constexpr long long kStaticMaxNodes = kStaticMaxBlocks * kStaticNodesPerBlock;  // 67,108,864
+constexpr long long kStaticMaxNodesPerBlock = 65536;  // nodes one block reduces at most
+constexpr long long kStaticMinNodesPerBlock = 2048;   // and at least (small fields use few blocks)
+constexpr long long kStaticMaxNodes = kStaticMaxBlocks * kStaticMaxNodesPerBlock;  // 67,108,864
 constexpr int kStaticVals = 8;
 constexpr int kStaticThreads = 256;
 constexpr int kMaxDevices = 64;
@@ -24,15 +25,17 @@ constexpr int kMaxDevices = 64;
 // 1024 x 8 doubles = 64 KiB of partial sums
 static __device__ __align__(256) double g_static_partials[kStaticMaxBlocks * kStaticVals];
 
-// Block b sums nodes [b*kStaticNodesPerBlock, (b+1)*kStaticNodesPerBlock) of the
-// dense array n[a][k][node] and writes one row of partials:
-// {M_r, M_b, Px, Py, Pz, non-finite count, fluid nodes, 0}.
+// Block b sums nodes [b*per, (b+1)*per) of the dense array n[a][k][node] and
+// writes one row of partials: {M_r, M_b, Px, Py, Pz, non-finite count, fluid
+// nodes, 0}. per = max(ceil(N / 1024), 2048), so a mid-size field spreads
+// over up to 1024 blocks and the rows never exceed the static array.
 __global__ void __launch_bounds__(kStaticThreads)
-    static_cons_kernel(const double* __restrict__ n, const uint8_t* __restrict__ solid, long long N, double* part)
+    static_cons_kernel(const double* __restrict__ n, const uint8_t* __restrict__ solid, long long N, long long per,
+                       double* part)
 {
     double acc[kStaticVals] = {0, 0, 0, 0, 0, 0, 0, 0};
-    const long long lo = blockIdx.x * kStaticNodesPerBlock;
-    const long long hi = lo + kStaticNodesPerBlock < N ? lo + kStaticNodesPerBlock : N;
+    const long long lo = blockIdx.x * per;
+    const long long hi = lo + per < N ? lo + per : N;
     for (long long i = lo + threadIdx.x; i < hi; i += kStaticThreads) {
         if (solid && solid[i]) continue;
         acc[6] += 1.0;
@@ -133,8 +136,10 @@ extern "C" int lb_conservation_static(const double* populations, const uint8_t* 
         return rc;
     }
     cudaStream_t st = (cudaStream_t)cuda_stream;
-    const int blocks = (int)((N + kStaticNodesPerBlock - 1) / kStaticNodesPerBlock);
-    static_cons_kernel<<<blocks, kStaticThreads, 0, st>>>(populations, solid, N, part);
+    long long per = (N + kStaticMaxBlocks - 1) / kStaticMaxBlocks;
+    if (per < kStaticMinNodesPerBlock) per = kStaticMinNodesPerBlock;
+    const int blocks = (int)((N + per - 1) / per);  // <= kStaticMaxBlocks since per >= ceil(N / 1024)
+    static_cons_kernel<<<blocks, kStaticThreads, 0, st>>>(populations, solid, N, per, part);
     static_finish_kernel<<<1, 32, 0, st>>>(part, blocks, cons);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {

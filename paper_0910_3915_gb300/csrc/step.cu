@@ -82,7 +82,7 @@ __device__ __forceinline__ void step_item(const StepArgs<S>& A, int col, int za,
     auto issue = [&](int zp) {
         const int zw = kGeneral ? wrapi(zp, nz) : zp;
         const int zoff = zw * plane;
-        const bool wall_plane = !kGeneral && (zp == 0 || zp == nz - 1);
+        const bool wall_plane = !kGeneral && ((zp == 0 && !(A.halo & 1)) || (zp == nz - 1 && !(A.halo & 2)));
         if (!active) so_ = true;  // idle row: no loads, no psi
         // bounds-checked build: every slot of a node lies in the buffer iff its offset in the slot does
         else if (kCheckBounds && !in_bounds((long long)zoff + own, L.slot, A.err)) so_ = true;
@@ -153,6 +153,7 @@ __device__ __forceinline__ void step_item(const StepArgs<S>& A, int col, int za,
     Dest D;
     D.set_column(L, valid ? gx : 0, valid ? gy : 0);
     D.err = A.err;
+    D.hoff = A.hkey;
 
     for (int z = za; z < zb; ++z) {
         reduce(z + 1, rn, jn, vn, mn);
@@ -178,8 +179,8 @@ __device__ __forceinline__ void step_item(const StepArgs<S>& A, int col, int za,
                 D.zo[2] = (z + 1) * plane;
             }
             D.zo[1] = z * plane;
-            D.bot = !kGeneral && z - 1 == 0;
-            D.top = !kGeneral && z + 1 == nz - 1;
+            D.bot = !kGeneral && z - 1 == 0 && !(A.halo & 1);  // a halo plane takes pushes like fluid
+            D.top = !kGeneral && z + 1 == nz - 1 && !(A.halo & 2);
             collide_store<S, kGeneral, kTauOne>(rc, jc, vc, F, tau, itau, ref, dst, L, gx, gy, D, mc, clk);
         }
         // rotate: next plane becomes current

@@ -208,6 +208,7 @@ struct Dest {
     int zo[3];         // plane offsets of z-1, z, z+1 (offsets stay below 2^31: slot < 2^31)
     bool bot, top;     // planar walls: solid plane below / above
     uint32_t nb;       // general geometry: bit k = link k ends on a solid node
+    uint32_t hoff;     // added to the node's offset in the dither hash (0 unless the lattice is a z slab)
     int* err;          // status word (bounds-checked build only)
 
     // per-thread part that stays fixed while the thread marches in z
@@ -222,6 +223,7 @@ struct Dest {
 #pragma unroll
         for (int dy = 0; dy < 3; ++dy) ro[dy] = (yo[dy] + 1) * L.px + L.gx;
         nb = 0;
+        hoff = 0;
     }
     template <class S>
     __device__ __forceinline__ void store(S* __restrict__ p, const Layout&, int dx, int dy, int dz, float v) const
@@ -287,7 +289,7 @@ __device__ __forceinline__ void collide_store(const float (&rc)[2], const float 
     const int self = D.zo[1] + D.ro[1] + D.xo[1];
     float2 sum = sp2(0.f), sax = sp2(0.f), sdi = sp2(0.f);
     uint32_t hsh = 0;
-    if constexpr (Codec<S>::kDitherMoving) hsh = node_hash((uint32_t)self, clk);
+    if constexpr (Codec<S>::kDitherMoving) hsh = node_hash((uint32_t)self + D.hoff, clk);
     // opposite velocities in pairs: c_{k+1} = -c_k (k odd, the first nonzero
     // component of c_k positive), so c_{k+1}.u = -(c_k.u) exactly
 #pragma unroll
@@ -350,7 +352,7 @@ __device__ __forceinline__ void collide_store(const float (&rc)[2], const float 
     if constexpr (Codec<S>::kDeviation) {
         uint32_t hrest;
         if constexpr (Codec<S>::kDitherMoving) hrest = node_hash(hsh, 0x632BE5ABu);  // a second full mixing round
-        else hrest = node_hash((uint32_t)self, clk);
+        else hrest = node_hash((uint32_t)self + D.hoff, clk);
         // 12 e_0* = m36 - 2 sum_axis e_k* - sum_diag e_k*, the right side exact in FP32
         // the residual step makes the quotient round as x/12 itself would;
         // the rounded reciprocal alone scales every rest value by 1 + 3e-8

@@ -294,6 +294,7 @@ __global__ void __launch_bounds__(32 * TY, (kTmaCtas<TY, kTauOne>)) step_tma_ker
         Dest D;
         D.set_column(L, valid ? gx : 0, valid ? gy : 0);
         D.err = A.err;
+        D.hoff = A.hkey;
 
         for (int z = za; z < zb; ++z) {
             if (!consume(z - za + 2, rn, jn, vn, mn)) {

@@ -33,6 +33,12 @@ LB_WEIGHTS_UNIT, LB_WEIGHTS_W36 = 0, 1
 LB_STEP_AUTO, LB_STEP_LDG, LB_STEP_TMA = 0, 1, 2
 LB_OBS_COM, LB_OBS_COM_SOFT, LB_OBS_WETTED = 0, 1, 2
 LB_BUILD_BOUNDS_CHECKED = 1
+LB_HALO_BELOW, LB_HALO_ABOVE = 1, 2
+LB_DROP_OK, LB_DROP_BAD_PLANE, LB_DROP_NO_PHASE, LB_DROP_NO_APEX, LB_DROP_LOW_APEX, LB_DROP_NO_BASE = range(6)
+DROP_STATUS = {LB_DROP_OK: "ok", LB_DROP_BAD_PLANE: "reference plane outside the lattice",
+               LB_DROP_NO_PHASE: "no droplet phase (dissolved)", LB_DROP_NO_APEX: "no apex crossing",
+               LB_DROP_LOW_APEX: "apex below the reference plane",
+               LB_DROP_NO_BASE: "no base at the reference plane (detached)"}
 OBSERVABLES = {"com": LB_OBS_COM, "com_soft": LB_OBS_COM_SOFT, "wetted": LB_OBS_WETTED}
 STEP_VARIANTS = {"auto": LB_STEP_AUTO, "ldg": LB_STEP_LDG, "tma": LB_STEP_TMA}
 
@@ -52,7 +58,8 @@ class lb_params(ctypes.Structure):
 class lb_droplet(ctypes.Structure):
     _fields_ = [(n, ctypes.c_double) for n in
                 ("theta_deg", "theta_fit_deg", "h", "b", "r", "base_ref", "xc", "yc", "zc", "r_fit")] + \
-               [("ok", ctypes.c_int), ("n_points", ctypes.c_int)]
+               [("ok", ctypes.c_int), ("n_points", ctypes.c_int), ("phi_max", ctypes.c_double),
+                ("phi_min", ctypes.c_double), ("status", ctypes.c_int)]
 
 
 @dataclass
@@ -91,6 +98,13 @@ SIGNATURES = [
     ("lb_selftest_psi", _I, [ctypes.POINTER(ctypes.c_float), _I, ctypes.POINTER(ctypes.c_float)]),
     ("lb_moments", _I, [_VP, _DP, _DP, _DP, _DP]),
     ("lb_conservation", _I, [_VP, _DP]),
+    ("lb_reset", _I, [_VP, _DP, _DP]),
+    ("lb_init_slab", _I, [ctypes.POINTER(_VP), _I, _I, _I, _I, _DP, _DP, _VP, _I, _I, _DP]),
+    ("lb_halo_bytes", _I, [_VP, ctypes.POINTER(ctypes.c_size_t)]),
+    ("lb_halo_pack", _I, [_VP, _I, _VP]),
+    ("lb_halo_unpack", _I, [_VP, _I, _VP]),
+    ("lb_halo_exchange", _I, [_VP, _VP]),
+    ("lb_slabs_step", _I, [ctypes.POINTER(_VP), _I, _I]),
     ("lb_contact_angle", _I, [_VP, ctypes.c_double, ctypes.POINTER(lb_droplet)]),
     ("lb_contact_angle_at", _I, [_VP, ctypes.c_double, ctypes.c_double, ctypes.POINTER(lb_droplet)]),
     ("lb_state_bytes", _I, [_VP, ctypes.POINTER(ctypes.c_size_t)]),
@@ -206,7 +220,8 @@ class Lattice:
     (lb_init_external); otherwise the library allocates it (lb_init).
     """
 
-    def __init__(self, rho_r, rho_b, precision: str = "f32", stream=None, torch_memory: bool = False):
+    def __init__(self, rho_r, rho_b, precision: str = "f32", stream=None, torch_memory: bool = False,
+                 slab=None):
         lib = load()
         rr, rb = _f64(rho_r), _f64(rho_b)
         if rr.shape != rb.shape or rr.ndim != 3:
@@ -216,7 +231,13 @@ class Lattice:
         st = _current_stream() if stream is None else ctypes.c_void_p(stream)
         ctx = ctypes.c_void_p()
         self._buf = None
-        if torch_memory:
+        if slab is not None:
+            # a z slab of a decomposed lattice: slab = (halo flags, zbase, references or None)
+            halo, zbase, ref = slab
+            ref_a = None if ref is None else np.ascontiguousarray(ref, dtype=np.float64)
+            rc = lib.lb_init_slab(ctypes.byref(ctx), self.nx, self.ny, self.nz, PRECISIONS[precision], _dp(rr),
+                                  _dp(rb), st, int(halo), int(zbase), None if ref_a is None else _dp(ref_a))
+        elif torch_memory:
             import torch
             nbytes = ctypes.c_size_t()
             _check(lib.lb_required_bytes(self.nx, self.ny, self.nz, PRECISIONS[precision], ctypes.byref(nbytes)))
@@ -245,6 +266,15 @@ class Lattice:
         cp = p.c()
         _check(load().lb_set_params(self._ctx, ctypes.byref(cp)), self._ctx)
         self._params = p
+        return self
+
+    def reset(self, rho_r, rho_b) -> "Lattice":
+        """Start again from new initial densities (lb_reset): no allocation; the
+        step count returns to 0, geometry, parameters and schedule stay."""
+        rr, rb = _f64(rho_r), _f64(rho_b)
+        if rr.shape != self.shape or rb.shape != self.shape:
+            raise ValueError("rho_r and rho_b must have the lattice's shape (nz, ny, nx)")
+        _check(load().lb_reset(self._ctx, _dp(rr), _dp(rb)), self._ctx)
         return self
 
     def set_geometry(self, solid) -> "Lattice":

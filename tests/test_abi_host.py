@@ -69,7 +69,9 @@ def test_constants_match_header():
 def test_struct_layouts_match_header(lib):
     from paper_0910_3915_gb300 import lbsc
     assert ctypes.sizeof(lbsc.lb_params) == 7 * 8
-    assert ctypes.sizeof(lbsc.lb_droplet) == 10 * 8 + 2 * 4
+    # 10 doubles, ok and n_points, phi_max and phi_min, status, tail padding to 8 bytes
+    assert ctypes.sizeof(lbsc.lb_droplet) == 10 * 8 + 2 * 4 + 2 * 8 + 4 + 4
+    assert lbsc.lb_droplet.phi_max.offset == 88 and lbsc.lb_droplet.status.offset == 104
 
 
 def test_argument_errors_before_cuda(lib):

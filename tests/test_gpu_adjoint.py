@@ -111,6 +111,33 @@ def test_adjoint_against_gpu_finite_differences_full_config(lbsc):
     assert np.allclose(g, fd, rtol=2e-2, atol=2e-2 * np.abs(fd).max())
 
 
+@pytest.mark.slow
+def test_adjoint_full_config_against_fp64_oracle_central_differences(lbsc):
+    """The adjoint calibration configuration itself: 64^3, R = 16, g_br = 0.08,
+    wall parameters at 0, 2000 steps with checkpoints every 100. The gradient
+    of the droplet's centre-of-mass height with respect to both wall
+    pseudo-densities against central differences (h = 1e-4) of the FP64 oracle
+    over the same 2000 steps: within 1e-3 relative."""
+    nx = ny = nz = 64
+    steps, ckpt, obs = 2000, 100, "com"
+    rr, rb = W.droplet_fields(nx, ny, nz, 16.0, seed=0)
+    prm = dict(CONTACT, eta_wall_r=0.0, eta_wall_b=0.0)
+    lat = lbsc.Lattice(rr, rb).set_params(**prm)
+    J, g = lat.step_backward(steps, ckpt_every=ckpt, observable=obs)
+    lat.close()
+    h = 1e-4
+    fd = []
+    for comp in ("eta_wall_r", "eta_wall_b"):
+        jp = oracle_J(rr, rb, dict(prm, **{comp: prm[comp] + h}), steps, obs)
+        jm = oracle_J(rr, rb, dict(prm, **{comp: prm[comp] - h}), steps, obs)
+        fd.append((jp - jm) / (2 * h))
+    fd = np.array(fd)
+    j0 = oracle_J(rr, rb, prm, steps, obs)
+    assert math.isclose(J, j0, rel_tol=1e-4), (J, j0)
+    assert np.abs(fd).max() > 1e-3  # the centre of mass does move with the wall
+    assert np.allclose(g, fd, rtol=1e-3, atol=1e-3 * np.abs(fd).max()), (g, fd)
+
+
 def test_autograd_function_chain_rule(lbsc):
     torch = pytest.importorskip("torch")
     nx, ny, nz = 16, 16, 12
