@@ -52,7 +52,7 @@ __global__ void adj_forward_kernel(Layout L, KParams P, const S* __restrict__ f,
             if (!solid) {
                 #pragma unroll
                 for (int k = 0; k < Q; ++k) {
-                    float v = Codec<S>::load(f + (long long)(a * Q + k) * L.slot + off);
+                    float v = Codec<S>::load(f + L.at(a, k, off));
                     if constexpr (Codec<S>::kDeviation) v = zeta(k) * (P.ref[a] + v);
                     r += v;
                     jx += cx(k) * v;

@@ -88,7 +88,7 @@ static size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 static Layout make_layout(int nx, int ny, int nz, int prec)
 {
     Layout L;
-    const int line = (int)(128 / elem_size(prec));
+    const int line = (int)(128 / (2 * elem_size(prec)));  // nodes (of two values) in 128 bytes
     L.nx = nx;
     L.ny = ny;
     L.nz = nz;
@@ -110,7 +110,7 @@ static Plan make_plan(const Layout& L, int prec)
     p.f = align256((size_t)2 * Q * L.slot * elem_size(prec));
     p.mask = align256((size_t)L.plane * L.nz * sizeof(uint32_t));
     p.scratch = align256((size_t)10 * N * sizeof(float));
-    p.part = align256((size_t)kRedBlocks * kAngleVals * sizeof(double));
+    p.part = align256((size_t)kPartRows * kAngleVals * sizeof(double));
     p.red = align256(64 * sizeof(double));
     p.total = 2 * p.f + p.mask + p.scratch + p.part + p.red;
     return p;
@@ -249,9 +249,10 @@ static EncodeTiledFn encode_fn()
     return fn;
 }
 
-// 5-D maps over a population buffer: (x incl. padding, y incl. ghost rows, z, k, a);
-// main box = the 32-node tile plus 16 bytes of columns on each side, TY + 2 rows,
-// one plane, all 38 slots; strip box = 16 bytes of columns (the x-edge images)
+// 4-D maps over a population buffer: (x incl. padding, two values per node;
+// y incl. ghost rows; z; k); main box = the 32-node tile plus 16 bytes of
+// columns on each side, TY + 2 rows, one plane, all 19 slots; strip box = 16
+// bytes of columns (the x-edge images)
 static int tensor_map(lb_ctx* c, int buf, int ty)
 {
     const int ti = tile_index(ty);
@@ -260,18 +261,19 @@ static int tensor_map(lb_ctx* c, int buf, int ty)
     if (!enc) return fail(c, LB_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
     const size_t es = elem_size(c->prec);
     const Layout& L = c->L;
-    const cuuint64_t dims[5] = {(cuuint64_t)L.px, (cuuint64_t)(L.ny + 2), (cuuint64_t)L.nz, (cuuint64_t)Q, 2};
-    const cuuint64_t strides[4] = {(cuuint64_t)L.px * es, (cuuint64_t)L.plane * es, (cuuint64_t)L.slot * es,
-                                   (cuuint64_t)Q * L.slot * es};
+    const cuuint64_t dims[4] = {(cuuint64_t)(2 * L.px), (cuuint64_t)(L.ny + 2), (cuuint64_t)L.nz, (cuuint64_t)Q};
+    const cuuint64_t strides[3] = {(cuuint64_t)(2 * L.px) * es, (cuuint64_t)(2 * L.plane) * es,
+                                   (cuuint64_t)(2 * L.slot) * es};
     // main box: the tile plus 16 bytes of columns on each side; strip: 16 bytes of columns (x edges)
-    const cuuint32_t box[5] = {(cuuint32_t)(es == 4 ? 40 : 48), (cuuint32_t)(ty + 2), 1, (cuuint32_t)Q, 2};
-    const cuuint32_t sbox[5] = {(cuuint32_t)(16 / es), (cuuint32_t)(ty + 2), 1, (cuuint32_t)Q, 2};
-    const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+    const cuuint32_t gxv = (cuuint32_t)(16 / es);  // values in 16 bytes
+    const cuuint32_t box[4] = {(cuuint32_t)(2 * 32) + 2 * gxv, (cuuint32_t)(ty + 2), 1, (cuuint32_t)Q};
+    const cuuint32_t sbox[4] = {gxv, (cuuint32_t)(ty + 2), 1, (cuuint32_t)Q};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
     const CUtensorMapDataType dt = c->prec == LB_F32   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
                                    : c->prec == LB_F16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
                                                        : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
     for (int kind = 0; kind < 2; ++kind) {
-        const CUresult r = enc(&c->tmap[buf][ti][kind], dt, 5, c->f[buf], dims, strides, kind ? sbox : box, estr,
+        const CUresult r = enc(&c->tmap[buf][ti][kind], dt, 4, c->f[buf], dims, strides, kind ? sbox : box, estr,
                                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS) return fail(c, LB_ERR_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
@@ -456,7 +458,9 @@ static int init_common(lb_ctx** out, int nx, int ny, int nz, int precision, cons
     if (e != cudaSuccess) return bail(LB_ERR_CUDA, std::string("lb_init: cudaMallocHost: ") + cudaGetErrorString(e));
 
     if (planar_default(c) != LB_OK) return bail(LB_ERR_CUDA, c->err);
-    e = cudaMemsetAsync(c->dev_err, 0, sizeof(int), c->stream);
+    // reduction area: outputs [0, 32), conservation accumulators [32, 40) and ticket [40], status word, step counter
+    e = cudaMemsetAsync(c->red, 0, 64 * sizeof(double), c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->dev_err, 0, sizeof(int), c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->clock, 0, 2 * sizeof(uint32_t), c->stream);
     if (e == cudaSuccess) e = tma_prepare(c);
     if (e != cudaSuccess) return bail(LB_ERR_CUDA, std::string("lb_init: ") + cudaGetErrorString(e));
@@ -780,7 +784,8 @@ int lb_sync(lb_ctx* c)
 template <class S>
 static cudaError_t run_cons(lb_ctx* c)
 {
-    return launch_conservation<S>(field_args(c), (const S*)c->f[c->cur], c->part, c->red, c->stream);
+    return launch_conservation<S>(field_args(c), (const S*)c->f[c->cur], (unsigned long long*)(c->red + 32),
+                                  (unsigned int*)(c->red + 40), c->red, c->stream);
 }
 template <class S>
 static cudaError_t run_fields(lb_ctx* c, bool vel)
@@ -797,16 +802,16 @@ static cudaError_t dispatch_cons(lb_ctx* c)
     }
 }
 template <class S>
-static cudaError_t run_rho(lb_ctx* c)
+static cudaError_t run_phi(lb_ctx* c)
 {
-    return launch_rho<S>(field_args(c), (const S*)c->f[c->cur], c->W, c->stream);
+    return launch_phi<S>(field_args(c), (const S*)c->f[c->cur], c->W, c->stream);
 }
-static cudaError_t dispatch_rho(lb_ctx* c)
+static cudaError_t dispatch_phi(lb_ctx* c)
 {
     switch (c->prec) {
-    case LB_F32: return run_rho<float>(c);
-    case LB_F16: return run_rho<__half>(c);
-    default: return run_rho<__nv_bfloat16>(c);
+    case LB_F32: return run_phi<float>(c);
+    case LB_F16: return run_phi<__half>(c);
+    default: return run_phi<__nv_bfloat16>(c);
     }
 }
 static cudaError_t dispatch_fields(lb_ctx* c, bool vel)
@@ -893,7 +898,7 @@ int lb_contact_angle_at(lb_ctx* c, double offset, double level, lb_droplet* out)
         return fail(c, LB_ERR_ARG, "lb_contact_angle: bad argument");
     memset(out, 0, sizeof(*out));
     const double zw = 0.5, zref = zw + offset;
-    LB_CUDA(c, dispatch_rho(c));
+    LB_CUDA(c, dispatch_phi(c));
     LB_CUDA(c, launch_angle(field_args(c), c->W, zref, level, c->part, c->red, c->stream));
     LB_CUDA(c, cudaMemcpyAsync(c->h_red, c->red, kAngleVals * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     LB_CUDA(c, cudaStreamSynchronize(c->stream));
@@ -984,7 +989,7 @@ int lb_save(lb_ctx* c, void* host, size_t bytes)
     const size_t pb = payload_bytes(c);
     if (bytes < sizeof(StateHeader) + pb) return fail(c, LB_ERR_ARG, "lb_save: buffer too small");
     StateHeader h;
-    memcpy(h.magic, "LBSCST01", 8);
+    memcpy(h.magic, "LBSCST02", 8);
     h.nx = c->nx;
     h.ny = c->ny;
     h.nz = c->nz;
@@ -1004,7 +1009,7 @@ int lb_load(lb_ctx* c, const void* host, size_t bytes)
     if (bytes < sizeof(StateHeader)) return fail(c, LB_ERR_ARG, "lb_load: truncated state");
     StateHeader h;
     memcpy(&h, host, sizeof(h));
-    if (memcmp(h.magic, "LBSCST01", 8) != 0) return fail(c, LB_ERR_ARG, "lb_load: not an lbsc state");
+    if (memcmp(h.magic, "LBSCST02", 8) != 0) return fail(c, LB_ERR_ARG, "lb_load: not an lbsc state");
     if (h.nx != c->nx || h.ny != c->ny || h.nz != c->nz || h.prec != c->prec || h.payload != (long long)pb)
         return fail(c, LB_ERR_ARG, "lb_load: state does not match this context");
     if (bytes < sizeof(StateHeader) + pb) return fail(c, LB_ERR_ARG, "lb_load: truncated state");

@@ -1,8 +1,8 @@
 // Non-step kernels: initial equilibrium, FP64 conservation sums, moment
 // fields for readback, contact-angle reductions and population copies.
-// All reductions are deterministic: fixed grid, fixed per-thread ranges,
-// warp shuffles, then a single-block pass over the per-block partials in
-// block order.
+// All reductions are deterministic: the conservation sums are exact integer
+// (fixed-point) sums; the others use a fixed grid, fixed per-thread ranges,
+// warp shuffles and a final pass over the per-block partials in block order.
 #include "lb_fields.cuh"
 
 namespace lbsc {
@@ -41,23 +41,27 @@ __device__ __forceinline__ void block_reduce(double (&acc)[NV], uint32_t is_max,
     }
 }
 
-// Sum (or max) nblocks partial rows of NV values: thread t takes rows t,
-// t + kRedThreads, ... in order, then the fixed warp and block tree of
-// block_reduce. Launched as one block of kRedThreads threads.
+// Sum (or max) nrows partial rows of NV values: warp v reduces value v, lane
+// l taking rows l, l + 32, ... in order, then a fixed shuffle tree. Launched
+// as one block of 32 NV threads.
 template <int NV>
-__global__ void __launch_bounds__(kRedThreads) finish_kernel(const double* __restrict__ part, int nblocks,
-                                                             uint32_t is_max, double* __restrict__ out)
+__global__ void finish_rows_kernel(const double* __restrict__ part, int nrows, uint32_t is_max, double* __restrict__ out)
 {
-    double acc[NV];
+    const int v = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (v >= NV) return;
+    const bool mx = (is_max >> v) & 1u;
+    double a = mx ? -1e300 : 0.0;
+#pragma unroll 4
+    for (int r = lane; r < nrows; r += 32) {
+        const double p = part[(long long)r * NV + v];
+        a = mx ? fmax(a, p) : a + p;
+    }
 #pragma unroll
-    for (int i = 0; i < NV; ++i) acc[i] = ((is_max >> i) & 1u) ? -1e300 : 0.0;
-    for (int b = threadIdx.x; b < nblocks; b += kRedThreads)
-#pragma unroll
-        for (int i = 0; i < NV; ++i) {
-            const double p = part[(long long)b * NV + i];
-            acc[i] = ((is_max >> i) & 1u) ? fmax(acc[i], p) : acc[i] + p;
-        }
-    block_reduce<NV>(acc, is_max, out);
+    for (int o = 16; o > 0; o >>= 1) {
+        const double w = __shfl_down_sync(0xffffffffu, a, o);
+        a = mx ? fmax(a, w) : a + w;
+    }
+    if (lane == 0) out[v] = a;
 }
 
 // blocks for n items at `threads` per block, at most cap (grid-stride loops cover the rest)
@@ -73,6 +77,20 @@ __device__ __forceinline__ float decode(const S* p, int k, float ref)
     const float v = Codec<S>::load(p);
     if constexpr (Codec<S>::kDeviation) return zeta(k) * (ref + v);
     else return v;
+}
+
+// both components' n_k of one node from their paired storage
+template <class S>
+__device__ __forceinline__ void decode2(const S* p, int k, const float (&ref)[2], float& n0, float& n1)
+{
+    const float2 v = Codec<S>::load2(p);
+    if constexpr (Codec<S>::kDeviation) {
+        n0 = zeta(k) * (ref[0] + v.x);
+        n1 = zeta(k) * (ref[1] + v.y);
+    } else {
+        n0 = v.x;
+        n1 = v.y;
+    }
 }
 
 __device__ __forceinline__ bool node_solid(const FieldArgs& F, int x, int y, int z, long long off)
@@ -99,7 +117,7 @@ __global__ void init_kernel(FieldArgs F, S* __restrict__ f, const double* __rest
                 float v;
                 if constexpr (Codec<S>::kDeviation) v = rho - F.P.ref[a];
                 else v = zeta(k) * rho;
-                put<S>(f + (long long)(a * Q + k) * F.L.slot, F.L, x, y, (long long)z * F.L.plane, v);
+                put<S>(f + F.L.at(a, k, 0), F.L, x, y, (long long)z * F.L.plane, v);
             }
         }
     }
@@ -108,24 +126,31 @@ __global__ void init_kernel(FieldArgs F, S* __restrict__ f, const double* __rest
 // ---------------------------------------------------------------- conservation
 // cons = {M_r, M_b, Px, Py, Pz, non-finite count, fluid nodes, -}
 // A grid-stride walk over the nodes of the fluid planes, x fastest, so that a
-// warp's load of one population slot covers consecutive addresses; every
-// thread of the fixed grid takes nodes t, t + T, t + 2T, ... (T threads), with
-// its 38 loads of a node independent of each other. A node's mass and
-// momentum are summed in FP32 over its 19 values per component, then added
-// into per-thread FP64 sums (two masses and the total momentum: five FP64
-// additions a node); the counts stay integers. Fixed grid, fixed per-thread
-// order, fixed block tree and final pass: the sums do not depend on scheduling.
+// warp's load of one population slot covers consecutive addresses, with a
+// node's 38 loads independent of each other. A node's mass and momentum are
+// summed in FP32 over its 19 values per component, and each thread adds its
+// nodes in FP32. The threads' sums then go into 64-bit integers in units of
+// 2^-28 (kConsFix) and are added as integers: across warps, blocks and the
+// whole grid, by shuffles and atomics. Integer addition is exact and
+// associative, so the totals do not depend on the grid or on the order the
+// blocks finish, and no FP64 arithmetic (slow on this GPU) runs per node. The
+// last block to finish converts the totals to FP64 into out[0..7] and clears
+// the accumulators (acc[0..7], ticket) for the next call.
+__device__ __forceinline__ long long to_fix(float v) { return __float2ll_rn(v * kConsFix); }
+
 template <class S>
-__global__ void __launch_bounds__(kRedThreads) cons_kernel(FieldArgs F, const S* __restrict__ f, double* __restrict__ part)
+__global__ void __launch_bounds__(kRedThreads) cons_kernel(FieldArgs F, const S* __restrict__ f,
+                                                           unsigned long long* __restrict__ acc,
+                                                           unsigned int* __restrict__ ticket, double* __restrict__ out)
 {
-    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    float m[2] = {0.f, 0.f}, j[3] = {0.f, 0.f, 0.f};
     int bad = 0, fluid = 0;
     const int nx = F.L.nx, ny = F.L.ny;
     const int zlo = F.general ? 0 : 1, zhi = F.general ? F.L.nz : F.L.nz - 1;
     const unsigned nxy = (unsigned)nx * (unsigned)ny;
     const unsigned n = nxy * (unsigned)(zhi - zlo);  // below 2^31 (the layout's limit)
     const unsigned T = gridDim.x * blockDim.x;
-    const long long slot = F.L.slot;
+    const float ref[2] = {F.P.ref[0], F.P.ref[1]};
     for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += T) {
         const unsigned zr = i / nxy, rem = i - zr * nxy;
         const int y = (int)(rem / (unsigned)nx), x = (int)(rem - (unsigned)y * nx), z = zlo + (int)zr;
@@ -134,33 +159,60 @@ __global__ void __launch_bounds__(kRedThreads) cons_kernel(FieldArgs F, const S*
         ++fluid;
         float v[2][Q];
 #pragma unroll
-        for (int a = 0; a < 2; ++a)
-#pragma unroll
-            for (int k = 0; k < Q; ++k) v[a][k] = decode<S>(f + (long long)(a * Q + k) * slot + off, k, F.P.ref[a]);
-        float rho[2], j[3] = {0.f, 0.f, 0.f};
+        for (int k = 0; k < Q; ++k) decode2<S>(f + F.L.at(0, k, off), k, ref, v[0][k], v[1][k]);
+        float rho[2], jn[3] = {0.f, 0.f, 0.f};
 #pragma unroll
         for (int a = 0; a < 2; ++a) {
-            float m = 0.f;
+            float s = 0.f;
 #pragma unroll
             for (int k = 0; k < Q; ++k) {
                 const float nk = v[a][k];
                 bad += isfinite(nk) ? 0 : 1;
-                m += nk;
-                if (cx(k)) j[0] += cx(k) * nk;
-                if (cy(k)) j[1] += cy(k) * nk;
-                if (cz(k)) j[2] += cz(k) * nk;
+                s += nk;
+                if (cx(k)) jn[0] += cx(k) * nk;
+                if (cy(k)) jn[1] += cy(k) * nk;
+                if (cz(k)) jn[2] += cz(k) * nk;
             }
-            rho[a] = m;
+            rho[a] = s;
         }
-        acc[0] += rho[0];
-        acc[1] += rho[1];
-        acc[2] += j[0];
-        acc[3] += j[1];
-        acc[4] += j[2];
+        m[0] += rho[0];
+        m[1] += rho[1];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) j[d] += jn[d];
     }
-    acc[5] = bad;
-    acc[6] = fluid;
-    block_reduce<8>(acc, 0u, part);
+    // a non-finite value would make the fixed-point conversion meaningless: it is counted instead
+    const bool fin = bad == 0 && isfinite(m[0]) && isfinite(m[1]) && isfinite(j[0]) && isfinite(j[1]) && isfinite(j[2]);
+    long long q[7] = {fin ? to_fix(m[0]) : 0, fin ? to_fix(m[1]) : 0, fin ? to_fix(j[0]) : 0, fin ? to_fix(j[1]) : 0,
+                      fin ? to_fix(j[2]) : 0, (long long)bad + (fin ? 0 : 1) * (bad == 0), (long long)fluid};
+#pragma unroll
+    for (int v = 0; v < 7; ++v)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) q[v] += __shfl_down_sync(0xffffffffu, q[v], o);
+    __shared__ long long sh[kRedThreads / 32][7];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0)
+#pragma unroll
+        for (int v = 0; v < 7; ++v) sh[warp][v] = q[v];
+    __syncthreads();
+    __shared__ bool last;
+    if (threadIdx.x < 7) {
+        long long t = 0;
+        for (int w = 0; w < kRedThreads / 32; ++w) t += sh[w][threadIdx.x];
+        atomicAdd(&acc[threadIdx.x], (unsigned long long)t);  // two's complement: signed sums wrap correctly
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (last && threadIdx.x < 8) {
+        __threadfence();
+        const int v = threadIdx.x;
+        const long long t = v < 7 ? (long long)atomicExch(&acc[v], 0ull) : 0;
+        out[v] = v < 5 ? (double)t / kConsFix : (double)t;
+        if (v == 0) *ticket = 0u;
+    }
 }
 
 // ---------------------------------------------------------------- moment fields
@@ -177,7 +229,7 @@ __global__ void fields_kernel(FieldArgs F, const S* __restrict__ f, Scratch W)
         if (!solid) {
             for (int a = 0; a < 2; ++a)
                 for (int k = 0; k < Q; ++k) {
-                    const float n = decode<S>(f + (long long)(a * Q + k) * F.L.slot + off, k, F.P.ref[a]);
+                    const float n = decode<S>(f + F.L.at(a, k, off), k, F.P.ref[a]);
                     rho[a] += n;
                     j[0] += cx(k) * n;
                     j[1] += cy(k) * n;
@@ -223,16 +275,17 @@ __global__ void velocity_kernel(FieldArgs F, Scratch W)
     }
 }
 
-// rho^r and rho^b of every node into the scratch fields (0 on solid nodes):
-// the contact angle needs phi = rho_r - rho_b only
+// phi = rho_r - rho_b of every node into W.rho[0] (0 on solid nodes), the
+// contact angle's only input: FP32 sums of each component's 19 values, then
+// their difference
 template <class S>
-__global__ void rho_kernel(FieldArgs F, const S* __restrict__ f, Scratch W)
+__global__ void phi_kernel(FieldArgs F, const S* __restrict__ f, Scratch W)
 {
     const int nx = F.L.nx, ny = F.L.ny;
     const unsigned nxy = (unsigned)nx * (unsigned)ny;
     const unsigned N = nxy * (unsigned)F.L.nz;
     const unsigned T = gridDim.x * blockDim.x;
-    const long long slot = F.L.slot;
+    const float ref[2] = {F.P.ref[0], F.P.ref[1]};
     for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += T) {
         const unsigned z = i / nxy, rem = i - z * nxy;
         const int y = (int)(rem / (unsigned)nx), x = (int)(rem - (unsigned)y * nx);
@@ -241,116 +294,140 @@ __global__ void rho_kernel(FieldArgs F, const S* __restrict__ f, Scratch W)
         if (!node_solid(F, x, y, (int)z, off)) {
             float v[2][Q];
 #pragma unroll
-            for (int a = 0; a < 2; ++a)
-#pragma unroll
-                for (int k = 0; k < Q; ++k) v[a][k] = decode<S>(f + (long long)(a * Q + k) * slot + off, k, F.P.ref[a]);
+            for (int k = 0; k < Q; ++k) decode2<S>(f + F.L.at(0, k, off), k, ref, v[0][k], v[1][k]);
 #pragma unroll
             for (int a = 0; a < 2; ++a)
 #pragma unroll
                 for (int k = 0; k < Q; ++k) rho[a] += v[a][k];
         }
-        W.rho[0][i] = rho[0];
-        W.rho[1][i] = rho[1];
+        W.rho[0][i] = rho[0] - rho[1];
     }
 }
 
 // ---------------------------------------------------------------- contact angle
-// phi - level at a node, in FP64 from the FP32 densities (as the host finish uses it)
-__device__ __forceinline__ double phi_at(float r, float b, double level) { return (double)r - (double)b - level; }
+// phi - level in FP64 at a node whose phi is the FP32 value p
+__device__ __forceinline__ double phi_at(float p, double level) { return (double)p - level; }
 
-// phi - level > 0, decided in FP32 where the margin is far above FP32's
-// rounding, else in FP64 exactly as phi_at: (double)r - (double)b - level > 0
-// holds iff the exact r - b exceeds level, and the FP32 difference is within
-// about 2^-23 (|r - b| + |level|) of it, far inside the 1e-5 margin. Bulk nodes
-// therefore need no FP64 arithmetic (slow on this GPU); the decisions are the
-// ones the FP64 expression takes.
-__device__ __forceinline__ bool phi_pos(float r, float b, float lf, double level)
+// p > level, i.e. phi_at(p, level) > 0, taken in FP32 where that is exact: when
+// level is an FP32 number, or when p is far from it (the margin exceeds the
+// rounding of level to FP32 many times over); else in FP64.
+__device__ __forceinline__ bool above(float p, float lf, bool lexact, double level)
 {
-    const float d = r - b;
-    const float m = d - lf;
-    if (fabsf(m) > 1e-5f * (fabsf(d) + fabsf(lf)) + 1e-30f) return m > 0.f;
-    return phi_at(r, b, level) > 0.0;
+    if (lexact || fabsf(p - lf) > 1e-6f * (fabsf(p) + fabsf(lf)) + 1e-30f) return p > lf;
+    return (double)p > level;
 }
 
-// One thread per node (grid-stride, x fastest), reading rho^r, rho^b of the
-// node and of its +x, +y, +z neighbours:
-//  acc[0]  (max) top phi = level crossing: z + p0/(p0 - p1) where phi > level
-//          below and <= level above (both nodes fluid);
-//  acc[1]  positive length along x of the reference-plane interpolant of
-//          phi (the node at z0 adds its segment to x + 1, periodic);
-//  acc[2..16] sphere-fit sums over crossings along +x, +y, +z at or above
-//          the reference plane: count, the 10 upper entries of M = sum row row^T
-//          and the 4 of v = sum row |p|^2, row = (2p, 1);
-//  acc[17] (max) max of rho_r - rho_b over fluid nodes, acc[18] (max) of
-//          rho_b - rho_r (the phase contrast, a validity check).
+// One thread per node (grid-stride, x fastest), reading phi at the node and at
+// its +x, +y, +z neighbours (the latter from L1/L2):
+//  [0]  (max) top phi = level crossing: z + p0/(p0 - p1) where phi > level
+//       below and <= level above (both nodes fluid);
+//  [1]  positive length along x of the reference-plane interpolant of phi
+//       (the node at z0 adds its segment to x + 1, periodic);
+//  [2..16] sphere-fit sums over crossings along +x, +y, +z at or above the
+//       reference plane: count, the 10 upper entries of M = sum row row^T and
+//       the 4 of v = sum row |p|^2, row = (2p, 1);
+//  [17] (max) max of phi over fluid nodes, [18] (max) of -phi (the contrast).
+// FP64 arithmetic (slow on this GPU) runs only at crossings and on the
+// reference plane; a thread's FP64 sums wait in shared memory, and a warp
+// reduces a value only if one of its lanes holds a contribution to it.
 __global__ void __launch_bounds__(kRedThreads) angle_kernel(FieldArgs F, Scratch W, double zref, double level,
                                                             double* __restrict__ part)
 {
     const int nx = F.L.nx, ny = F.L.ny, nz = F.L.nz;
-    double acc[kAngleVals];
-#pragma unroll
-    for (int i = 0; i < kAngleVals; ++i) acc[i] = 0.0;
-    acc[0] = -1e300;
-    float dmax = -3.0e38f, dmin = 3.0e38f;
+    __shared__ double sacc[kAngleVals][kRedThreads];
+    const int tid = threadIdx.x;
+#define ACC(i) sacc[i][tid]
+    for (int i = 0; i < 17; ++i) ACC(i) = 0.0;
+    ACC(0) = -1e300;
+    float pmax = -3.0e38f, pmin = 3.0e38f;
     const int z0 = (int)floor(zref);
     const double fz = zref - z0;
     const float lf = (float)level;
-    const float* __restrict__ R = W.rho[0];
-    const float* __restrict__ B = W.rho[1];
+    const bool lexact = (double)lf == level;
+    const float* __restrict__ P = W.rho[0];
     const unsigned nxy = (unsigned)nx * (unsigned)ny;
     const unsigned N = nxy * (unsigned)nz;
     const unsigned T = gridDim.x * blockDim.x;
-    auto solid = [&](int x, int y, int z) -> bool { return node_solid(F, x, y, z, F.L.off(x, y, z)); };
     for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += T) {
         const int z = (int)(i / nxy);
         const unsigned rem = i - (unsigned)z * nxy;
         const int y = (int)(rem / (unsigned)nx), x = (int)(rem - (unsigned)y * nx);
-        const float r0 = R[i], b0 = B[i];
+        // the node and its +x, +y, +z neighbours (the node itself past an edge), loaded together
+        const float p0 = P[i];
+        const float pn[3] = {P[x + 1 < nx ? i + 1 : i], P[y + 1 < ny ? i + nx : i], P[z + 1 < nz ? i + nxy : i]};
         if (z == z0 && z0 + 1 < nz) {  // reference plane: every column, solid or not
             const int x1 = x + 1 < nx ? x + 1 : 0;
             const unsigned i1 = i - x + x1;
-            const double a0 = (1 - fz) * phi_at(r0, b0, level) + fz * phi_at(R[i + nxy], B[i + nxy], level);
-            const double a1 = (1 - fz) * phi_at(R[i1], B[i1], level) + fz * phi_at(R[i1 + nxy], B[i1 + nxy], level);
+            const double a0 = (1 - fz) * phi_at(p0, level) + fz * phi_at(pn[2], level);
+            const double a1 = (1 - fz) * phi_at(P[i1], level) + fz * phi_at(P[i1 + nxy], level);
             double len;
             if (a0 > 0 && a1 > 0) len = 1.0;
             else if (a0 <= 0 && a1 <= 0) len = 0.0;
             else if (a0 > 0) len = a0 / (a0 - a1);
             else len = a1 / (a1 - a0);
-            acc[1] += len;
+            ACC(1) += len;
         }
-        if (solid(x, y, z)) continue;
-        const float d0 = r0 - b0;
-        dmax = fmaxf(dmax, d0);
-        dmin = fminf(dmin, d0);
-        const bool s0 = phi_pos(r0, b0, lf, level);
+        if (!F.general ? (z == 0 || z == nz - 1) : (F.nbmask[F.L.off(x, y, z)] & kSelfSolid) != 0) continue;
+        pmax = fmaxf(pmax, p0);
+        pmin = fminf(pmin, p0);
+        const bool s0 = above(p0, lf, lexact, level);
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
             const int x1 = x + (d == 0), y1 = y + (d == 1), z1 = z + (d == 2);
-            if (x1 >= nx || y1 >= ny || z1 >= nz || solid(x1, y1, z1)) continue;
-            const unsigned j = d == 0 ? i + 1 : (d == 1 ? i + nx : i + nxy);
-            const float r1 = R[j], b1 = B[j];
-            const bool s1 = phi_pos(r1, b1, lf, level);
-            if (s0 == s1) continue;
-            const double p0 = phi_at(r0, b0, level), p1 = phi_at(r1, b1, level);
-            const double t = p0 / (p0 - p1);
-            if (d == 2 && s0) acc[0] = fmax(acc[0], z + t);  // phi > level below, <= level above
+            if (x1 >= nx || y1 >= ny || z1 >= nz) continue;
+            if (F.general ? (F.nbmask[F.L.off(x1, y1, z1)] & kSelfSolid) != 0 : z1 == nz - 1) continue;
+            const float p1 = pn[d];
+            if (s0 == above(p1, lf, lexact, level)) continue;
+            const double q0 = phi_at(p0, level), q1 = phi_at(p1, level);
+            const double t = q0 / (q0 - q1);
+            if (d == 2 && s0) ACC(0) = fmax(ACC(0), z + t);  // phi > level below, <= level above
             const double pxv = x + t * (d == 0), pyv = y + t * (d == 1), pzv = z + t * (d == 2);
             if (pzv < zref) continue;
             const double row[4] = {2 * pxv, 2 * pyv, 2 * pzv, 1.0};
             const double rhs = pxv * pxv + pyv * pyv + pzv * pzv;
-            acc[2] += 1.0;
+            ACC(2) += 1.0;
             int m = 3;
 #pragma unroll
             for (int r = 0; r < 4; ++r)
 #pragma unroll
-                for (int q = r; q < 4; ++q) acc[m++] += row[r] * row[q];
+                for (int q = r; q < 4; ++q) ACC(m++) += row[r] * row[q];
 #pragma unroll
-            for (int r = 0; r < 4; ++r) acc[13 + r] += row[r] * rhs;
+            for (int r = 0; r < 4; ++r) ACC(13 + r) += row[r] * rhs;
         }
     }
-    acc[17] = dmax > -3.0e38f ? (double)dmax : -1e300;
-    acc[18] = dmin < 3.0e38f ? -(double)dmin : -1e300;
-    block_reduce<kAngleVals>(acc, kAngleMaxMask, part);
+    // block reduction: FP32 maxima by shuffles; FP64 values only in warps that hold some
+    __shared__ double sh[kRedThreads / 32][kAngleVals];
+    const int lane = tid & 31, warp = tid >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        pmax = fmaxf(pmax, __shfl_down_sync(0xffffffffu, pmax, o));
+        pmin = fminf(pmin, __shfl_down_sync(0xffffffffu, pmin, o));
+    }
+    if (lane == 0) {
+        sh[warp][17] = pmax > -3.0e38f ? (double)pmax : -1e300;
+        sh[warp][18] = pmin < 3.0e38f ? -(double)pmin : -1e300;
+    }
+    for (int v = 0; v < 17; ++v) {
+        const bool is_max = v == 0;
+        double val = ACC(v);
+        const bool held = is_max ? val > -1e299 : val != 0.0;
+        if (__any_sync(0xffffffffu, held)) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const double w = __shfl_down_sync(0xffffffffu, val, o);
+                val = is_max ? fmax(val, w) : val + w;
+            }
+        }
+        if (lane == 0) sh[warp][v] = val;
+    }
+#undef ACC
+    __syncthreads();
+    if (tid < kAngleVals) {
+        const bool is_max = (kAngleMaxMask >> tid) & 1u;
+        double v = sh[0][tid];
+        for (int w = 1; w < kRedThreads / 32; ++w) v = is_max ? fmax(v, sh[w][tid]) : v + sh[w][tid];
+        part[(long long)blockIdx.x * kAngleVals + tid] = v;
+    }
 }
 
 // ---------------------------------------------------------------- pressure tensor
@@ -374,7 +451,7 @@ __device__ bool node_pressure(const FieldArgs& F, const S* __restrict__ f, const
     const double u[3] = {W.u[0][i], W.u[1][i], W.u[2][i]};
     for (int a = 0; a < 2; ++a)
         for (int k = 0; k < Q; ++k) {
-            const double n = decode<S>(f + (long long)(a * Q + k) * F.L.slot + off, k, F.P.ref[a]);
+            const double n = decode<S>(f + F.L.at(a, k, off), k, F.P.ref[a]);
             const double d[3] = {cx(k) - u[0], cy(k) - u[1], cz(k) - u[2]};
             P[0] += d[0] * d[0] * n;
             P[1] += d[1] * d[1] * n;
@@ -498,8 +575,8 @@ __global__ void ghost_rows_kernel(Layout L, S* __restrict__ f, int z0, int nzp)
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const int x = i % L.nx, t = i / L.nx;
         const int z = z0 + t % nzp, ak = t / nzp;
-        S* p = f + (long long)ak * L.slot + (long long)z * L.plane + L.gx + x;  // row y = -1
-        const long long row = L.px;
+        S* p = f + L.at(ak / Q, ak % Q, (long long)z * L.plane + L.gx + x);  // row y = -1
+        const long long row = 2 * (long long)L.px;                         // one row, in elements
         p[0] = p[(long long)L.ny * row];          // y = -1  <- y = ny-1
         p[(long long)(L.ny + 1) * row] = p[row];  // y = ny  <- y = 0
     }
@@ -526,7 +603,7 @@ __global__ void get_pop_kernel(FieldArgs F, const S* __restrict__ f, double* __r
         const int a = ak / Q, k = ak % Q;
         const int x = (int)(n % F.L.nx), y = (int)((n / F.L.nx) % F.L.ny), z = (int)(n / ((long long)F.L.nx * F.L.ny));
         const long long off = F.L.off(x, y, z);
-        out[i] = decode<S>(f + (long long)ak * F.L.slot + off, k, F.P.ref[a]);
+        out[i] = decode<S>(f + F.L.at(a, k, off), k, F.P.ref[a]);
     }
 }
 
@@ -542,7 +619,7 @@ __global__ void set_pop_kernel(FieldArgs F, S* __restrict__ f, const double* __r
         const long long off = F.L.off(x, y, z);
         float v = (float)in[i];
         if constexpr (Codec<S>::kDeviation) v = (float)(in[i] / (double)zeta(k) - (double)F.P.ref[a]);
-        put<S>(f + (long long)ak * F.L.slot, F.L, x, y, (long long)z * F.L.plane, v);
+        put<S>(f + F.L.at(a, k, 0), F.L, x, y, (long long)z * F.L.plane, v);
     }
 }
 
@@ -569,10 +646,10 @@ cudaError_t launch_init(const FieldArgs& F, S* f, const double* rr, const double
 }
 
 template <class S>
-cudaError_t launch_conservation(const FieldArgs& F, const S* f, double* part, double* out, cudaStream_t st)
+cudaError_t launch_conservation(const FieldArgs& F, const S* f, unsigned long long* acc, unsigned int* ticket,
+                                double* out, cudaStream_t st)
 {
-    cons_kernel<S><<<kRedBlocks, kRedThreads, 0, st>>>(F, f, part);
-    finish_kernel<8><<<1, kRedThreads, 0, st>>>(part, kRedBlocks, 0u, out);
+    cons_kernel<S><<<kConsBlocks, kRedThreads, 0, st>>>(F, f, acc, ticket, out);
     return cudaGetLastError();
 }
 
@@ -586,18 +663,18 @@ cudaError_t launch_fields(const FieldArgs& F, const S* f, const Scratch& W, bool
 }
 
 template <class S>
-cudaError_t launch_rho(const FieldArgs& F, const S* f, const Scratch& W, cudaStream_t st)
+cudaError_t launch_phi(const FieldArgs& F, const S* f, const Scratch& W, cudaStream_t st)
 {
     const long long N = (long long)F.L.nx * F.L.ny * F.L.nz;
-    rho_kernel<S><<<grid_for(N, 256, 65536), 256, 0, st>>>(F, f, W);
+    phi_kernel<S><<<grid_for(N, 256, 65536), 256, 0, st>>>(F, f, W);
     return cudaGetLastError();
 }
 
 cudaError_t launch_angle(const FieldArgs& F, const Scratch& W, double zref, double level, double* part, double* out,
                          cudaStream_t st)
 {
-    angle_kernel<<<kRedBlocks, kRedThreads, 0, st>>>(F, W, zref, level, part);
-    finish_kernel<kAngleVals><<<1, kRedThreads, 0, st>>>(part, kRedBlocks, kAngleMaxMask, out);
+    angle_kernel<<<kAngleBlocks, kRedThreads, 0, st>>>(F, W, zref, level, part);
+    finish_rows_kernel<kAngleVals><<<1, 32 * kAngleVals, 0, st>>>(part, kAngleBlocks, kAngleMaxMask, out);
     return cudaGetLastError();
 }
 
@@ -645,9 +722,10 @@ cudaError_t launch_pressure_radial(const FieldArgs& F, const void* f, int prec, 
 
 #define LBSC_INST(S)                                                                                  \
     template cudaError_t launch_init<S>(const FieldArgs&, S*, const double*, const double*, cudaStream_t, int*); \
-    template cudaError_t launch_conservation<S>(const FieldArgs&, const S*, double*, double*, cudaStream_t); \
+    template cudaError_t launch_conservation<S>(const FieldArgs&, const S*, unsigned long long*, unsigned int*, \
+                                                double*, cudaStream_t);                                        \
     template cudaError_t launch_fields<S>(const FieldArgs&, const S*, const Scratch&, bool, cudaStream_t); \
-    template cudaError_t launch_rho<S>(const FieldArgs&, const S*, const Scratch&, cudaStream_t);      \
+    template cudaError_t launch_phi<S>(const FieldArgs&, const S*, const Scratch&, cudaStream_t);      \
     template cudaError_t launch_get_pop<S>(const FieldArgs&, const S*, double*, cudaStream_t);       \
     template cudaError_t launch_set_pop<S>(const FieldArgs&, S*, const double*, cudaStream_t);   \
     template cudaError_t launch_ghosts<S>(const Layout&, S*, int, int, cudaStream_t);                 \

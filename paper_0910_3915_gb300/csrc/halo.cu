@@ -35,22 +35,26 @@ __device__ __forceinline__ int plane_k(int i, int dir)
     if (i < 9) return i < 5 ? i : i + 2;  // 0..4 (rest, +-x, +-y), 7..10 (the xy diagonals)
     return cross_k(i - 9, dir);
 }
-// lattice slot (a*19 + k) and plane of message entry j for a face whose
+// component a, velocity k and plane z of message entry j for a face whose
 // crossing entries live on plane zc with direction dc and whose plane entries
 // live on plane zp with direction dp
-__device__ __forceinline__ void entry_of(int j, int zc, int dc, int zp, int dp, int& slot, int& z)
+__device__ __forceinline__ void entry_of(int j, int zc, int dc, int zp, int dp, int& a, int& k, int& z)
 {
     if (j < 10) {
-        slot = (j / 5) * Q + cross_k(j % 5, dc);
+        a = j / 5;
+        k = cross_k(j % 5, dc);
         z = zc;
     } else {
         const int t = j - 10;
-        slot = (t / 14) * Q + plane_k(t % 14, dp);
+        a = t / 14;
+        k = plane_k(t % 14, dp);
         z = zp;
     }
 }
 
-// pack (lattice -> message) or unpack (message -> lattice), T the storage's raw type
+// pack (lattice -> message) or unpack (message -> lattice), T the storage's raw
+// type (the lattice keeps a node's two components side by side, the message
+// keeps each component's entries apart)
 template <class T>
 __global__ void halo_copy_kernel(Layout L, T* __restrict__ f, T* __restrict__ msg, int zc, int dc, int zp, int dp,
                                  int unpack)
@@ -60,9 +64,9 @@ __global__ void halo_copy_kernel(Layout L, T* __restrict__ f, T* __restrict__ ms
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const int j = i / nxy, r = i - j * nxy;
         const int y = r / L.nx, x = r - y * L.nx;
-        int slot, z;
-        entry_of(j, zc, dc, zp, dp, slot, z);
-        T* p = f + (long long)slot * L.slot + L.off(x, y, z);
+        int a, k, z;
+        entry_of(j, zc, dc, zp, dp, a, k, z);
+        T* p = f + L.at(a, k, L.off(x, y, z));
         if (unpack) *p = msg[i];
         else msg[i] = *p;
     }
@@ -81,15 +85,15 @@ __global__ void halo_exchange_kernel(Layout LA, T* __restrict__ fa, Layout LB, T
         const int e = up ? i : i - n;
         const int j = e / nxy, r = e - j * nxy;
         const int y = r / LA.nx, x = r - y * LA.nx;
-        int s_src, z_src, s_dst, z_dst;
+        int a, k, z_src, z_dst;
         if (up) {  // A packs its top face, B unpacks at its bottom face
-            entry_of(j, za - 1, +1, za - 2, +1, s_src, z_src);
-            entry_of(j, 1, +1, 0, +1, s_dst, z_dst);
-            fb[(long long)s_dst * LB.slot + LB.off(x, y, z_dst)] = fa[(long long)s_src * LA.slot + LA.off(x, y, z_src)];
+            entry_of(j, za - 1, +1, za - 2, +1, a, k, z_src);
+            entry_of(j, 1, +1, 0, +1, a, k, z_dst);
+            fb[LB.at(a, k, LB.off(x, y, z_dst))] = fa[LA.at(a, k, LA.off(x, y, z_src))];
         } else {  // B packs its bottom face, A unpacks at its top face
-            entry_of(j, 0, -1, 1, -1, s_src, z_src);
-            entry_of(j, za - 2, -1, za - 1, -1, s_dst, z_dst);
-            fa[(long long)s_dst * LA.slot + LA.off(x, y, z_dst)] = fb[(long long)s_src * LB.slot + LB.off(x, y, z_src)];
+            entry_of(j, 0, -1, 1, -1, a, k, z_src);
+            entry_of(j, za - 2, -1, za - 1, -1, a, k, z_dst);
+            fa[LA.at(a, k, LA.off(x, y, z_dst))] = fb[LB.at(a, k, LB.off(x, y, z_src))];
         }
     }
 }

@@ -9,7 +9,10 @@ namespace lbsc {
 
 constexpr int kRedThreads = 256;  // threads per reduction block
 constexpr int kRedBlocks = 512;   // fixed grid of the reductions: fixed summation order
+constexpr int kConsBlocks = 2048;   // grid of the conservation sums (enough loads in flight for HBM)
+constexpr int kAngleBlocks = 1216;  // fixed grid of the contact-angle reduction
 constexpr int kAngleVals = 19;    // contact-angle partial sums per block
+constexpr int kPartRows = kConsBlocks > kAngleBlocks ? kConsBlocks : kAngleBlocks;  // rows of the partials area
 constexpr uint32_t kAngleMaxMask = (1u << 0) | (1u << 17) | (1u << 18);  // max-reduced entries of the 19
 
 // Geometry and parameters for the non-step kernels.
@@ -75,13 +78,17 @@ cudaError_t launch_ghosts(const Layout& L, S* f, int z0, int z1, cudaStream_t st
 template <class S>
 cudaError_t launch_init(const FieldArgs& F, S* f, const double* rr, const double* rb, cudaStream_t st,
                         int* err = nullptr);
+// FP64 conservation sums into out[0..7] through 64-bit fixed-point accumulators
+// acc[0..6] and a block ticket, both zero between calls (the kernel clears them)
+constexpr float kConsFix = 268435456.0f;  // 2^28: the accumulators' unit is 2^-28
 template <class S>
-cudaError_t launch_conservation(const FieldArgs& F, const S* f, double* part, double* out, cudaStream_t st);
+cudaError_t launch_conservation(const FieldArgs& F, const S* f, unsigned long long* acc, unsigned int* ticket,
+                                double* out, cudaStream_t st);
 template <class S>
 cudaError_t launch_fields(const FieldArgs& F, const S* f, const Scratch& W, bool velocity, cudaStream_t st);
-// rho^r, rho^b of every node into W.rho (the contact angle's input)
+// phi = rho_r - rho_b of every node into W.rho[0] (the contact angle's input)
 template <class S>
-cudaError_t launch_rho(const FieldArgs& F, const S* f, const Scratch& W, cudaStream_t st);
+cudaError_t launch_phi(const FieldArgs& F, const S* f, const Scratch& W, cudaStream_t st);
 cudaError_t launch_angle(const FieldArgs& F, const Scratch& W, double zref, double level, double* part, double* out,
                          cudaStream_t st);
 // pressure tensor of Sec. 4.1 (after launch_fields with velocity): every node,

@@ -47,11 +47,15 @@ struct Codec;
 
 template <>
 struct Codec<float> {
+    using Pair = float2;  // the two components' values of one velocity, side by side
     static constexpr bool kDeviation = false;
     static constexpr bool kDitherMoving = false;
     static __device__ __forceinline__ float load(const float* p) { return __ldg(p); }
+    static __device__ __forceinline__ float2 load2(const float* p) { return __ldg((const float2*)p); }
     static __device__ __forceinline__ float val(float v) { return v; }
+    static __device__ __forceinline__ float2 val2(float2 v) { return v; }
     static __device__ __forceinline__ void store(float* p, float v) { *p = v; }
+    static __device__ __forceinline__ void store2(float* p, float a, float b) { *(float2*)p = make_float2(a, b); }
 };
 // Random bits for stochastic rounding. A 32-bit hash per node and step (the
 // 32-bit finaliser of MurmurHash3 applied to a combined key); value j of the
@@ -79,10 +83,14 @@ __device__ __forceinline__ uint32_t rand16(uint32_t h, int j)
 
 template <>
 struct Codec<__half> {
+    using Pair = __half2;
     static constexpr bool kDeviation = true;
     static constexpr bool kDitherMoving = false;  // 11 significant bits: only the rest value is dithered
     static __device__ __forceinline__ float load(const __half* p) { return __half2float(__ldg(p)); }
+    static __device__ __forceinline__ float2 load2(const __half* p) { return __half22float2(__ldg((const __half2*)p)); }
     static __device__ __forceinline__ float val(__half v) { return __half2float(v); }
+    static __device__ __forceinline__ float2 val2(__half2 v) { return __half22float2(v); }
+    static __device__ __forceinline__ void put2(__half* p, __half a, __half b) { *(__half2*)p = __halves2half2(a, b); }
     static __device__ __forceinline__ __half rn(float v) { return __float2half_rn(v); }
     // stochastic rounding: add a uniform dither of one unit in the last place
     // (r16 / 2^16 - 1/2 units, the unit taken from v's binade), round to nearest
@@ -97,10 +105,20 @@ struct Codec<__half> {
 };
 template <>
 struct Codec<__nv_bfloat16> {
+    using Pair = __nv_bfloat162;
     static constexpr bool kDeviation = true;
     static constexpr bool kDitherMoving = true;  // 8 significant bits: every value is dithered
     static __device__ __forceinline__ float load(const __nv_bfloat16* p) { return __bfloat162float(__ldg(p)); }
+    static __device__ __forceinline__ float2 load2(const __nv_bfloat16* p)
+    {
+        return __bfloat1622float2(__ldg((const __nv_bfloat162*)p));
+    }
     static __device__ __forceinline__ float val(__nv_bfloat16 v) { return __bfloat162float(v); }
+    static __device__ __forceinline__ float2 val2(__nv_bfloat162 v) { return __bfloat1622float2(v); }
+    static __device__ __forceinline__ void put2(__nv_bfloat16* p, __nv_bfloat16 a, __nv_bfloat16 b)
+    {
+        *(__nv_bfloat162*)p = __halves2bfloat162(a, b);
+    }
     static __device__ __forceinline__ __nv_bfloat16 rn(float v) { return __float2bfloat16_rn(v); }
     // stochastic rounding: BF16 is the upper half of the FP32 word, so adding
     // 16 uniform bits to the lower half and truncating rounds the magnitude up
@@ -114,18 +132,22 @@ struct Codec<__nv_bfloat16> {
     static __device__ __forceinline__ void store(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
 };
 
-// Lattice storage: 2*19 population planes of `slot` elements each, slot
-// index a*19 + k. Inside a slot, node (x, y, z) sits at
-//   z*plane + (y + 1)*px + (x + gx),
+// Lattice storage: 19 population planes ("slots") of `slot` nodes each, one
+// per velocity k, every node holding the two components' values side by side
+// (r then b): value (a, k) of the node at offset o sits at element
+// 2 (k slot + o) + a. So one 8-byte (FP32) or 4-byte (16-bit) access moves
+// both components of a velocity, and a warp's access to one slot covers 256
+// (128) contiguous bytes. Inside a slot, node (x, y, z) sits at
+//   o = z*plane + (y + 1)*px + (x + gx),
 // with gx = 128 bytes of row padding on the left (so x = 0 starts a 128-byte
-// line) and at least one element on the right, and one ghost row above and
-// below each plane. Ghost row y = -1 mirrors y = ny-1 and y = ny mirrors
-// y = 0, so a tile plus its one-node ring is one box across the periodic y
-// edges; the step kernels write real nodes only, and a row copy refreshes
-// the images where a reader needs them (the TMA-staged step, which takes the
-// periodic x images from strips of real columns instead). The initial
-// populations also fill ghost columns x = -1 and x = nx; nothing relies on
-// them afterwards.
+// line) and at least one node on the right, and one ghost row above and below
+// each plane. Ghost row y = -1 mirrors y = ny-1 and y = ny mirrors y = 0, so a
+// tile plus its one-node ring is one box across the periodic y edges; the step
+// kernels write real nodes only, and a row copy refreshes the images where a
+// reader needs them (the TMA-staged step, which takes the periodic x images
+// from strips of real columns instead). The initial populations also fill
+// ghost columns x = -1 and x = nx; nothing relies on them afterwards. px,
+// plane and slot count nodes.
 struct Layout {
     int nx, ny, nz, px, gx;
     long long plane, slot;
@@ -133,27 +155,31 @@ struct Layout {
     {
         return (long long)z * plane + (long long)(y + 1) * px + (x + gx);
     }
+    // element index of value (a, k) of the node at slot offset o
+    __host__ __device__ __forceinline__ long long at(int a, int k, long long o) const { return 2 * ((long long)k * slot + o) + a; }
 };
 
+// Element accessor of one (component, velocity): node offset o -> p[2 o]
+// with p = f + L.at(a, k, 0).
 // Write the ghost images (only) of node (x, y) of the plane at zoff.
 template <class S>
 __device__ __forceinline__ void put_ghosts(S* __restrict__ p, const Layout& L, int x, int y, long long zoff, float v)
 {
     const long long row = zoff + (long long)(y + 1) * L.px + L.gx;
     const bool xl = x == L.nx - 1, xr = x == 0;
-    if (xl) Codec<S>::store(p + row - 1, v);
-    if (xr) Codec<S>::store(p + row + L.nx, v);
+    if (xl) Codec<S>::store(p + 2 * (row - 1), v);
+    if (xr) Codec<S>::store(p + 2 * (row + L.nx), v);
     if (y == L.ny - 1) {
         const long long g = zoff + L.gx;  // row y = -1
-        Codec<S>::store(p + g + x, v);
-        if (xl) Codec<S>::store(p + g - 1, v);
-        if (xr) Codec<S>::store(p + g + L.nx, v);
+        Codec<S>::store(p + 2 * (g + x), v);
+        if (xl) Codec<S>::store(p + 2 * (g - 1), v);
+        if (xr) Codec<S>::store(p + 2 * (g + L.nx), v);
     }
     if (y == 0) {
         const long long g = zoff + (long long)(L.ny + 1) * L.px + L.gx;  // row y = ny
-        Codec<S>::store(p + g + x, v);
-        if (xl) Codec<S>::store(p + g - 1, v);
-        if (xr) Codec<S>::store(p + g + L.nx, v);
+        Codec<S>::store(p + 2 * (g + x), v);
+        if (xl) Codec<S>::store(p + 2 * (g - 1), v);
+        if (xr) Codec<S>::store(p + 2 * (g + L.nx), v);
     }
 }
 
@@ -163,12 +189,12 @@ __host__ __device__ __forceinline__ bool has_ghost(const Layout& L, int x, int y
     return x == 0 || x == L.nx - 1 || y == 0 || y == L.ny - 1;
 }
 
-// Store v for node (x, y) of the plane at zoff into slot base p, with the
-// ghost images of edge nodes.
+// Store v for node (x, y) of the plane at zoff through the accessor p
+// (p = f + L.at(a, k, 0)), with the ghost images of edge nodes.
 template <class S>
 __device__ __forceinline__ void put(S* __restrict__ p, const Layout& L, int x, int y, long long zoff, float v)
 {
-    Codec<S>::store(p + zoff + (long long)(y + 1) * L.px + L.gx + x, v);
+    Codec<S>::store(p + 2 * (zoff + (long long)(y + 1) * L.px + L.gx + x), v);
     if (has_ghost(L, x, y)) put_ghosts<S>(p, L, x, y, zoff, v);
 }
 
@@ -241,8 +267,9 @@ __device__ __forceinline__ void clock_tick(uint32_t* clk)
     }
 }
 
-// elements in 16 bytes: the ring column a TMA box carries on each side of a tile
+// nodes in 16 bytes (a node holds two values): the ring columns a TMA box
+// carries on each side of a tile
 template <class S>
-__host__ __device__ constexpr int ghost_x() { return 16 / (int)sizeof(S); }
+__host__ __device__ constexpr int ghost_x() { return 16 / (2 * (int)sizeof(S)); }
 
 }  // namespace lbsc

@@ -89,11 +89,13 @@ __device__ __forceinline__ void step_item(const StepArgs<S>& A, int col, int za,
         else if constexpr (kGeneral) so_ = (__ldg(nbmask + zoff + own) & kSelfSolid) != 0;
         else so_ = wall_plane;
         if (!so_) {
-            const S* p = src + (zoff + own);  // per-thread node pointer, uniform slot offsets
+            const S* p = src + 2 * (long long)(zoff + own);  // per-thread node pointer, uniform slot offsets
 #pragma unroll
-            for (int a = 0; a < 2; ++a)
-#pragma unroll
-                for (int k = 0; k < Q; ++k) ro_[a][k] = Codec<S>::load(p + (long long)(a * Q + k) * slot);
+            for (int k = 0; k < Q; ++k) {
+                const float2 t = Codec<S>::load2(p + 2 * k * slot);  // both components of velocity k
+                ro_[0][k] = t.x;
+                ro_[1][k] = t.y;
+            }
         }
 #pragma unroll
         for (int i = 0; i < NIT; ++i) {
@@ -102,9 +104,9 @@ __device__ __forceinline__ void step_item(const StepArgs<S>& A, int col, int za,
             else if constexpr (kGeneral) si_[i] = (__ldg(nbmask + zoff + it_off[i]) & kSelfSolid) != 0;
             else si_[i] = wall_plane;
             if (!si_[i]) {
-                const S* p = src + (it_a[i] * Q * slot + zoff + it_off[i]);
+                const S* p = src + 2 * (long long)(zoff + it_off[i]) + it_a[i];  // one component of the ring node
 #pragma unroll
-                for (int k = 0; k < Q; ++k) ri_[i][k] = Codec<S>::load(p + (long long)k * slot);
+                for (int k = 0; k < Q; ++k) ri_[i][k] = Codec<S>::load(p + 2 * k * slot);
             }
         }
     };

@@ -239,9 +239,9 @@ struct Dest {
 // remainder of the node's mass, which Eq. Equil and BGK leave unchanged, so
 // that rounded lattice weights (1/3 + 6/18 + 12/36 != 1 in FP32) and 16-bit
 // rounding of the stored values do not bias the mass.
-// The two components are the lanes of packed pairs, so each destination
-// address is formed once per velocity and component b's slot is reached by a
-// uniform offset; opposite velocities are taken together (c_kbar.u = -c_k.u).
+// The two components are the lanes of packed pairs and are stored side by
+// side, so each destination takes one paired store per velocity; opposite
+// velocities are taken together (c_kbar.u = -c_k.u).
 // For 16-bit storage the rest value, which balances the node's mass (taken
 // exactly from m36 and the stored moving values), is rounded stochastically:
 // round-to-nearest of nearly equal bulk values would bias the mass of every
@@ -285,7 +285,6 @@ __device__ __forceinline__ void collide_store(const float (&rc)[2], const float 
         base = sp2(0.f);
     }
     const long long slot = L.slot;
-    const long long cslot = (long long)Q * slot;  // component b's slots follow component r's
     const int self = D.zo[1] + D.ro[1] + D.xo[1];
     float2 sum = sp2(0.f), sax = sp2(0.f), sdi = sp2(0.f);
     uint32_t hsh = 0;
@@ -324,7 +323,7 @@ __device__ __forceinline__ void collide_store(const float (&rc)[2], const float 
             const int qo = wall ? self : D.zo[cz(kk) + 1] + D.ro[cy(kk) + 1] + D.xo[cx(kk) + 1];
             if constexpr (kCheckBounds)
                 if (!in_bounds(qo, slot, D.err)) continue;
-            S* q = dst + qo + (long long)(wall ? opp(kk) : kk) * slot;
+            S* q = dst + 2 * (qo + (long long)(wall ? opp(kk) : kk) * slot);  // the pair of both components
             if constexpr (Codec<S>::kDeviation) {
                 S h0, h1;
                 if constexpr (Codec<S>::kDitherMoving) {
@@ -337,18 +336,16 @@ __device__ __forceinline__ void collide_store(const float (&rc)[2], const float 
                 const float2 hv = f2(Codec<S>::val(h0), Codec<S>::val(h1));
                 if (is_axis(kk)) sax = add2(sax, hv);
                 else sdi = add2(sdi, hv);
-                q[0] = h0;
-                q[cslot] = h1;
+                Codec<S>::put2(q, h0, h1);
             } else {
                 sum = add2(sum, s);
-                Codec<S>::store(q, s.x);
-                Codec<S>::store(q + cslot, s.y);
+                Codec<S>::store2(q, s.x, s.y);
             }
         }
     }
     if constexpr (kCheckBounds)
         if (!in_bounds(self, slot, D.err)) return;
-    S* q0 = dst + self;
+    S* q0 = dst + 2 * (long long)self;
     if constexpr (Codec<S>::kDeviation) {
         uint32_t hrest;
         if constexpr (Codec<S>::kDitherMoving) hrest = node_hash(hsh, 0x632BE5ABu);  // a second full mixing round
@@ -359,12 +356,10 @@ __device__ __forceinline__ void collide_store(const float (&rc)[2], const float 
         const float2 x0 = sub2(f2(m36[0], m36[1]), fma2(sp2(2.0f), sax, sdi));
         float2 s0 = mul2(x0, sp2(1.0f / 12.0f));
         s0 = fma2(fma2(sp2(-12.0f), s0, x0), sp2(1.0f / 12.0f), s0);
-        q0[0] = Codec<S>::sr(s0.x, rand16(hrest, 0));
-        q0[cslot] = Codec<S>::sr(s0.y, rand16(hrest, 1));
+        Codec<S>::put2(q0, Codec<S>::sr(s0.x, rand16(hrest, 0)), Codec<S>::sr(s0.y, rand16(hrest, 1)));
     } else {
         const float2 r0 = sub2(R, sum);
-        Codec<S>::store(q0, r0.x);
-        Codec<S>::store(q0 + cslot, r0.y);
+        Codec<S>::store2(q0, r0.x, r0.y);
     }
 }
 

@@ -3,8 +3,8 @@
 //
 // A CTA owns a 32 x TY tile of columns and a z segment, as in the
 // load-from-global kernel, but one thread streams whole planes of the tile
-// plus its one-node ring (all 38 population slots, one 5-D tensor box per
-// plane) into an NS-deep ring of shared-memory stages with
+// plus its one-node ring (all 19 slots of paired values, one 4-D tensor box
+// per plane) into an NS-deep ring of shared-memory stages with
 // cp.async.bulk.tensor, completion tracked by one mbarrier per stage. The
 // compute warps reduce a landed plane to rho, j and psi out of shared memory
 // while the following planes are in flight, then collide and push the plane
@@ -58,33 +58,35 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity)
     return false;
 }
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-__device__ __forceinline__ void tma_load_5d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1, int c2,
-                                            int c3, int c4)
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1, int c2,
+                                            int c3)
 {
     asm volatile(
-        "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(smem_u32(dst)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(smem_u32(bar))
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
         : "memory");
 }
 
-// Geometry of one stage: the main box [a][k][row][col] of 2 x 19 x (TY+2) x BX
-// elements, column c holding x = x0 - GX + c (16 bytes of columns left of the
-// tile, so the box starts on a 16-byte boundary), row r holding y = y0 - 1 + r;
-// then two strips [a][k][row][SX] of 16 bytes of columns each, loaded only by
-// the tiles at the x edges: the left strip holds the columns around
-// x = nx - 1 (the periodic image of x = -1), the right strip x = 0 .. SX - 1
-// (the image of x = nx). Rows y = -1 and y = ny come from the ghost rows.
+// Geometry of one stage: the main box [k][row][col][a] of 19 x (TY+2) x BX
+// nodes of two values, column c holding x = x0 - GX + c (16 bytes of columns
+// left of the tile, so the box starts on a 16-byte boundary), row r holding
+// y = y0 - 1 + r; then two strips [k][row][SX][a] of 16 bytes of columns
+// each, loaded only by the tiles at the x edges: the left strip holds the
+// columns around x = nx - 1 (the periodic image of x = -1), the right strip
+// x = 0 .. SX - 1 (the image of x = nx). Rows y = -1 and y = ny come from the
+// ghost rows. Element offsets below count values (two per node).
 template <class S, int TY>
 struct TmaGeom {
     static constexpr int TX = 32, HX = TX + 2, HY = TY + 2;
-    static constexpr int GX = ghost_x<S>();
-    static constexpr int BX = sizeof(S) == 4 ? 40 : 48;  // >= 32 + 2 GX, a multiple of 16 bytes
-    static constexpr int SX = GX;                        // strip width: 16 bytes of columns
+    static constexpr int GX = ghost_x<S>();                  // nodes in 16 bytes
+    static constexpr int BX = TX + 2 * GX;                   // the box's nodes per row: 16 bytes of columns each side
+    static constexpr int SX = GX;                            // strip width: 16 bytes of columns
     static constexpr int MAIN_ELEMS = 2 * Q * HY * BX;
+    static constexpr int MAIN_SPAN = (MAIN_ELEMS * (int)sizeof(S) + 127) / 128 * 128 / (int)sizeof(S);  // 128-B aligned
     static constexpr int STRIP_BOX_ELEMS = 2 * Q * HY * SX;
     static constexpr int STRIP_ELEMS = (STRIP_BOX_ELEMS * (int)sizeof(S) + 127) / 128 * 128 / (int)sizeof(S);
-    static constexpr int STAGE_ELEMS = MAIN_ELEMS + 2 * STRIP_ELEMS;
+    static constexpr int STAGE_ELEMS = MAIN_SPAN + 2 * STRIP_ELEMS;
     static constexpr uint32_t MAIN_BYTES = MAIN_ELEMS * sizeof(S);
     static constexpr uint32_t STRIP_BOX_BYTES = STRIP_BOX_ELEMS * sizeof(S);
     static constexpr uint32_t STAGE_BYTES = STAGE_ELEMS * sizeof(S);
@@ -106,7 +108,10 @@ __global__ void __launch_bounds__(32 * TY, (kTmaCtas<TY, kTauOne>)) step_tma_ker
     constexpr int TX = 32, NT = TX * TY, HX = G::HX, HY = G::HY, GX = G::GX, BX = G::BX, SX = G::SX;
     constexpr int RING = 2 * HX + 2 * TY;
     constexpr int NIT = (2 * RING + NT - 1) / NT;
-    static_assert(G::STAGE_BYTES % 128 == 0 && G::MAIN_BYTES % 128 == 0, "stages and strips stay 128-byte aligned");
+    static_assert(G::STAGE_BYTES % 128 == 0 && (G::MAIN_SPAN * sizeof(S)) % 128 == 0,
+                  "stages and strips stay 128-byte aligned");
+    static_assert((2 * BX * sizeof(S)) % 16 == 0 && (2 * SX * sizeof(S)) % 16 == 0, "box rows are whole 16-byte units");
+    using P2 = typename Codec<S>::Pair;
 
     extern __shared__ unsigned char smem_raw[];
     unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
@@ -178,13 +183,13 @@ __global__ void __launch_bounds__(32 * TY, (kTmaCtas<TY, kTauOne>)) step_tma_ker
                 const int xr = x0 - 1 + ix;  // the ring node's x (unwrapped)
                 if (xr < 0) {
                     it_src[i] = 1;  // x = -1: the image of x = nx - 1
-                    it_base[i] = G::MAIN_ELEMS + (a * Q * HY + iy) * SX + ol;
+                    it_base[i] = G::MAIN_SPAN + 2 * (iy * SX + ol) + a;
                 } else if (xr >= nx && xr - nx < SX) {
                     it_src[i] = 2;  // x >= nx: the images of x - nx
-                    it_base[i] = G::MAIN_ELEMS + G::STRIP_ELEMS + (a * Q * HY + iy) * SX + xr - nx;
+                    it_base[i] = G::MAIN_SPAN + G::STRIP_ELEMS + 2 * (iy * SX + xr - nx) + a;
                 } else {
                     it_src[i] = 0;
-                    it_base[i] = (a * Q * HY + iy) * BX + ix - 1 + GX;
+                    it_base[i] = 2 * (iy * BX + ix - 1 + GX) + a;
                 }
             }
         }
@@ -198,9 +203,10 @@ __global__ void __launch_bounds__(32 * TY, (kTmaCtas<TY, kTauOne>)) step_tma_ker
                 fence_proxy_async();
                 mbar_expect_tx(b, G::MAIN_BYTES + (left_edge ? G::STRIP_BOX_BYTES : 0u) +
                                       (right_edge ? G::STRIP_BOX_BYTES : 0u));
-                tma_load_5d(stg, &tmap, b, x0 + L.gx - GX, y0, zp, 0, 0);
-                if (left_edge) tma_load_5d(stg + G::MAIN_ELEMS, &tstrip, b, sl, y0, zp, 0, 0);
-                if (right_edge) tma_load_5d(stg + G::MAIN_ELEMS + G::STRIP_ELEMS, &tstrip, b, L.gx, y0, zp, 0, 0);
+                // x coordinates count values (two per node): 16-byte aligned, as the copy requires
+                tma_load_4d(stg, &tmap, b, 2 * (x0 + L.gx - GX), y0, zp, 0);
+                if (left_edge) tma_load_4d(stg + G::MAIN_SPAN, &tstrip, b, 2 * sl, y0, zp, 0);
+                if (right_edge) tma_load_4d(stg + G::MAIN_SPAN + G::STRIP_ELEMS, &tstrip, b, 2 * L.gx, y0, zp, 0);
             }
         };
 
@@ -220,16 +226,22 @@ __global__ void __launch_bounds__(32 * TY, (kTmaCtas<TY, kTauOne>)) step_tma_ker
                 for (int a = 0; a < 2; ++a) j[a][0] = j[a][1] = j[a][2] = 0.f;
                 if (!solid && own_rd) {
                     float w[2][Q];
+                    // both components of velocity k in one shared-memory load
+                    if (!own_strip) {
+                        const P2* so = (const P2*)(st + 2 * ((ty + 1) * BX + tx + GX));
 #pragma unroll
-                    for (int a = 0; a < 2; ++a) {
-                        if (!own_strip) {
-                            const S* so = st + (a * Q * HY + ty + 1) * BX + tx + GX;
+                        for (int k = 0; k < Q; ++k) {
+                            const float2 t = Codec<S>::val2(so[k * HY * BX]);
+                            w[0][k] = t.x;
+                            w[1][k] = t.y;
+                        }
+                    } else {
+                        const P2* so = (const P2*)(st + G::MAIN_SPAN + G::STRIP_ELEMS + 2 * ((ty + 1) * SX + gx - nx));
 #pragma unroll
-                            for (int k = 0; k < Q; ++k) w[a][k] = Codec<S>::val(so[k * HY * BX]);
-                        } else {
-                            const S* so = st + G::MAIN_ELEMS + G::STRIP_ELEMS + (a * Q * HY + ty + 1) * SX + gx - nx;
-#pragma unroll
-                            for (int k = 0; k < Q; ++k) w[a][k] = Codec<S>::val(so[k * HY * SX]);
+                        for (int k = 0; k < Q; ++k) {
+                            const float2 t = Codec<S>::val2(so[k * HY * SX]);
+                            w[0][k] = t.x;
+                            w[1][k] = t.y;
                         }
                     }
                     moments2<S>(w, ref, rho, j, m);
@@ -259,10 +271,10 @@ __global__ void __launch_bounds__(32 * TY, (kTmaCtas<TY, kTauOne>)) step_tma_ker
                         const S* si = st + it_base[q];
                         if (it_src[q] == 0) {
 #pragma unroll
-                            for (int k = 0; k < Q; ++k) w[k] = Codec<S>::val(si[k * HY * BX]);
+                            for (int k = 0; k < Q; ++k) w[k] = Codec<S>::val(si[2 * k * HY * BX]);
                         } else {
 #pragma unroll
-                            for (int k = 0; k < Q; ++k) w[k] = Codec<S>::val(si[k * HY * SX]);
+                            for (int k = 0; k < Q; ++k) w[k] = Codec<S>::val(si[2 * k * HY * SX]);
                         }
                         ps = psi_of(rho_of<S>(w, ref_a));
                     }
