@@ -51,6 +51,12 @@ WORKLOADS = {
     "slabs": dict(dims=(128, 128, 128), radius=30.0, precision="f32", w=0.05, nslab=2, schedule=(8, 19, 4)),
     "sizes": dict(edges=(32, 64, 128, 256), radius_frac=30.0 / 128.0, precision="f32", steps=20000,
                   w=(0.03, 0.06, 0.09)),
+    # the paper's own parameter set (Sec. 4): g = 0.16, W36 weights at force scale 1, a one-sided wall
+    # (eta_wall_r, eta_wall_b) = (0, eta) with eta = 0.1 / 0.2 / 0.3, drops of initial volume 70^3 in 128^3
+    # and 141^3 in 256^3 (hemispheres of that volume on the wall), the same step count for both sizes
+    "sizes-paper": dict(edges=(128, 256), drop_edge={128: 70, 256: 141}, precision="f32", steps=20000,
+                        w=(0.1, 0.2, 0.3), prm=dict(g_br=0.16, force_weights=1, force_scale=1.0),
+                        wall="one-sided"),
     # adjoint calibration: 64^3, R = 16, 2000 steps, checkpoints every 100
     "adjoint": dict(dims=(64, 64, 64), radius=16.0, precision="f32", steps=2000, ckpt=100),
     # surface tensions (Sec. 4.1-4.2): 8x8x128 periodic lamellae (gamma_LG), 8x8x(64+2) slabs of each
@@ -104,16 +110,17 @@ def step_source_sha256() -> str:
     return h.hexdigest()
 
 
-def step_kernel_traffic(workload: str):
-    """Per-launch DRAM bytes of the step kernel from the committed ncu summary,
-    or None when the kernel's sources changed since it was taken."""
+def step_kernel_traffic(workload: str, schedule: str | None):
+    """Per-launch DRAM bytes of the step kernel under `schedule` from the
+    committed ncu summary, or None when the kernel's sources changed since it
+    was taken or that schedule was not captured."""
     path = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
     try:
         with open(path) as f:
             rec = json.load(f)
-        if rec.get("step_sources_sha256") != step_source_sha256():
+        if rec.get("step_sources_sha256") != step_source_sha256() or not schedule:
             return None
-        return rec.get("bytes_per_launch", {}).get(workload)
+        return rec.get("bytes_per_launch", {}).get(f"{workload} {schedule}")
     except Exception:
         return None
 
@@ -341,8 +348,11 @@ def run_ours(args):
     bpl = BYTES_PER_LU[prec]
     achieved = nf * bpl / (step_ms * 1e-3) / 1e9
     roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-            "frac": round(achieved / peak, 4), "traffic": step_kernel_traffic(args.workload),
-            "peak_source": peak_kind, "kernel": "step_kernel",
+            "frac": round(achieved / peak, 4),
+            "traffic": step_kernel_traffic(args.workload, tune.name(schedule) if schedule else None),
+            "peak_source": peak_kind,
+            "kernel": ("step_tma_kernel (with its ghost-row copy in the timed steps)"
+                       if schedule and schedule[0] == "tma" else "step_kernel"),
             "algorithmic_bytes_per_launch": nf * bpl}
     cpu = None
     if not args.no_cpu_baseline and ws == 1:
@@ -764,10 +774,19 @@ def run_sizes(args):
     from paper_0910_3915_gb300 import workloads as W
 
     torch.cuda.set_device(0)
-    wl = WORKLOADS["sizes"]
+    wl = WORKLOADS[args.workload]
     T = args.steps if args.steps != 20000 else wl["steps"]
     T1 = T - T // 10
     ws, edges = wl["w"], wl["edges"]
+    base = wl.get("prm", CONTACT)
+
+    def radius(L):
+        if "drop_edge" in wl:  # a hemisphere of the paper's initial drop volume e^3
+            return (3.0 * wl["drop_edge"][L] ** 3 / (2.0 * math.pi)) ** (1.0 / 3.0)
+        return wl["radius_frac"] * L
+
+    def wall(w):
+        return (0.0, w) if wl.get("wall") == "one-sided" else W.wall_split(w)
     stream = torch.cuda.current_stream()
     ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
     res = {}
@@ -780,8 +799,8 @@ def run_sizes(args):
 
     small = [L for L in edges if L < 256]
     cases = [(L, w) for L in small for w in ws]
-    fields = [W.droplet_fields(L, L, L, wl["radius_frac"] * L, seed=0) for L, _ in cases]
-    params = [lbsc.Params(**CONTACT, eta_wall_r=W.wall_split(w)[0], eta_wall_b=W.wall_split(w)[1]) for _, w in cases]
+    fields = [W.droplet_fields(L, L, L, radius(L), seed=0) for L, _ in cases]
+    params = [lbsc.Params(**base, eta_wall_r=wall(w)[0], eta_wall_b=wall(w)[1]) for _, w in cases]
     batch = lbsc.Batch(fields, params, wl["precision"])
     e0, e1 = ev(), ev()
     e0.record(stream)
@@ -801,9 +820,9 @@ def run_sizes(args):
     batch.close()
     for L in [L for L in edges if L >= 256]:
         for w in ws:
-            rr, rb = W.droplet_fields(L, L, L, wl["radius_frac"] * L, seed=0)
-            er, eb = W.wall_split(w)
-            lat = lbsc.Lattice(rr, rb, wl["precision"]).set_params(**CONTACT, eta_wall_r=er, eta_wall_b=eb)
+            rr, rb = W.droplet_fields(L, L, L, radius(L), seed=0)
+            er, eb = wall(w)
+            lat = lbsc.Lattice(rr, rb, wl["precision"]).set_params(**base, eta_wall_r=er, eta_wall_b=eb)
             e0, e1 = ev(), ev()
             e0.record(stream)
             lat.step(T1)
@@ -835,8 +854,11 @@ def run_sizes(args):
         "metric": METRIC, "value": round(total_lu / (total_ms * 1e-3) / 1e6, 1), "unit": "MLUPS", "n_gpus": 1,
         "steps": T, "warmup": 0, "ms_per_step": round(total_ms / T, 5), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": wl["precision"], "data": "synthetic",
-        "config": {"workload": "theta vs lattice size: cubic %s, R = %.3f L, w = %s, %d steps each"
-                               % ("/".join(str(L) for L in edges), wl["radius_frac"], list(ws), T)},
+        "config": {"workload": "theta vs lattice size: cubic %s, R = %s, %s = %s, %d steps each"
+                               % ("/".join(str(L) for L in edges),
+                                  "/".join("%.1f" % radius(L) for L in edges), "eta (one-sided)"
+                                  if wl.get("wall") == "one-sided" else "w", list(ws), T),
+                   "params": base},
         "sizes": rows,
     }
     print(json.dumps(line), flush=True)
@@ -1056,7 +1078,7 @@ def main():
         run_angles(args)
     elif args.workload == "young":
         run_young(args)
-    elif args.workload == "sizes":
+    elif args.workload in ("sizes", "sizes-paper"):
         run_sizes(args)
     else:
         run_ours(args)

@@ -43,7 +43,9 @@ struct lb_ctx {
     int y_tiles_req = 0;  // y-tiles of the step kernel (0 = ceil(ny / tile_y))
     int nseg_cache = 0;  // segments per tile column for the current schedule (0 = not computed)
     long long steps = 0;
-    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    // CUDA graphs of 2^i steps (i = 0 .. kGraphLevels - 1) for each starting buffer
+    static constexpr int kGraphLevels = 6;
+    cudaGraphExec_t graph[2][kGraphLevels] = {};
     int variant = LB_STEP_AUTO, stages = 0;  // step kernel selection
     CUtensorMap tmap[2][3][2];               // per buffer, per tile height 4/8/16: main box, x-edge strip
     bool tmap_ok[2][3] = {{false, false, false}, {false, false, false}};
@@ -137,11 +139,12 @@ static FieldArgs field_args(const lb_ctx* c)
 static void drop_graphs(lb_ctx* c)
 {
     c->nseg_cache = 0;
-    for (int i = 0; i < 2; ++i)
-        if (c->graph[i]) {
-            cudaGraphExecDestroy(c->graph[i]);
-            c->graph[i] = nullptr;
-        }
+    for (int p = 0; p < 2; ++p)
+        for (int i = 0; i < lb_ctx::kGraphLevels; ++i)
+            if (c->graph[p][i]) {
+                cudaGraphExecDestroy(c->graph[p][i]);
+                c->graph[p][i] = nullptr;
+            }
 }
 
 static void set_kparams(lb_ctx* c)
@@ -732,42 +735,56 @@ int lb_set_schedule(lb_ctx* c, int tile_y, int z_segments)
     return lb_set_tiling(c, tile_y, 0, z_segments);
 }
 
-int lb_step(lb_ctx* c, int nsteps)
+// Capture the step graphs of every size for both starting buffers (after a
+// change of schedule or parameters dropped them), so that no later call
+// captures inside a caller's timed or captured region.
+static int capture_graphs(lb_ctx* c)
 {
-    if (!c || nsteps < 0) return fail(c, LB_ERR_ARG, "lb_step: bad argument");
-    const int G = lb_ctx::kGraphSteps;
-    int n = nsteps;
-    const int ns = tma_stages(c);
-    if (ns && !c->ghost_ok && n > 0) {  // the TMA path reads the source's ghost images
-        LB_CUDA(c, refresh_ghosts_any(c, c->cur, c->stream));
-        c->ghost_ok = true;
-    }
-    if (n >= G) {
-        int& par = c->cur;
-        if (!c->graph[par]) {
+    if (c->graph[0][0]) return LB_OK;
+    nseg_for(c, ((c->nx + 31) / 32) * y_tiles(c));
+    for (int p = 0; p < 2; ++p)
+        for (int i = 0; i < lb_ctx::kGraphLevels; ++i) {
             cudaGraph_t g = nullptr;
-            nseg_for(c, ((c->nx + 31) / 32) * y_tiles(c));
             LB_CUDA(c, cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
-            int p2 = par;
-            cudaError_t e = launch_steps(c, G, p2, c->cap);
+            int p2 = p;
+            cudaError_t e = launch_steps(c, 1 << i, p2, c->cap);
             cudaError_t e2 = cudaStreamEndCapture(c->cap, &g);
             if (e != cudaSuccess) return cuda_fail(c, e, "lb_step: capture");
             if (e2 != cudaSuccess) return cuda_fail(c, e2, "lb_step: end capture");
-            e = cudaGraphInstantiate(&c->graph[par], g, 0);
+            e = cudaGraphInstantiate(&c->graph[p][i], g, 0);
             cudaGraphDestroy(g);
             if (e != cudaSuccess) return cuda_fail(c, e, "lb_step: graph instantiate");
         }
-        while (n >= G) {
-            LB_CUDA(c, cudaGraphLaunch(c->graph[par], c->stream));
-            n -= G;  // G is even: parity unchanged
-        }
+    return LB_OK;
+}
+
+int lb_step(lb_ctx* c, int nsteps)
+{
+    if (!c || nsteps < 0) return fail(c, LB_ERR_ARG, "lb_step: bad argument");
+    if (nsteps == 0) return LB_OK;
+    const int ns = tma_stages(c);
+    if (ns && !c->ghost_ok) {  // the TMA path reads the source's ghost images
+        LB_CUDA(c, refresh_ghosts_any(c, c->cur, c->stream));
+        c->ghost_ok = true;
     }
-    int par = c->cur;
-    cudaError_t e = launch_steps(c, n, par, c->stream);
-    if (e != cudaSuccess) return cuda_fail(c, e, "lb_step: launch");
+    // n steps as graphs of 2^i steps: one launch per set bit (and per 32 steps),
+    // so that consecutive kernels follow each other without host launch gaps
+    const int rc = capture_graphs(c);
+    if (rc != LB_OK) return rc;
+    constexpr int top = lb_ctx::kGraphLevels - 1;
+    int par = c->cur, n = nsteps;
+    while (n >= (1 << top)) {
+        LB_CUDA(c, cudaGraphLaunch(c->graph[par][top], c->stream));
+        n -= 1 << top;  // an even number of steps: the buffers end where they began
+    }
+    for (int i = top - 1; i >= 0; --i)
+        if (n & (1 << i)) {
+            LB_CUDA(c, cudaGraphLaunch(c->graph[par][i], c->stream));
+            if (i == 0) par ^= 1;
+        }
     c->cur = par;
     c->steps += nsteps;
-    if (nsteps > 0) c->ghost_ok = ns != 0;  // only the TMA path leaves the images current
+    c->ghost_ok = ns != 0;  // only the TMA path leaves the images current
     return LB_OK;
 }
 

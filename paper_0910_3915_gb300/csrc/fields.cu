@@ -106,19 +106,21 @@ template <class S>
 __global__ void init_kernel(FieldArgs F, S* __restrict__ f, const double* __restrict__ rr, const double* __restrict__ rb,
                             int* err)
 {
-    const long long N = (long long)F.L.nx * F.L.ny * F.L.nz;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
-        const int x = (int)(i % F.L.nx), y = (int)((i / F.L.nx) % F.L.ny), z = (int)(i / ((long long)F.L.nx * F.L.ny));
-        for (int a = 0; a < 2; ++a) {
-            const double d = a == 0 ? rr[i] : rb[i];
-            if (err && !(isfinite(d) && d >= 0.0)) atomicOr(err, kErrInput);
-            const float rho = (float)d;
-            for (int k = 0; k < Q; ++k) {
-                float v;
-                if constexpr (Codec<S>::kDeviation) v = rho - F.P.ref[a];
-                else v = zeta(k) * rho;
-                put<S>(f + F.L.at(a, k, 0), F.L, x, y, (long long)z * F.L.plane, v);
-            }
+    const unsigned nxy = (unsigned)F.L.nx * (unsigned)F.L.ny;
+    const unsigned N = nxy * (unsigned)F.L.nz;  // below 2^31 (the layout's limit)
+    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+        const unsigned z = i / nxy, rem = i - z * nxy;
+        const int y = (int)(rem / (unsigned)F.L.nx), x = (int)(rem - (unsigned)y * F.L.nx);
+        const double d0 = rr[i], d1 = rb[i];
+        if (err && !(isfinite(d0) && d0 >= 0.0 && isfinite(d1) && d1 >= 0.0)) atomicOr(err, kErrInput);
+        const float r0 = (float)d0, r1 = (float)d1;
+        const long long zoff = (long long)z * F.L.plane;
+#pragma unroll
+        for (int k = 0; k < Q; ++k) {
+            if constexpr (Codec<S>::kDeviation)
+                put_pair<S>(f + F.L.at(0, k, 0), F.L, x, y, zoff, r0 - F.P.ref[0], r1 - F.P.ref[1]);
+            else
+                put_pair<S>(f + F.L.at(0, k, 0), F.L, x, y, zoff, zeta(k) * r0, zeta(k) * r1);
         }
     }
 }
@@ -317,6 +319,29 @@ __device__ __forceinline__ bool above(float p, float lf, bool lexact, double lev
     return (double)p > level;
 }
 
+// An interface crossing between node (x, y, z) (phi = p0) and its neighbour
+// along axis d (phi = p1): the top crossing (along z, from phi > level
+// below to phi <= level above) and the sphere-fit sums of the crossing point at
+// or above the reference plane, into the thread's accumulators acc[i * stride].
+// Kept out of line so that the FP64 work runs only in the warps that meet a
+// crossing instead of being predicated into every node's path.
+__device__ __noinline__ void add_crossing(double* acc, int stride, int x, int y, int z, int d, float p0, float p1,
+                                         double level, bool s0, double zref)
+{
+    const double q0 = phi_at(p0, level), q1 = phi_at(p1, level);
+    const double t = q0 / (q0 - q1);
+    if (d == 2 && s0) acc[0] = fmax(acc[0], z + t);  // phi > level below, <= level above
+    const double pxv = x + t * (d == 0), pyv = y + t * (d == 1), pzv = z + t * (d == 2);
+    if (pzv < zref) return;
+    const double row[4] = {2 * pxv, 2 * pyv, 2 * pzv, 1.0};
+    const double rhs = pxv * pxv + pyv * pyv + pzv * pzv;
+    acc[2 * stride] += 1.0;
+    int m = 3;
+    for (int r = 0; r < 4; ++r)
+        for (int q = r; q < 4; ++q) acc[(m++) * stride] += row[r] * row[q];
+    for (int r = 0; r < 4; ++r) acc[(13 + r) * stride] += row[r] * rhs;
+}
+
 // One thread per node (grid-stride, x fastest), reading phi at the node and at
 // its +x, +y, +z neighbours (the latter from L1/L2):
 //  [0]  (max) top phi = level crossing: z + p0/(p0 - p1) where phi > level
@@ -378,21 +403,7 @@ __global__ void __launch_bounds__(kRedThreads) angle_kernel(FieldArgs F, Scratch
             if (F.general ? (F.nbmask[F.L.off(x1, y1, z1)] & kSelfSolid) != 0 : z1 == nz - 1) continue;
             const float p1 = pn[d];
             if (s0 == above(p1, lf, lexact, level)) continue;
-            const double q0 = phi_at(p0, level), q1 = phi_at(p1, level);
-            const double t = q0 / (q0 - q1);
-            if (d == 2 && s0) ACC(0) = fmax(ACC(0), z + t);  // phi > level below, <= level above
-            const double pxv = x + t * (d == 0), pyv = y + t * (d == 1), pzv = z + t * (d == 2);
-            if (pzv < zref) continue;
-            const double row[4] = {2 * pxv, 2 * pyv, 2 * pzv, 1.0};
-            const double rhs = pxv * pxv + pyv * pyv + pzv * pzv;
-            ACC(2) += 1.0;
-            int m = 3;
-#pragma unroll
-            for (int r = 0; r < 4; ++r)
-#pragma unroll
-                for (int q = r; q < 4; ++q) ACC(m++) += row[r] * row[q];
-#pragma unroll
-            for (int r = 0; r < 4; ++r) ACC(13 + r) += row[r] * rhs;
+            add_crossing(&sacc[0][tid], kRedThreads, x, y, z, d, p0, p1, level, s0, zref);
         }
     }
     // block reduction: FP32 maxima by shuffles; FP64 values only in warps that hold some

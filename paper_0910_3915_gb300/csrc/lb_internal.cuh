@@ -198,6 +198,37 @@ __device__ __forceinline__ void put(S* __restrict__ p, const Layout& L, int x, i
     if (has_ghost(L, x, y)) put_ghosts<S>(p, L, x, y, zoff, v);
 }
 
+// Store both components' values (v0, v1) of velocity k for node (x, y) of the
+// plane at zoff (p = f + L.at(0, k, 0)), with the ghost images of edge nodes:
+// one paired store per position.
+template <class S>
+__device__ __forceinline__ void put_pair(S* __restrict__ p, const Layout& L, int x, int y, long long zoff, float v0,
+                                         float v1)
+{
+    auto st = [&](long long o) {
+        if constexpr (sizeof(S) == 4) Codec<S>::store2(p + 2 * o, v0, v1);
+        else Codec<S>::put2(p + 2 * o, Codec<S>::rn(v0), Codec<S>::rn(v1));
+    };
+    const long long row = zoff + (long long)(y + 1) * L.px + L.gx;
+    st(row + x);
+    if (!has_ghost(L, x, y)) return;
+    const bool xl = x == L.nx - 1, xr = x == 0;
+    if (xl) st(row - 1);
+    if (xr) st(row + L.nx);
+    if (y == L.ny - 1) {
+        const long long g = zoff + L.gx;  // row y = -1
+        st(g + x);
+        if (xl) st(g - 1);
+        if (xr) st(g + L.nx);
+    }
+    if (y == 0) {
+        const long long g = zoff + (long long)(L.ny + 1) * L.px + L.gx;  // row y = ny
+        st(g + x);
+        if (xl) st(g - 1);
+        if (xr) st(g + L.nx);
+    }
+}
+
 // Parameters as the kernels use them.
 struct KParams {
     float gk;            // g_br * force_scale
