@@ -310,13 +310,29 @@ __global__ void phi_kernel(FieldArgs F, const S* __restrict__ f, Scratch W)
 // phi - level in FP64 at a node whose phi is the FP32 value p
 __device__ __forceinline__ double phi_at(float p, double level) { return (double)p - level; }
 
+// p > level in FP64, out of line: the rare case the FP32 test below cannot decide
+__device__ __noinline__ bool above_fp64(float p, double level) { return (double)p > level; }
+
 // p > level, i.e. phi_at(p, level) > 0, taken in FP32 where that is exact: when
 // level is an FP32 number, or when p is far from it (the margin exceeds the
 // rounding of level to FP32 many times over); else in FP64.
 __device__ __forceinline__ bool above(float p, float lf, bool lexact, double level)
 {
     if (lexact || fabsf(p - lf) > 1e-6f * (fabsf(p) + fabsf(lf)) + 1e-30f) return p > lf;
-    return (double)p > level;
+    return above_fp64(p, level);
+}
+
+// Positive length along x, from a node to its +x neighbour, of the linear
+// interpolant of phi - level on the reference plane z0 + fz (p: phi at the
+// node, above it, at the +x neighbour and above that). Out of line, so that
+// its FP64 work runs only on that plane's rows.
+__device__ __noinline__ double plane_length(float p0, float p0up, float p1, float p1up, double fz, double level)
+{
+    const double a0 = (1 - fz) * phi_at(p0, level) + fz * phi_at(p0up, level);
+    const double a1 = (1 - fz) * phi_at(p1, level) + fz * phi_at(p1up, level);
+    if (a0 > 0 && a1 > 0) return 1.0;
+    if (a0 <= 0 && a1 <= 0) return 0.0;
+    return a0 > 0 ? a0 / (a0 - a1) : a1 / (a1 - a0);
 }
 
 // An interface crossing between node (x, y, z) (phi = p0) and its neighbour
@@ -342,7 +358,7 @@ __device__ __noinline__ void add_crossing(double* acc, int stride, int x, int y,
     for (int r = 0; r < 4; ++r) acc[(13 + r) * stride] += row[r] * rhs;
 }
 
-// One thread per node (grid-stride, x fastest), reading phi at the node and at
+// One warp per lattice row, a lane per node, reading phi at the node and at
 // its +x, +y, +z neighbours (the latter from L1/L2):
 //  [0]  (max) top phi = level crossing: z + p0/(p0 - p1) where phi > level
 //       below and <= level above (both nodes fluid);
@@ -371,26 +387,18 @@ __global__ void __launch_bounds__(kRedThreads) angle_kernel(FieldArgs F, Scratch
     const bool lexact = (double)lf == level;
     const float* __restrict__ P = W.rho[0];
     const unsigned nxy = (unsigned)nx * (unsigned)ny;
-    const unsigned N = nxy * (unsigned)nz;
-    const unsigned T = gridDim.x * blockDim.x;
-    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += T) {
-        const int z = (int)(i / nxy);
-        const unsigned rem = i - (unsigned)z * nxy;
-        const int y = (int)(rem / (unsigned)nx), x = (int)(rem - (unsigned)y * nx);
+    // a warp takes lattice rows (y, z) = w, w + W, ... (W warps in the grid), its lanes x = lane, lane + 32, ...
+    const int rows = ny * nz, nwarps = gridDim.x * (kRedThreads / 32);
+    for (int r = blockIdx.x * (kRedThreads / 32) + (tid >> 5); r < rows; r += nwarps)
+    for (int x = tid & 31; x < nx; x += 32) {
+        const int z = r / ny, y = r - z * ny;
+        const unsigned i = (unsigned)r * (unsigned)nx + (unsigned)x;
         // the node and its +x, +y, +z neighbours (the node itself past an edge), loaded together
         const float p0 = P[i];
         const float pn[3] = {P[x + 1 < nx ? i + 1 : i], P[y + 1 < ny ? i + nx : i], P[z + 1 < nz ? i + nxy : i]};
         if (z == z0 && z0 + 1 < nz) {  // reference plane: every column, solid or not
-            const int x1 = x + 1 < nx ? x + 1 : 0;
-            const unsigned i1 = i - x + x1;
-            const double a0 = (1 - fz) * phi_at(p0, level) + fz * phi_at(pn[2], level);
-            const double a1 = (1 - fz) * phi_at(P[i1], level) + fz * phi_at(P[i1 + nxy], level);
-            double len;
-            if (a0 > 0 && a1 > 0) len = 1.0;
-            else if (a0 <= 0 && a1 <= 0) len = 0.0;
-            else if (a0 > 0) len = a0 / (a0 - a1);
-            else len = a1 / (a1 - a0);
-            ACC(1) += len;
+            const unsigned i1 = x + 1 < nx ? i + 1 : i - x;
+            ACC(1) += plane_length(p0, pn[2], P[i1], P[i1 + nxy], fz, level);
         }
         if (!F.general ? (z == 0 || z == nz - 1) : (F.nbmask[F.L.off(x, y, z)] & kSelfSolid) != 0) continue;
         pmax = fmaxf(pmax, p0);
@@ -421,7 +429,8 @@ __global__ void __launch_bounds__(kRedThreads) angle_kernel(FieldArgs F, Scratch
     for (int v = 0; v < 17; ++v) {
         const bool is_max = v == 0;
         double val = ACC(v);
-        const bool held = is_max ? val > -1e299 : val != 0.0;
+        // a contribution changed the value's bits from their start (integer test: no FP64 operation)
+        const bool held = __double_as_longlong(val) != __double_as_longlong(is_max ? -1e300 : 0.0);
         if (__any_sync(0xffffffffu, held)) {
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {

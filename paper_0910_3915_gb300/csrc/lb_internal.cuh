@@ -80,6 +80,9 @@ __device__ __forceinline__ uint32_t rand16(uint32_t h, int j)
 {
     return (h * (0x9E3779B1u * (2u * (uint32_t)j + 1u))) >> 16;
 }
+// 32 random bits for the pair of values of velocity j (both components): the
+// product h * M_j whole; its two halves dither the two values
+__device__ __forceinline__ uint32_t rand32(uint32_t h, int j) { return h * (0x9E3779B1u * (2u * (uint32_t)j + 1u)); }
 
 template <>
 struct Codec<__half> {
@@ -91,6 +94,13 @@ struct Codec<__half> {
     static __device__ __forceinline__ float val(__half v) { return __half2float(v); }
     static __device__ __forceinline__ float2 val2(__half2 v) { return __half22float2(v); }
     static __device__ __forceinline__ void put2(__half* p, __half a, __half b) { *(__half2*)p = __halves2half2(a, b); }
+    // both values rounded to nearest into one pair (one conversion), and the stored values back in FP32
+    static __device__ __forceinline__ __half2 rn2(float2 v, float2& back)
+    {
+        const __half2 h = __float22half2_rn(v);
+        back = __half22float2(h);
+        return h;
+    }
     static __device__ __forceinline__ __half rn(float v) { return __float2half_rn(v); }
     // stochastic rounding: add a uniform dither of one unit in the last place
     // (r16 / 2^16 - 1/2 units, the unit taken from v's binade), round to nearest
@@ -118,6 +128,19 @@ struct Codec<__nv_bfloat16> {
     static __device__ __forceinline__ void put2(__nv_bfloat16* p, __nv_bfloat16 a, __nv_bfloat16 b)
     {
         *(__nv_bfloat162*)p = __halves2bfloat162(a, b);
+    }
+    // stochastic rounding of a pair from one 32-bit random word m (its upper 16
+    // bits dither the first value, its lower 16 bits the second), as sr does for
+    // one value, and the stored values back in FP32: integer operations only
+    static __device__ __forceinline__ __nv_bfloat162 sr2(float2 v, uint32_t m, float2& back)
+    {
+        const uint32_t a = __float_as_uint(v.x) + (m >> 16);
+        const uint32_t b = __float_as_uint(v.y) + (m & 0xFFFFu);
+        const uint32_t packed = __byte_perm(a, b, 0x7632);  // a's upper half low, b's upper half high
+        back = make_float2(__uint_as_float(packed << 16), __uint_as_float(packed & 0xFFFF0000u));
+        __nv_bfloat162 h;
+        *(uint32_t*)&h = packed;
+        return h;
     }
     static __device__ __forceinline__ __nv_bfloat16 rn(float v) { return __float2bfloat16_rn(v); }
     // stochastic rounding: BF16 is the upper half of the FP32 word, so adding

@@ -246,7 +246,8 @@ struct Dest {
 // exactly from m36 and the stored moving values), is rounded stochastically:
 // round-to-nearest of nearly equal bulk values would bias the mass of every
 // bulk node the same way, step after step. BF16 (8 significant bits) rounds
-// the moving values stochastically too. The random bits come from a hash of
+// the moving values stochastically too, a velocity's two values from the two
+// halves of one 32-bit random word. The random bits come from a hash of
 // the node and the lattice's step counter `clk`: fresh every step, and the
 // same again when a checkpoint is replayed.
 template <class S, bool kGeneral, bool kTauOne>
@@ -325,18 +326,14 @@ __device__ __forceinline__ void collide_store(const float (&rc)[2], const float 
                 if (!in_bounds(qo, slot, D.err)) continue;
             S* q = dst + 2 * (qo + (long long)(wall ? opp(kk) : kk) * slot);  // the pair of both components
             if constexpr (Codec<S>::kDeviation) {
-                S h0, h1;
-                if constexpr (Codec<S>::kDitherMoving) {
-                    h0 = Codec<S>::sr(s.x, rand16(hsh, kk));
-                    h1 = Codec<S>::sr(s.y, rand16(hsh, Q + kk));
-                } else {
-                    h0 = Codec<S>::rn(s.x);
-                    h1 = Codec<S>::rn(s.y);
-                }
-                const float2 hv = f2(Codec<S>::val(h0), Codec<S>::val(h1));
+                // round both components' values into one pair; hv: the stored values in FP32
+                float2 hv;
+                typename Codec<S>::Pair h;
+                if constexpr (Codec<S>::kDitherMoving) h = Codec<S>::sr2(s, rand32(hsh, kk), hv);
+                else h = Codec<S>::rn2(s, hv);
                 if (is_axis(kk)) sax = add2(sax, hv);
                 else sdi = add2(sdi, hv);
-                Codec<S>::put2(q, h0, h1);
+                *(typename Codec<S>::Pair*)q = h;
             } else {
                 sum = add2(sum, s);
                 Codec<S>::store2(q, s.x, s.y);
@@ -356,7 +353,12 @@ __device__ __forceinline__ void collide_store(const float (&rc)[2], const float 
         const float2 x0 = sub2(f2(m36[0], m36[1]), fma2(sp2(2.0f), sax, sdi));
         float2 s0 = mul2(x0, sp2(1.0f / 12.0f));
         s0 = fma2(fma2(sp2(-12.0f), s0, x0), sp2(1.0f / 12.0f), s0);
-        Codec<S>::put2(q0, Codec<S>::sr(s0.x, rand16(hrest, 0)), Codec<S>::sr(s0.y, rand16(hrest, 1)));
+        if constexpr (Codec<S>::kDitherMoving) {
+            float2 unused;
+            *(typename Codec<S>::Pair*)q0 = Codec<S>::sr2(s0, rand32(hrest, 0), unused);
+        } else {
+            Codec<S>::put2(q0, Codec<S>::sr(s0.x, rand16(hrest, 0)), Codec<S>::sr(s0.y, rand16(hrest, 1)));
+        }
     } else {
         const float2 r0 = sub2(R, sum);
         Codec<S>::store2(q0, r0.x, r0.y);
