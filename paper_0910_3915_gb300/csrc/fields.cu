@@ -5,6 +5,8 @@
 // warp shuffles and a final pass over the per-block partials in block order.
 #include "lb_fields.cuh"
 
+#include <type_traits>
+
 namespace lbsc {
 
 __device__ __forceinline__ double warp_sum(double v)
@@ -387,36 +389,73 @@ __global__ void __launch_bounds__(kRedThreads) angle_kernel(FieldArgs F, Scratch
     const bool lexact = (double)lf == level;
     const float* __restrict__ P = W.rho[0];
     const unsigned nxy = (unsigned)nx * (unsigned)ny;
+    // Interface crossings are rare and scattered: a lane that meets one would
+    // run the FP64 work of add_crossing alone, at the cost of a whole warp's.
+    // So the warp queues its crossings in shared memory, in lane order, and
+    // works through them 32 at a time with every lane busy; which lane sums
+    // which crossing depends only on the data, so the sums are reproducible.
+    __shared__ int4 qpos[kRedThreads / 32][64];     // (x, y, z, axis)
+    __shared__ float2 qphi[kRedThreads / 32][64];   // (phi at the node, phi at the neighbour)
+    const int lane = tid & 31, warp = tid >> 5;
+    int queued = 0;
+    auto drain = [&](int n) {  // lanes < n take a queued crossing each, then the queue shifts by n
+        __syncwarp();
+        if (lane < n) {
+            const int4 q = qpos[warp][lane];
+            const float2 f = qphi[warp][lane];
+            const bool s0 = above(f.x, lf, lexact, level);
+            add_crossing(&sacc[0][tid], kRedThreads, q.x, q.y, q.z, q.w, f.x, f.y, level, s0, zref);
+        }
+        __syncwarp();
+        if (lane + n < queued) {  // at most 31 left, read from [n, queued), written to [0, queued - n)
+            const int4 q = qpos[warp][lane + n];
+            const float2 f = qphi[warp][lane + n];
+            qpos[warp][lane] = q;
+            qphi[warp][lane] = f;
+        }
+        __syncwarp();
+        queued -= n;
+    };
     // a warp takes lattice rows (y, z) = w, w + W, ... (W warps in the grid), its lanes x = lane, lane + 32, ...
     const int rows = ny * nz, nwarps = gridDim.x * (kRedThreads / 32);
-    for (int r = blockIdx.x * (kRedThreads / 32) + (tid >> 5); r < rows; r += nwarps)
-    for (int x = tid & 31; x < nx; x += 32) {
+    for (int r = blockIdx.x * (kRedThreads / 32) + warp; r < rows; r += nwarps)
+    for (int xb = 0; xb < nx; xb += 32) {  // warp-uniform: the queue needs the whole warp
+        const int x = xb + lane;
+        const bool in = x < nx;
         const int z = r / ny, y = r - z * ny;
-        const unsigned i = (unsigned)r * (unsigned)nx + (unsigned)x;
+        const unsigned i = (unsigned)r * (unsigned)nx + (unsigned)(in ? x : nx - 1);
         // the node and its +x, +y, +z neighbours (the node itself past an edge), loaded together
         const float p0 = P[i];
-        const float pn[3] = {P[x + 1 < nx ? i + 1 : i], P[y + 1 < ny ? i + nx : i], P[z + 1 < nz ? i + nxy : i]};
-        if (z == z0 && z0 + 1 < nz) {  // reference plane: every column, solid or not
+        const float pn[3] = {P[in && x + 1 < nx ? i + 1 : i], P[y + 1 < ny ? i + nx : i], P[z + 1 < nz ? i + nxy : i]};
+        if (in && z == z0 && z0 + 1 < nz) {  // reference plane: every column, solid or not
             const unsigned i1 = x + 1 < nx ? i + 1 : i - x;
             ACC(1) += plane_length(p0, pn[2], P[i1], P[i1 + nxy], fz, level);
         }
-        if (!F.general ? (z == 0 || z == nz - 1) : (F.nbmask[F.L.off(x, y, z)] & kSelfSolid) != 0) continue;
-        pmax = fmaxf(pmax, p0);
-        pmin = fminf(pmin, p0);
+        const bool fluid = in && (!F.general ? !(z == 0 || z == nz - 1) : (F.nbmask[F.L.off(x, y, z)] & kSelfSolid) == 0);
+        if (fluid) {
+            pmax = fmaxf(pmax, p0);
+            pmin = fminf(pmin, p0);
+        }
         const bool s0 = above(p0, lf, lexact, level);
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
             const int x1 = x + (d == 0), y1 = y + (d == 1), z1 = z + (d == 2);
-            if (x1 >= nx || y1 >= ny || z1 >= nz) continue;
-            if (F.general ? (F.nbmask[F.L.off(x1, y1, z1)] & kSelfSolid) != 0 : z1 == nz - 1) continue;
-            const float p1 = pn[d];
-            if (s0 == above(p1, lf, lexact, level)) continue;
-            add_crossing(&sacc[0][tid], kRedThreads, x, y, z, d, p0, p1, level, s0, zref);
+            bool cross = fluid && x1 < nx && y1 < ny && z1 < nz;
+            if (cross) cross = !(F.general ? (F.nbmask[F.L.off(x1, y1, z1)] & kSelfSolid) != 0 : z1 == nz - 1);
+            if (cross) cross = s0 != above(pn[d], lf, lexact, level);
+            const unsigned m = __ballot_sync(0xffffffffu, cross);
+            if (cross) {
+                const int at = queued + __popc(m & ((1u << lane) - 1u));
+                qpos[warp][at] = make_int4(x, y, z, d);
+                qphi[warp][at] = make_float2(p0, pn[d]);
+            }
+            queued += __popc(m);
+            if (queued >= 32) drain(32);
         }
     }
+    if (queued > 0) drain(queued);
     // block reduction: FP32 maxima by shuffles; FP64 values only in warps that hold some
     __shared__ double sh[kRedThreads / 32][kAngleVals];
-    const int lane = tid & 31, warp = tid >> 5;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         pmax = fmaxf(pmax, __shfl_down_sync(0xffffffffu, pmax, o));
@@ -588,15 +627,17 @@ __global__ void __launch_bounds__(kRedThreads) pressure_radial_kernel(FieldArgs 
 // Refresh the ghost rows y = -1 and y = ny of planes [z0, z0 + nzp) from
 // rows ny-1 and 0 (x = 0 .. nx-1; the TMA-staged step reads them as the
 // periodic images in y, and takes its x images from strips of real columns).
-template <class S>
-__global__ void ghost_rows_kernel(Layout L, S* __restrict__ f, int z0, int nzp)
+// One thread per (velocity, plane, x) copies the node's pair of values (both
+// components: P is the raw type of a pair) in both ghost rows.
+template <class P>
+__global__ void ghost_rows_kernel(Layout L, P* __restrict__ f, int z0, int nzp)
 {
-    const int n = 2 * Q * nzp * L.nx;
+    const int n = Q * nzp * L.nx;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const int x = i % L.nx, t = i / L.nx;
-        const int z = z0 + t % nzp, ak = t / nzp;
-        S* p = f + L.at(ak / Q, ak % Q, (long long)z * L.plane + L.gx + x);  // row y = -1
-        const long long row = 2 * (long long)L.px;                         // one row, in elements
+        const int z = z0 + t % nzp, k = t / nzp;
+        P* p = f + (long long)k * L.slot + (long long)z * L.plane + L.gx + x;  // row y = -1, in pairs
+        const long long row = L.px;
         p[0] = p[(long long)L.ny * row];          // y = -1  <- y = ny-1
         p[(long long)(L.ny + 1) * row] = p[row];  // y = ny  <- y = 0
     }
@@ -607,8 +648,9 @@ cudaError_t launch_ghosts(const Layout& L, S* f, int z0, int z1, cudaStream_t st
 {
     if (z1 <= z0) return cudaSuccess;
     const int nzp = z1 - z0;
-    const long long n = (long long)2 * Q * nzp * L.nx;
-    ghost_rows_kernel<S><<<grid_for(n, 256, 8192), 256, 0, st>>>(L, f, z0, nzp);
+    const long long n = (long long)Q * nzp * L.nx;
+    using P = typename std::conditional<sizeof(S) == 4, uint2, uint32_t>::type;
+    ghost_rows_kernel<P><<<grid_for(n, 256, 8192), 256, 0, st>>>(L, (P*)f, z0, nzp);
     return cudaGetLastError();
 }
 

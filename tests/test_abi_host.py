@@ -152,3 +152,44 @@ def test_huang_theta_hand_worked_values(lib):
                             rel_tol=1e-12, abs_tol=1e-15)
         th = lbsc.huang_theta(e["eta_wall_r"], e["eta_wall_b"], e["rho_in"], e["rho_out"])
         assert math.isclose(th, e["theta_deg"], rel_tol=0, abs_tol=1e-9), e
+
+
+def test_reset_and_slab_argument_errors_before_cuda(lib):
+    """lb_reset and the z-slab entry points reject bad arguments before any CUDA call."""
+    from paper_0910_3915_gb300 import lbsc
+    ctx = ctypes.c_void_p()
+    rr = np.ones(2 * 2 * 4)
+    dp = rr.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    assert lib.lb_reset(None, dp, dp) == lbsc.LB_ERR_ARG
+    # halo flags beyond LB_HALO_BELOW | LB_HALO_ABOVE, a slab without an owned plane, a negative base
+    assert lib.lb_init_slab(ctypes.byref(ctx), 2, 2, 4, lbsc.LB_F32, dp, dp, None, 4, 0, None) == lbsc.LB_ERR_ARG
+    assert lib.lb_init_slab(ctypes.byref(ctx), 2, 2, 2, lbsc.LB_F32, dp, dp, None, 1, 0, None) == lbsc.LB_ERR_ARG
+    assert lib.lb_init_slab(ctypes.byref(ctx), 2, 2, 4, lbsc.LB_F32, dp, dp, None, 1, -1, None) == lbsc.LB_ERR_ARG
+    bad_ref = np.array([np.nan, 0.1])
+    assert lib.lb_init_slab(ctypes.byref(ctx), 2, 2, 4, lbsc.LB_BF16, dp, dp, None, 1, 0,
+                            bad_ref.ctypes.data_as(ctypes.POINTER(ctypes.c_double))) == lbsc.LB_ERR_ARG
+    assert ctx.value is None
+    assert lib.lb_halo_exchange(None, None) == lbsc.LB_ERR_ARG
+    assert lib.lb_halo_pack(None, 0, None) == lbsc.LB_ERR_ARG
+    assert lib.lb_halo_unpack(None, 1, None) == lbsc.LB_ERR_ARG
+    assert lib.lb_slabs_step(None, 0, 1) == lbsc.LB_ERR_ARG
+    nb = ctypes.c_size_t()
+    assert lib.lb_halo_bytes(None, ctypes.byref(nb)) == lbsc.LB_ERR_ARG
+
+
+def test_slab_split_covers_the_fluid_planes():
+    """slabs.split: even, contiguous, every fluid plane owned exactly once, at
+    least one plane a slab; halo flags on the inner faces only."""
+    from paper_0910_3915_gb300 import lbsc, slabs
+    for nz, n in ((128, 2), (37, 3), (19, 17), (5, 3)):
+        b = slabs.split(nz, n)
+        assert b[0][0] == 1 and b[-1][1] == nz - 1
+        assert all(b[i][1] == b[i + 1][0] for i in range(n - 1))
+        sizes = [z1 - z0 for z0, z1 in b]
+        assert min(sizes) >= 1 and max(sizes) - min(sizes) <= 1
+        flags = [slabs.halo_flags(i, n) for i in range(n)]
+        assert flags[0] == (lbsc.LB_HALO_ABOVE if n > 1 else 0)
+        assert flags[-1] == (lbsc.LB_HALO_BELOW if n > 1 else 0)
+        assert all(f == lbsc.LB_HALO_BELOW | lbsc.LB_HALO_ABOVE for f in flags[1:-1])
+    with pytest.raises(ValueError):
+        slabs.split(5, 4)

@@ -147,3 +147,43 @@ def test_distributed_slabs_host_staged_two_processes(lbsc):
     assert np.array_equal(got, n_whole[:, :, 1:-1])
     assert np.array_equal(res[0][0], res[1][0])
     assert np.allclose(res[0][0][:2], m_whole[3][:2], rtol=1e-12, atol=0)
+
+
+def test_single_slab_and_thin_slabs(lbsc):
+    """Degenerate splits: one slab (no halo planes: the whole lattice) and slabs
+    of a single owned plane each stay bitwise equal to the whole lattice."""
+    from paper_0910_3915_gb300.slabs import Slabs
+    nx, ny, nz, steps = 32, 20, 8, 25
+    rr, rb = W.droplet_fields(nx, ny, nz, 5.0, seed=14)
+    n_whole, _ = _whole(lbsc, rr, rb, steps)
+    for nslab in (1, nz - 2):
+        with Slabs(rr, rb, nslab).set_params(**CONTACT) as s:
+            s.step(steps)
+            assert np.array_equal(s.populations()[:, :, 1:-1], n_whole[:, :, 1:-1]), nslab
+
+
+def test_reset_restarts_bitwise_and_rejects_bad_densities(lbsc):
+    """lb_reset: a lattice restarted from its initial densities repeats its run
+    bit for bit (the step counter, which keys 16-bit rounding, restarts too); a
+    negative or non-finite density is rejected and a later reset still works."""
+    nx, ny, nz = 36, 28, 20
+    rr, rb = W.droplet_fields(nx, ny, nz, 6.0, seed=8)
+    for precision in ("f32", "bf16"):
+        lat = lbsc.Lattice(rr, rb, precision).set_params(**CONTACT)
+        lat.step(30)
+        first = lat.populations()
+        lat.reset(rr, rb)
+        assert lat.conservation()[7] == 0
+        lat.step(30)
+        assert np.array_equal(lat.populations(), first)
+        bad = rr.copy()
+        bad[3, 4, 5] = -0.1
+        with pytest.raises(lbsc.LBError) as e:
+            lat.reset(bad, rb)
+        assert e.value.code == lbsc.LB_ERR_ARG
+        bad[3, 4, 5] = np.nan
+        with pytest.raises(lbsc.LBError):
+            lat.reset(rr, bad)
+        lat.reset(rr, rb).step(30)
+        assert np.array_equal(lat.populations(), first)
+        lat.close()
