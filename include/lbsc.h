@@ -140,7 +140,9 @@ int lb_reset(lb_ctx* ctx, const double* rho_r, const double* rho_b);
  * the neighbour's halo plane takes; then the slabs' owned planes hold exactly
  * what the whole lattice holds (bitwise: each node's arithmetic is the same).
  * Stepping a slab further without the exchange leaves its boundary planes
- * stale. Slabs always use the load-from-global step kernel and planar walls. */
+ * stale. A slab with neighbours on both faces owns at least two planes (the
+ * plane it sends must be final after its own step). Slabs always use the
+ * load-from-global step kernel and planar walls. */
 #define LB_HALO_BELOW 1 /* plane 0 is a halo plane (a neighbour below) */
 #define LB_HALO_ABOVE 2 /* plane nz-1 is a halo plane (a neighbour above) */
 

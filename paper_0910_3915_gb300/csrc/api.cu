@@ -531,6 +531,10 @@ int lb_init_slab(lb_ctx** out, int nx, int ny, int nz, int precision, const doub
     if (halo < 0 || halo > (LB_HALO_BELOW | LB_HALO_ABOVE))
         return fail(nullptr, LB_ERR_ARG, "lb_init_slab: halo must be a combination of LB_HALO_BELOW and LB_HALO_ABOVE");
     if (nz < 3 || zbase < 0) return fail(nullptr, LB_ERR_ARG, "lb_init_slab: a slab needs nz >= 3 and zbase >= 0");
+    // the boundary plane a slab sends must be final after its own step: with neighbours on both faces, a
+    // single owned plane would receive its crossing populations from one face only after sending to the other
+    if (halo == (LB_HALO_BELOW | LB_HALO_ABOVE) && nz < 4)
+        return fail(nullptr, LB_ERR_ARG, "lb_init_slab: a slab with neighbours on both faces needs two owned planes");
     if (ref && !(std::isfinite(ref[0]) && std::isfinite(ref[1])))
         return fail(nullptr, LB_ERR_ARG, "lb_init_slab: reference densities must be finite");
     return init_common(out, nx, ny, nz, precision, rho_r, rho_b, cuda_stream, nullptr, 0, halo, zbase, ref);

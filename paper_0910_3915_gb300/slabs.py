@@ -35,10 +35,13 @@ ENTRIES = 38                  # 2 x 5 crossing + 2 x 14 boundary-plane values pe
 
 
 def split(nz: int, nslab: int):
-    """Owned plane ranges [z0, z1) of the whole lattice's fluid planes 1..nz-2, as even as possible."""
+    """Owned plane ranges [z0, z1) of the whole lattice's fluid planes 1..nz-2,
+    as even as possible. Every slab owns at least two planes when there are
+    more than one: a slab sends its boundary plane right after its own step, so
+    that plane's populations must all come from the slab itself (or the wall)."""
     nf = nz - 2
-    if nslab < 1 or nslab > nf:
-        raise ValueError("need 1 <= nslab <= nz - 2")
+    if nslab < 1 or (nslab > 1 and 2 * nslab > nf) or nslab > nf:
+        raise ValueError("need 1 <= nslab and at least two fluid planes per slab")
     return [(1 + i * nf // nslab, 1 + (i + 1) * nf // nslab) for i in range(nslab)]
 
 

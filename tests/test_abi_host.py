@@ -181,15 +181,17 @@ def test_slab_split_covers_the_fluid_planes():
     """slabs.split: even, contiguous, every fluid plane owned exactly once, at
     least one plane a slab; halo flags on the inner faces only."""
     from paper_0910_3915_gb300 import lbsc, slabs
-    for nz, n in ((128, 2), (37, 3), (19, 17), (5, 3)):
+    for nz, n in ((128, 2), (37, 3), (19, 8), (8, 3), (5, 1)):
         b = slabs.split(nz, n)
         assert b[0][0] == 1 and b[-1][1] == nz - 1
         assert all(b[i][1] == b[i + 1][0] for i in range(n - 1))
         sizes = [z1 - z0 for z0, z1 in b]
-        assert min(sizes) >= 1 and max(sizes) - min(sizes) <= 1
+        assert min(sizes) >= (2 if n > 1 else 1) and max(sizes) - min(sizes) <= 1
         flags = [slabs.halo_flags(i, n) for i in range(n)]
         assert flags[0] == (lbsc.LB_HALO_ABOVE if n > 1 else 0)
         assert flags[-1] == (lbsc.LB_HALO_BELOW if n > 1 else 0)
         assert all(f == lbsc.LB_HALO_BELOW | lbsc.LB_HALO_ABOVE for f in flags[1:-1])
     with pytest.raises(ValueError):
-        slabs.split(5, 4)
+        slabs.split(5, 2)  # three fluid planes: two slabs would leave one with a single plane
+    with pytest.raises(ValueError):
+        slabs.split(8, 4)

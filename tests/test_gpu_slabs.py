@@ -151,12 +151,16 @@ def test_distributed_slabs_host_staged_two_processes(lbsc):
 
 def test_single_slab_and_thin_slabs(lbsc):
     """Degenerate splits: one slab (no halo planes: the whole lattice) and slabs
-    of a single owned plane each stay bitwise equal to the whole lattice."""
+    of two owned planes each (the thinnest a slab with two neighbours may be)
+    stay bitwise equal to the whole lattice; a one-plane slab between two
+    neighbours is refused."""
     from paper_0910_3915_gb300.slabs import Slabs
     nx, ny, nz, steps = 32, 20, 8, 25
     rr, rb = W.droplet_fields(nx, ny, nz, 5.0, seed=14)
     n_whole, _ = _whole(lbsc, rr, rb, steps)
-    for nslab in (1, nz - 2):
+    with pytest.raises(lbsc.LBError):
+        lbsc.Lattice(rr[:3], rb[:3], slab=(lbsc.LB_HALO_BELOW | lbsc.LB_HALO_ABOVE, 2, None))
+    for nslab in (1, (nz - 2) // 2):
         with Slabs(rr, rb, nslab).set_params(**CONTACT) as s:
             s.step(steps)
             assert np.array_equal(s.populations()[:, :, 1:-1], n_whole[:, :, 1:-1]), nslab
