@@ -98,7 +98,7 @@ def peaks():
         return 6800.0, "fallback"
 
 
-STEP_SOURCES = ("step.cu", "step_common.cuh", "lb_internal.cuh", "step_tma.cuh")
+STEP_SOURCES = ("step.cu", "step_common.cuh", "lb_internal.cuh", "step_tma.cuh", "api.cu")  # api.cu: the layout
 
 
 def step_source_sha256() -> str:

@@ -162,8 +162,8 @@ struct Codec<__nv_bfloat16> {
 // both components of a velocity, and a warp's access to one slot covers 256
 // (128) contiguous bytes. Inside a slot, node (x, y, z) sits at
 //   o = z*plane + (y + 1)*px + (x + gx),
-// with gx = 128 bytes of row padding on the left (so x = 0 starts a 128-byte
-// line) and at least one node on the right, and one ghost row above and below
+// with gx = 256 bytes of row padding on the left (so x = 0 starts a 256-byte
+// unit) and at least one node on the right, and one ghost row above and below
 // each plane. Ghost row y = -1 mirrors y = ny-1 and y = ny mirrors y = 0, so a
 // tile plus its one-node ring is one box across the periodic y edges; the step
 // kernels write real nodes only, and a row copy refreshes the images where a

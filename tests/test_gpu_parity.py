@@ -433,8 +433,10 @@ def _oracle_node_update(n_t, solid, prm, z, y, x):
 # The benchmark's launch configurations: the schedules its tuner picks on a GB300
 # for these lattices (FP32: loads from global, 32x8 tiles, the 128 rows split
 # evenly into 19 tiles, 4 z segments; 16-bit: TMA-staged, one stage, 32x8 tiles,
-# 32 y-tiles, 4 z segments).
+# 32 y-tiles, 4 z segments), and the FP32 runner-up within 3 % of it (TMA-staged,
+# one stage, 32x4 tiles, 32 y-tiles, 4 z segments).
 BENCH_SCHEDULES = {"f32": "ldg:0:8:4:19", "f16": "tma:1:8:4", "bf16": "tma:1:8:4"}
+FP32_RUNNER_UP = "tma:1:4:4:32"
 
 
 @pytest.mark.parametrize("precision,dims,radius,tol", [
@@ -477,23 +479,23 @@ def test_full_size_sampled_nodes(lbsc, precision, dims, radius, tol):
 
 
 def test_full_size_100_steps_bench_schedule(lbsc):
-    """The headline kernel instance over many steps: the 128^3 droplet (R = 30)
-    under the benchmark's FP32 schedule, 100 steps, every node's density
-    against the oracle's within the 1e-5 bar."""
+    """The headline kernel instances over many steps: the 128^3 droplet (R = 30)
+    under the benchmark's FP32 schedule and its runner-up, 100 steps, every
+    node's density against the oracle's within the 1e-5 bar."""
     from paper_0910_3915_gb300 import tune
     nx = ny = nz = 128
     rr, rb = W.droplet_fields(nx, ny, nz, 30.0, seed=0)
     prm = dict(CONTACT, eta_wall_r=-0.05, eta_wall_b=0.05)
-    sched = BENCH_SCHEDULES["f32"]
-    lat = lbsc.Lattice(rr, rb).set_params(**prm)
-    tune.apply(lat, tune.parse(sched))
-    lat.step(100)
-    g = lat.moments()
-    lat.close()
     solid = W.wall_mask(nx, ny, nz)
     o = oracle.State(rr, rb, solid, oracle.Params(**prm)).step(100).moments()
-    err = rel_err(g, o, solid)
-    assert err <= 1e-5, f"schedule {sched}: {err}"
+    for sched in (BENCH_SCHEDULES["f32"], FP32_RUNNER_UP):
+        lat = lbsc.Lattice(rr, rb).set_params(**prm)
+        tune.apply(lat, tune.parse(sched))
+        lat.step(100)
+        g = lat.moments()
+        lat.close()
+        err = rel_err(g, o, solid)
+        assert err <= 1e-5, f"schedule {sched}: {err}"
 
 
 def test_bounded_wait_reports_timeout_and_context_survives(lbsc):
