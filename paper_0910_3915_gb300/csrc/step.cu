@@ -17,10 +17,10 @@
 namespace lbsc {
 
 // One work item: tile column `col` of the lattice A, fluid planes [za, zb).
-// sp: the CTA's psi ring, [4][2][TY+2][34] floats.
+// sp: the CTA's psi ring, [4][TY+2][34] pairs (psi^b, psi^r).
 template <class S, int TY, bool kGeneral, bool kTauOne>
 __device__ __forceinline__ void step_item(const StepArgs<S>& A, int col, int za, int zb,
-                                          float (&sp)[4][2][TY + 2][34], uint32_t clk)
+                                          float2 (&sp)[4][TY + 2][34], uint32_t clk)
 {
     constexpr int TX = 32, NT = TX * TY, HX = TX + 2, HY = TY + 2;
     constexpr int RING = 2 * HX + 2 * TY;          // ring nodes around the tile
@@ -112,7 +112,7 @@ __device__ __forceinline__ void step_item(const StepArgs<S>& A, int col, int za,
     };
     // reduce the raw registers of plane zp: psi into its ring slot, own moments out
     auto reduce = [&](int zp, float (&rho)[2], float (&j)[2][3], float (&v)[2][Q], float (&m)[2]) {
-        float* spl = &sp[zp & 3][0][0][0];
+        float2* spl = &sp[zp & 3][0][0];
         float ps[2] = {eta[0], eta[1]};
         rho[0] = rho[1] = m[0] = m[1] = 0.f;
 #pragma unroll
@@ -130,8 +130,7 @@ __device__ __forceinline__ void step_item(const StepArgs<S>& A, int col, int za,
             }
         }
         if (active) {
-            spl[(ty + 1) * HX + tx + 1] = ps[0];
-            spl[(HY + ty + 1) * HX + tx + 1] = ps[1];
+            spl[(ty + 1) * HX + tx + 1] = psi_pair(ps[0], ps[1]);
         }
 #pragma unroll
         for (int i = 0; i < NIT; ++i) {
@@ -139,7 +138,7 @@ __device__ __forceinline__ void step_item(const StepArgs<S>& A, int col, int za,
             const int a = it_a[i];
             // select, not index: a runtime index would put eta and ref in local memory
             const float eta_a = a ? eta[1] : eta[0], ref_a = a ? ref[1] : ref[0];
-            spl[a * HY * HX + it_sm[i]] = si_[i] ? eta_a : psi_of(rho_of<S>(ri_[i], ref_a));
+            *psi_lane(&spl[it_sm[i]], a) = si_[i] ? eta_a : psi_of(rho_of<S>(ri_[i], ref_a));
         }
     };
 
@@ -171,7 +170,7 @@ __device__ __forceinline__ void step_item(const StepArgs<S>& A, int col, int za,
         }
         if (valid && !self_solid) {
             float F[2][3];
-            sc_force<HX, HY>(&sp[(z - 1) & 3][0][0][0], &sp[z & 3][0][0][0], &sp[(z + 1) & 3][0][0][0], ty, tx,
+            sc_force<HX, HY>(&sp[(z - 1) & 3][0][0], &sp[z & 3][0][0], &sp[(z + 1) & 3][0][0], ty, tx,
                              gk, Gax, Gdi, F);
             if constexpr (kGeneral) {
                 D.zo[0] = wrapi(z - 1, nz) * plane;
@@ -210,7 +209,7 @@ constexpr int kMinCtas = !kTauOne ? 1 : (TY == 4 ? 3 : ((sizeof(S) == 4 && TY ==
 template <class S, int TY, bool kGeneral, bool kTauOne>
 __global__ void __launch_bounds__(32 * TY, (kMinCtas<S, TY, kTauOne>)) step_kernel(const StepArgs<S> A)
 {
-    __shared__ float sp[4][2][TY + 2][34];  // psi of 4 planes, slot = z & 3
+    __shared__ float2 sp[4][TY + 2][34];  // psi pairs of 4 planes, slot = z & 3
     const int ncol = A.tiles_x * A.tiles_y;
     const int nzf = A.zhi - A.zlo;
     uint32_t clk = 0;
@@ -233,7 +232,7 @@ __global__ void __launch_bounds__(32 * TY)
     batch_step_kernel(const StepArgs<S>* __restrict__ args, const int4* __restrict__ items, int nitems, int parity,
                       int nbox, uint32_t* done)
 {
-    __shared__ float sp[4][2][TY + 2][34];
+    __shared__ float2 sp[4][TY + 2][34];
     for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
         const int4 w = items[it];
         const StepArgs<S> A = args[2 * w.x + parity];

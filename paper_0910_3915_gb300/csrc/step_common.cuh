@@ -161,17 +161,17 @@ __device__ __forceinline__ float2 psi2_of(float2 rho)
 }
 
 // Eq. SCforce on the psi ring: s0, s1, s2 are the planes z-1, z, z+1 of a
-// [2][HY][HX] psi array, the node at row ty+1, column tx+1.
-// S^a = sum_k G_k psi^abar(x + c_k) c_k ;  F^a = -g kappa psi^a(x) S^a
-// Pairs hold (psi^b, psi^r) at each neighbour: lane a sums psi^abar.
+// [HY][HX] ring of pairs (psi^b, psi^r) (psi_pair), the node at row ty+1,
+// column tx+1. S^a = sum_k G_k psi^abar(x + c_k) c_k ;  F^a = -g kappa psi^a(x) S^a.
+// A neighbour's pair is one 8-byte shared-memory load, and its lanes are
+// already the other component's psi for each lane a of the force.
 template <int HX, int HY>
-__device__ __forceinline__ void sc_force(const float* s0, const float* s1, const float* s2, int ty, int tx, float gk,
-                                         float Gax, float Gdi, float (&F)[2][3])
+__device__ __forceinline__ void sc_force(const float2* s0, const float2* s1, const float2* s2, int ty, int tx,
+                                         float gk, float Gax, float Gdi, float (&F)[2][3])
 {
     auto psi_at = [&](int k) {
-        const float* sl = cz(k) < 0 ? s0 : (cz(k) > 0 ? s2 : s1);
-        const int o = (ty + 1 + cy(k)) * HX + tx + 1 + cx(k);
-        return f2(sl[HY * HX + o], sl[o]);
+        const float2* sl = cz(k) < 0 ? s0 : (cz(k) > 0 ? s2 : s1);
+        return sl[(ty + 1 + cy(k)) * HX + tx + 1 + cx(k)];
     };
     // opposite neighbours in pairs: psi(x + c_k) - psi(x - c_k), k odd
     float2 ax[3], di[3];
@@ -187,8 +187,8 @@ __device__ __forceinline__ void sc_force(const float* s0, const float* s1, const
             else acc_signed(di[q], hdi[q], dk, c);
         }
     }
-    const int o0 = (ty + 1) * HX + tx + 1;
-    const float2 pre = mul2(sp2(-gk), f2(s1[o0], s1[HY * HX + o0]));
+    const float2 own = s1[(ty + 1) * HX + tx + 1];
+    const float2 pre = mul2(sp2(-gk), f2(own.y, own.x));  // (psi^r, psi^b) of the node
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
         const float2 Fd = mul2(pre, fma2(sp2(Gax), ax[d], mul2(sp2(Gdi), di[d])));
@@ -196,6 +196,11 @@ __device__ __forceinline__ void sc_force(const float* s0, const float* s1, const
         F[1][d] = Fd.y;
     }
 }
+
+// The ring stores each node's pair as (psi^b, psi^r): the value of component a
+// sits in lane 1 - a.
+__device__ __forceinline__ float2 psi_pair(float psi_r, float psi_b) { return make_float2(psi_b, psi_r); }
+__device__ __forceinline__ float* psi_lane(float2* node, int a) { return (float*)node + (1 - a); }
 
 // Where the node's populations go: neighbours (wrapped), the planes of z-1,
 // z, z+1, and which links end on a wall.

@@ -116,7 +116,7 @@ __global__ void __launch_bounds__(32 * TY, (kTmaCtas<TY, kTauOne>)) step_tma_ker
     extern __shared__ unsigned char smem_raw[];
     unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
     S* stages = (S*)base;
-    float* sp = (float*)(base + (size_t)NS * G::STAGE_BYTES);  // psi ring [4][2][HY][HX]
+    float* sp = (float*)(base + (size_t)NS * G::STAGE_BYTES);  // psi ring [4][HY][HX] of pairs (psi^b, psi^r)
     uint64_t* bar = (uint64_t*)(sp + G::PSI_FLOATS);
 
     const Layout L = A.L;
@@ -216,7 +216,7 @@ __global__ void __launch_bounds__(32 * TY, (kTmaCtas<TY, kTauOne>)) step_tma_ker
             const int zp = za - 1 + i;
             const uint32_t gi = g + i;
             const bool ok = mbar_wait(&bar[gi % NS], (gi / NS) & 1u);
-            float* spl = sp + (zp & 3) * (2 * HY * HX);
+            float2* spl = (float2*)sp + (zp & 3) * (HY * HX);
             const bool solid = zp == 0 || zp == nz - 1;
             if (ok) {
                 const S* st = stages + (size_t)(gi % NS) * G::STAGE_ELEMS;
@@ -256,8 +256,7 @@ __global__ void __launch_bounds__(32 * TY, (kTmaCtas<TY, kTauOne>)) step_tma_ker
                     }
                 }
                 if (active) {
-                    spl[(ty + 1) * HX + tx + 1] = ps[0];
-                    spl[(HY + ty + 1) * HX + tx + 1] = ps[1];
+                    spl[(ty + 1) * HX + tx + 1] = psi_pair(ps[0], ps[1]);
                 }
 #pragma unroll
                 for (int q = 0; q < NIT; ++q) {
@@ -278,7 +277,7 @@ __global__ void __launch_bounds__(32 * TY, (kTmaCtas<TY, kTauOne>)) step_tma_ker
                         }
                         ps = psi_of(rho_of<S>(w, ref_a));
                     }
-                    spl[a * HY * HX + it_sm[q]] = ps;
+                    *psi_lane(&spl[it_sm[q]], a) = ps;
                 }
             }
             const bool bad = __syncthreads_or(!ok);
@@ -315,8 +314,9 @@ __global__ void __launch_bounds__(32 * TY, (kTmaCtas<TY, kTauOne>)) step_tma_ker
             }
             if (valid) {
                 float F[2][3];
-                sc_force<HX, HY>(sp + ((z - 1) & 3) * (2 * HY * HX), sp + (z & 3) * (2 * HY * HX),
-                                 sp + ((z + 1) & 3) * (2 * HY * HX), ty, tx, gk, Gax, Gdi, F);
+                const float2* ring = (const float2*)sp;
+                sc_force<HX, HY>(ring + ((z - 1) & 3) * (HY * HX), ring + (z & 3) * (HY * HX),
+                                 ring + ((z + 1) & 3) * (HY * HX), ty, tx, gk, Gax, Gdi, F);
                 D.zo[0] = (int)((z - 1) * plane);
                 D.zo[1] = (int)(z * plane);
                 D.zo[2] = (int)((z + 1) * plane);
