@@ -205,7 +205,11 @@ int lb_set_params(lb_ctx* ctx, const lb_params* params);
 
 /* Advance nsteps >= 0 time steps of Eq. LBeqs (moments, psi, Shan-Chen and
  * wall force, force-shifted cubic equilibrium, BGK, streaming with mid-grid
- * bounce-back) on the context's stream. Asynchronous. */
+ * bounce-back) on the context's stream. Asynchronous. The steps run as
+ * launches of CUDA graphs of 2^i steps (one per set bit of nsteps, and one
+ * per 32 steps); the first call after the schedule, the parameters or the
+ * geometry changed captures those graphs (on a private stream) before it
+ * launches. */
 int lb_step(lb_ctx* ctx, int nsteps);
 
 /* Wait for the stream and report a device-side failure, if any. */
