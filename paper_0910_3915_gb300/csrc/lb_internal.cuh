@@ -58,12 +58,12 @@ struct Codec<float> {
     static __device__ __forceinline__ void store2(float* p, float a, float b) { *(float2*)p = make_float2(a, b); }
 };
 // Random bits for stochastic rounding. A 32-bit hash per node and step (the
-// 32-bit finaliser of MurmurHash3 applied to a combined key); value j of the
-// node takes the upper half of h * M_j with the odd multiplier
+// 32-bit finaliser of MurmurHash3 applied to a combined key); the pair of
+// values of velocity j takes the 32-bit word h * M_j with the odd multiplier
 // M_j = 0x9E3779B1 (2j + 1). Multiplication by an odd number permutes the
-// 32-bit integers, so each value's bits are uniform when h is. The rest
-// value balances the node's mass against the rounded moving values, so when
-// those are dithered too its bits come from a second mixing round of h: bits
+// 32-bit integers, so each word is uniform when h is. The rest value
+// balances the node's mass against the rounded moving values, so when those
+// are dithered too its bits come from a second mixing round of h: bits
 // shared with the moving values would correlate with the fraction being
 // rounded and bias the mass.
 __device__ __forceinline__ uint32_t node_hash(uint32_t node, uint32_t key)
@@ -76,13 +76,29 @@ __device__ __forceinline__ uint32_t node_hash(uint32_t node, uint32_t key)
     h ^= h >> 16;
     return h;
 }
-__device__ __forceinline__ uint32_t rand16(uint32_t h, int j)
-{
-    return (h * (0x9E3779B1u * (2u * (uint32_t)j + 1u))) >> 16;
-}
-// 32 random bits for the pair of values of velocity j (both components): the
-// product h * M_j whole; its two halves dither the two values
+// 32 random bits for the pair of values of velocity j (both components)
 __device__ __forceinline__ uint32_t rand32(uint32_t h, int j) { return h * (0x9E3779B1u * (2u * (uint32_t)j + 1u)); }
+
+// Stochastic rounding of a pair of FP32 values into a 16-bit pair, in one
+// conversion instruction (cvt.rs, sm_100 and later): each value's magnitude
+// gets uniform random bits added below its last kept bit and is then
+// truncated, so it rounds up with probability equal to the discarded
+// fraction. The first value (stored in the low half) takes the low 16 bits
+// of m, the second (high half) the high 16 bits; BF16 uses all 16 of a
+// half, FP16 its low 13 (the 13 discarded bits of a normal FP16 value).
+// .satfinite clamps an overflow to the largest finite value.
+__device__ __forceinline__ uint32_t cvt_rs_bf16x2(float2 v, uint32_t m)
+{
+    uint32_t packed;
+    asm("cvt.rs.satfinite.bf16x2.f32 %0, %1, %2, %3;" : "=r"(packed) : "f"(v.y), "f"(v.x), "r"(m));
+    return packed;
+}
+__device__ __forceinline__ uint32_t cvt_rs_f16x2(float2 v, uint32_t m)
+{
+    uint32_t packed;
+    asm("cvt.rs.satfinite.f16x2.f32 %0, %1, %2, %3;" : "=r"(packed) : "f"(v.y), "f"(v.x), "r"(m));
+    return packed;
+}
 
 template <>
 struct Codec<__half> {
@@ -101,16 +117,17 @@ struct Codec<__half> {
         back = __half22float2(h);
         return h;
     }
-    static __device__ __forceinline__ __half rn(float v) { return __float2half_rn(v); }
-    // stochastic rounding: add a uniform dither of one unit in the last place
-    // (r16 / 2^16 - 1/2 units, the unit taken from v's binade), round to nearest
-    static __device__ __forceinline__ __half sr(float v, uint32_t r16)
+    // stochastic rounding of both values from one random word m (cvt_rs_f16x2),
+    // and the stored values back in FP32
+    static __device__ __forceinline__ __half2 sr2(float2 v, uint32_t m, float2& back)
     {
-        const int e = (__float_as_int(v) >> 23) & 0xff;
-        const int eu = e - 10 > 103 ? e - 10 : 103;  // FP16 subnormals: one unit is 2^-24
-        const float u = (float)r16 * (1.0f / 65536.0f) - 0.5f;
-        return __float2half_rn(fmaf(u, __int_as_float(eu << 23), v));
+        const uint32_t packed = cvt_rs_f16x2(v, m);
+        __half2 h;
+        *(uint32_t*)&h = packed;
+        back = __half22float2(h);
+        return h;
     }
+    static __device__ __forceinline__ __half rn(float v) { return __float2half_rn(v); }
     static __device__ __forceinline__ void store(__half* p, float v) { *p = __float2half_rn(v); }
 };
 template <>
@@ -129,29 +146,18 @@ struct Codec<__nv_bfloat16> {
     {
         *(__nv_bfloat162*)p = __halves2bfloat162(a, b);
     }
-    // stochastic rounding of a pair from one 32-bit random word m (its upper 16
-    // bits dither the first value, its lower 16 bits the second), as sr does for
-    // one value, and the stored values back in FP32: integer operations only
+    // stochastic rounding of both values from one random word m (cvt_rs_bf16x2),
+    // and the stored values back in FP32 (a BF16 value is the upper half of its
+    // FP32 word)
     static __device__ __forceinline__ __nv_bfloat162 sr2(float2 v, uint32_t m, float2& back)
     {
-        const uint32_t a = __float_as_uint(v.x) + (m >> 16);
-        const uint32_t b = __float_as_uint(v.y) + (m & 0xFFFFu);
-        const uint32_t packed = __byte_perm(a, b, 0x7632);  // a's upper half low, b's upper half high
+        const uint32_t packed = cvt_rs_bf16x2(v, m);
         back = make_float2(__uint_as_float(packed << 16), __uint_as_float(packed & 0xFFFF0000u));
         __nv_bfloat162 h;
         *(uint32_t*)&h = packed;
         return h;
     }
     static __device__ __forceinline__ __nv_bfloat16 rn(float v) { return __float2bfloat16_rn(v); }
-    // stochastic rounding: BF16 is the upper half of the FP32 word, so adding
-    // 16 uniform bits to the lower half and truncating rounds the magnitude up
-    // with probability equal to the discarded fraction
-    static __device__ __forceinline__ __nv_bfloat16 sr(float v, uint32_t r16)
-    {
-        __nv_bfloat16_raw raw;
-        raw.x = (unsigned short)((__float_as_uint(v) + r16) >> 16);
-        return __nv_bfloat16(raw);
-    }
     static __device__ __forceinline__ void store(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
 };
 

@@ -34,8 +34,10 @@ __device__ __forceinline__ void acc_signed(float2& acc, bool& has, float2 t, int
 
 // rho of one component from its 19 stored values v_k: FP32 stores n_k;
 // 16-bit formats store e_k with n_k = zeta_k (rho_ref + e_k). This routine
-// (for a tile's ring) and moments2 (for the tile's own nodes) perform the
-// same operations in the same order, so both see bit-identical rho.
+// (one component of a ring node, load-from-global kernel) and rho2_of (both
+// components in packed lanes: a ring node of the TMA kernel, and every
+// tile's own nodes through moments2) perform the same operations in the same
+// order, so every kernel sees bit-identical rho for a node.
 //
 // For 16-bit storage, m36 = 36 (rho - rho_ref) = 12 e_0 + 2 sum_axis e_k + sum_diag e_k
 // is also returned: the values are 16-bit numbers, so these FP32 sums are exact
@@ -57,6 +59,23 @@ __device__ __forceinline__ float rho_of(const float (&v)[Q], float ref, float* m
     }
 }
 
+// Both components' rho of one node from its 19 pairs of stored values, in
+// the packed lanes: the operations of rho_of in the same order, so each lane
+// is the bits rho_of gives for that component. m36 as in rho_of.
+template <class S>
+__device__ __forceinline__ float2 rho2_of(const float2 (&p)[Q], float2 ref, float2& m36)
+{
+    const float2 ax = add2(add2(add2(p[1], p[2]), add2(p[3], p[4])), add2(p[5], p[6]));
+    const float2 di = add2(add2(add2(add2(p[7], p[8]), add2(p[9], p[10])), add2(add2(p[11], p[12]), add2(p[13], p[14]))),
+                           add2(add2(p[15], p[16]), add2(p[17], p[18])));
+    if constexpr (Codec<S>::kDeviation) {
+        m36 = fma2(sp2(12.0f), p[0], fma2(sp2(2.0f), ax, di));
+        return fma2(m36, sp2(1.0f / 36.0f), ref);
+    } else {
+        return add2(add2(p[0], ax), di);
+    }
+}
+
 // Both components' rho (as rho_of), m36 (16-bit storage) and
 // j = sum_k n_k c_k, the latter from the differences of opposite pairs:
 // d = n_k - n_kbar (k odd), j = sum over pairs of c_k d.
@@ -67,16 +86,8 @@ __device__ __forceinline__ void moments2(const float (&v)[2][Q], const float (&r
     float2 p[Q];
 #pragma unroll
     for (int k = 0; k < Q; ++k) p[k] = f2(v[0][k], v[1][k]);
-    const float2 ax = add2(add2(add2(p[1], p[2]), add2(p[3], p[4])), add2(p[5], p[6]));
-    const float2 di = add2(add2(add2(add2(p[7], p[8]), add2(p[9], p[10])), add2(add2(p[11], p[12]), add2(p[13], p[14]))),
-                           add2(add2(p[15], p[16]), add2(p[17], p[18])));
-    float2 r, m = sp2(0.f);
-    if constexpr (Codec<S>::kDeviation) {
-        m = fma2(sp2(12.0f), p[0], fma2(sp2(2.0f), ax, di));
-        r = fma2(m, sp2(1.0f / 36.0f), f2(ref[0], ref[1]));
-    } else {
-        r = add2(add2(p[0], ax), di);
-    }
+    float2 m = sp2(0.f);
+    const float2 r = rho2_of<S>(p, f2(ref[0], ref[1]), m);
     rho[0] = r.x;
     rho[1] = r.y;
     m36[0] = m.x;
@@ -308,13 +319,17 @@ __device__ __forceinline__ void collide_store(const float (&rc)[2], const float 
             const float2 u0 = cx(k) ? u[0] : u[1];           // first nonzero component (+1)
             cuk = s1 > 0 ? add2(u0, u[d1]) : sub2(u0, u[d1]);
         }
+        // P(+-cu) = E +- O with the even part E = 4.5 cu^2 + B0 and the odd
+        // part O = cu (A0 + 4.5 cu^2), so the pair's equilibria in storage form
+        // are T +- U with T = w E + base and U = w O
+        const float2 w = is_axis(k) ? w1 : w2;
+        const float2 c2 = mul2(cuk, cuk);
+        const float2 T = fma2(w, fma2(sp2(4.5f), c2, B0), Codec<S>::kDeviation ? base : w);
+        const float2 U = mul2(w, mul2(cuk, fma2(sp2(4.5f), c2, A0)));
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const int kk = k + h;
-            const float2 cu = h ? neg2(cuk) : cuk;
-            const float2 P = fma2(cu, fma2(cu, fma2(sp2(4.5f), cu, sp2(4.5f)), A0), B0);
-            const float2 w = is_axis(kk) ? w1 : w2;
-            const float2 qk = fma2(w, P, Codec<S>::kDeviation ? base : w);  // equilibrium, storage form
+            const float2 qk = h ? sub2(T, U) : add2(T, U);  // equilibrium, storage form
             float2 s;
             if constexpr (kTauOne) {
                 s = qk;
@@ -358,12 +373,8 @@ __device__ __forceinline__ void collide_store(const float (&rc)[2], const float 
         const float2 x0 = sub2(f2(m36[0], m36[1]), fma2(sp2(2.0f), sax, sdi));
         float2 s0 = mul2(x0, sp2(1.0f / 12.0f));
         s0 = fma2(fma2(sp2(-12.0f), s0, x0), sp2(1.0f / 12.0f), s0);
-        if constexpr (Codec<S>::kDitherMoving) {
-            float2 unused;
-            *(typename Codec<S>::Pair*)q0 = Codec<S>::sr2(s0, rand32(hrest, 0), unused);
-        } else {
-            Codec<S>::put2(q0, Codec<S>::sr(s0.x, rand16(hrest, 0)), Codec<S>::sr(s0.y, rand16(hrest, 1)));
-        }
+        float2 unused;
+        *(typename Codec<S>::Pair*)q0 = Codec<S>::sr2(s0, rand32(hrest, 0), unused);
     } else {
         const float2 r0 = sub2(R, sum);
         Codec<S>::store2(q0, r0.x, r0.y);

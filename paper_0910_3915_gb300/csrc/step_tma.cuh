@@ -94,20 +94,22 @@ struct TmaGeom {
     static constexpr size_t smem(int NS) { return 128 + (size_t)NS * STAGE_BYTES + PSI_FLOATS * 4 + NS * 8; }
 };
 
-// Resident CTAs per SM the registers are held to (tau = 1): three CTAs of
-// 8-row tiles, five of 4-row tiles; other variants take the compiler's choice.
-template <int TY, bool kTauOne>
-constexpr int kTmaCtas = !kTauOne ? 1 : (TY == 8 ? 3 : (TY == 4 ? 5 : 1));
+// Resident CTAs per SM the registers are held to (tau = 1): for 8-row tiles
+// three FP32 CTAs (shared memory admits no more) and four 16-bit CTAs (64
+// registers, a few words spilled: 32 warps per SM measured faster than 24);
+// five CTAs of 4-row tiles; other variants take the compiler's choice.
+template <class S, int TY, bool kTauOne>
+constexpr int kTmaCtas = !kTauOne ? 1 : (TY == 8 ? (sizeof(S) == 2 ? 4 : 3) : (TY == 4 ? 5 : 1));
 
 template <class S, int TY, int NS, bool kTauOne>
-__global__ void __launch_bounds__(32 * TY, (kTmaCtas<TY, kTauOne>)) step_tma_kernel(const __grid_constant__ CUtensorMap tmap,
+__global__ void __launch_bounds__(32 * TY, (kTmaCtas<S, TY, kTauOne>)) step_tma_kernel(const __grid_constant__ CUtensorMap tmap,
                                                            const __grid_constant__ CUtensorMap tstrip,
                                                            const StepArgs<S> A)
 {
     using G = TmaGeom<S, TY>;
     constexpr int TX = 32, NT = TX * TY, HX = G::HX, HY = G::HY, GX = G::GX, BX = G::BX, SX = G::SX;
     constexpr int RING = 2 * HX + 2 * TY;
-    constexpr int NIT = (2 * RING + NT - 1) / NT;
+    constexpr int NIT = (RING + NT - 1) / NT;
     static_assert(G::STAGE_BYTES % 128 == 0 && (G::MAIN_SPAN * sizeof(S)) % 128 == 0,
                   "stages and strips stay 128-byte aligned");
     static_assert((2 * BX * sizeof(S)) % 16 == 0 && (2 * SX * sizeof(S)) % 16 == 0, "box rows are whole 16-byte units");
@@ -164,32 +166,33 @@ __global__ void __launch_bounds__(32 * TY, (kTmaCtas<TY, kTauOne>)) step_tma_ker
         const bool own_strip = gx >= nx;
         const bool own_rd = active && gx - nx < SX;
 
-        // ring items: shared-memory position, stage position of slot 0 of the
-        // item's component, source (0 main box, 1 left strip, 2 right strip)
-        int it_sm[NIT], it_base[NIT], it_src[NIT], it_a[NIT];
+        // ring items (one per ring node, both components): shared-memory
+        // position, stage position of the node's slot-0 pair, source (0 main
+        // box, 1 left strip, 2 right strip)
+        int it_sm[NIT], it_base[NIT], it_src[NIT];
+        bool it_on[NIT];
 #pragma unroll
         for (int i = 0; i < NIT; ++i) {
-            const int it = tid + i * NT;
-            it_a[i] = -1;
-            if (it < 2 * RING) {
-                const int a = it >= RING, r = it - a * RING;
+            const int r = tid + i * NT;
+            it_on[i] = false;
+            if (r < RING) {
                 int ix, iy;
                 if (r < HX) { ix = r; iy = 0; }
                 else if (r < 2 * HX) { ix = r - HX; iy = hgt + 1; }
                 else if (r < 2 * HX + TY) { ix = 0; iy = r - 2 * HX + 1; }
                 else { ix = HX - 1; iy = r - 2 * HX - TY + 1; }
-                if (r < 2 * HX || iy <= hgt) it_a[i] = a;  // side columns: the tile's own rows only
+                it_on[i] = r < 2 * HX || iy <= hgt;  // side columns: the tile's own rows only
                 it_sm[i] = iy * HX + ix;
                 const int xr = x0 - 1 + ix;  // the ring node's x (unwrapped)
                 if (xr < 0) {
                     it_src[i] = 1;  // x = -1: the image of x = nx - 1
-                    it_base[i] = G::MAIN_SPAN + 2 * (iy * SX + ol) + a;
+                    it_base[i] = G::MAIN_SPAN + 2 * (iy * SX + ol);
                 } else if (xr >= nx && xr - nx < SX) {
                     it_src[i] = 2;  // x >= nx: the images of x - nx
-                    it_base[i] = G::MAIN_SPAN + G::STRIP_ELEMS + 2 * (iy * SX + xr - nx) + a;
+                    it_base[i] = G::MAIN_SPAN + G::STRIP_ELEMS + 2 * (iy * SX + xr - nx);
                 } else {
                     it_src[i] = 0;
-                    it_base[i] = 2 * (iy * BX + ix - 1 + GX) + a;
+                    it_base[i] = 2 * (iy * BX + ix - 1 + GX);
                 }
             }
         }
@@ -260,24 +263,23 @@ __global__ void __launch_bounds__(32 * TY, (kTmaCtas<TY, kTauOne>)) step_tma_ker
                 }
 #pragma unroll
                 for (int q = 0; q < NIT; ++q) {
-                    if (it_a[q] < 0) continue;
-                    const int a = it_a[q];
-                    // select, not index: a runtime index would put eta and ref in local memory
-                    const float ref_a = a ? ref[1] : ref[0];
-                    float ps = a ? eta[1] : eta[0];
+                    if (!it_on[q]) continue;
+                    float2 pr = f2(eta[0], eta[1]);
                     if (!solid) {
-                        float w[Q];
-                        const S* si = st + it_base[q];
+                        // both components of velocity k in one shared-memory load
+                        float2 w[Q];
+                        const P2* si = (const P2*)(st + it_base[q]);
                         if (it_src[q] == 0) {
 #pragma unroll
-                            for (int k = 0; k < Q; ++k) w[k] = Codec<S>::val(si[2 * k * HY * BX]);
+                            for (int k = 0; k < Q; ++k) w[k] = Codec<S>::val2(si[k * HY * BX]);
                         } else {
 #pragma unroll
-                            for (int k = 0; k < Q; ++k) w[k] = Codec<S>::val(si[2 * k * HY * SX]);
+                            for (int k = 0; k < Q; ++k) w[k] = Codec<S>::val2(si[k * HY * SX]);
                         }
-                        ps = psi_of(rho_of<S>(w, ref_a));
+                        float2 unused;
+                        pr = psi2_of(rho2_of<S>(w, f2(ref[0], ref[1]), unused));
                     }
-                    *psi_lane(&spl[it_sm[q]], a) = ps;
+                    spl[it_sm[q]] = psi_pair(pr.x, pr.y);
                 }
             }
             const bool bad = __syncthreads_or(!ok);

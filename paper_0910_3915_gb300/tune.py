@@ -17,7 +17,7 @@ from __future__ import annotations
 import json
 import os
 
-SEGMENTS = (1, 2, 4, 8, 16)
+SEGMENTS = (1, 2, 3, 4, 6, 7, 8, 12, 16)
 TMA_PAIRS = ((4, 1), (4, 2), (4, 3), (8, 1), (8, 2), (8, 3), (16, 1), (16, 2))  # (tile height, stages)
 LDG_TILES = (4, 8)
 LDG_CTAS_PER_SM = {4: 3, 8: 2}  # resident CTAs of the tau = 1 load-from-global kernel
