@@ -237,6 +237,20 @@ int lb_selftest_bounded_wait(lb_ctx* ctx, unsigned spin_limit);
  * (messages via lb_last_error(NULL)). */
 int lb_selftest_psi(const float* rho, int n, float* out);
 
+/* Self-test of the stochastic rounding of 16-bit storage (a design choice
+ * of this library, not of the paper: the values stored are rounded so that
+ * each rounds up with probability equal to its discarded fraction).
+ * precision: LB_F16 or LB_BF16. v: 2n host floats, pairs (v[2i], v[2i+1]) as
+ * the step stores a velocity's two components; m: n random words, one per
+ * pair. out: 3n host words, written with
+ *   out[i]        the stored pair as a 32-bit word (first value in the low half),
+ *   out[n + i]    the first stored value converted back to FP32, as bits,
+ *   out[2n + i]   the second, likewise (the values the mass balance uses).
+ * 1 <= n <= 2^24. Runs on the current device with temporary device memory
+ * (synchronous). LB_ERR_ARG for another precision, NULL arrays or n out of
+ * range, LB_ERR_CUDA on a CUDA error (messages via lb_last_error(NULL)). */
+int lb_selftest_round(int precision, const float* v, const unsigned* m, int n, unsigned* out);
+
 /* Read densities and conservation sums (Sec. 2, moments). Any output may be NULL.
  * rho_r, rho_b: nx*ny*nz doubles. u: 3*nx*ny*nz doubles (component-major),
  * the barycentric velocity (sum_a j^a + F/2)/sum_a rho^a with F the total

@@ -71,6 +71,9 @@ int batch_occupancy(int tile_y, bool tau_one);
 // bounded-wait self-test: a wait nothing satisfies, limit try_wait rounds
 cudaError_t launch_wait_probe(int* err, unsigned limit, cudaStream_t st);
 cudaError_t launch_psi_probe(const float* rho, int n, float* out, cudaStream_t st);
+// 16-bit rounding self-test (precision 1 = FP16, 2 = BF16)
+cudaError_t launch_round_probe(int precision, const float* v, const uint32_t* m, int n, uint32_t* out,
+                               cudaStream_t st);
 // set a lattice's device step counter to v (and its done-ticket to 0)
 cudaError_t launch_clock_set(uint32_t* clk, uint32_t v, cudaStream_t st);
 template <class S>

@@ -377,6 +377,32 @@ cudaError_t launch_psi_probe(const float* rho, int n, float* out, cudaStream_t s
     return cudaGetLastError();
 }
 
+// Self-test of the 16-bit stochastic rounding: out[i] = the stored pair
+// (as its 32-bit word) that Codec<S>::sr2 makes of (v[2i], v[2i+1]) with the
+// random word m[i]; out[n + i] and out[2n + i] = the FP32 values it reports
+// back for the mass balance, as bit patterns.
+template <class S>
+__global__ void round_probe_kernel(const float* __restrict__ v, const uint32_t* __restrict__ m, int n,
+                                   uint32_t* __restrict__ out)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        float2 back;
+        const typename Codec<S>::Pair h = Codec<S>::sr2(make_float2(v[2 * i], v[2 * i + 1]), m[i], back);
+        out[i] = *(const uint32_t*)&h;
+        out[n + i] = __float_as_uint(back.x);
+        out[2 * n + i] = __float_as_uint(back.y);
+    }
+}
+
+cudaError_t launch_round_probe(int precision, const float* v, const uint32_t* m, int n, uint32_t* out,
+                               cudaStream_t st)
+{
+    const int blocks = (n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024;
+    if (precision == 1) round_probe_kernel<__half><<<blocks < 1 ? 1 : blocks, 256, 0, st>>>(v, m, n, out);
+    else round_probe_kernel<__nv_bfloat16><<<blocks < 1 ? 1 : blocks, 256, 0, st>>>(v, m, n, out);
+    return cudaGetLastError();
+}
+
 #define LBSC_BATCH_INST(S)                                                                                     \
     template cudaError_t launch_batch_step<S>(const StepArgs<S>*, const int4*, int, int, int, bool, int, int, uint32_t*, \
                                               cudaStream_t);                                                 \

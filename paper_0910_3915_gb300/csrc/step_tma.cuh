@@ -159,6 +159,11 @@ __global__ void __launch_bounds__(32 * TY, (kTmaCtas<S, TY, kTauOne>)) step_tma_
         const int np = zb - za + 2;  // planes za-1 .. zb
         // x edges: the periodic images come from the strips (column of x = nx - 1 in the left strip)
         const bool left_edge = x0 == 0, right_edge = x0 + TX >= nx;
+        // the box's column of node x0: GX (16 bytes of ring columns on each
+        // side); an edge tile takes its outer ring column from a strip, so its
+        // box is shifted inward and reads no padding columns beyond the lattice
+        // (0 at the left edge, 2 GX at the right edge)
+        const int cofs = left_edge ? 0 : (right_edge ? 2 * GX : GX);
         const int sl = (L.gx + nx - 1) / SX * SX, ol = L.gx + nx - 1 - sl;
         // own node: the main box; lanes past x = nx - 1 of a ragged last tile
         // hold the periodic images x - nx from the right strip (the one at
@@ -192,7 +197,7 @@ __global__ void __launch_bounds__(32 * TY, (kTmaCtas<S, TY, kTauOne>)) step_tma_
                     it_base[i] = G::MAIN_SPAN + G::STRIP_ELEMS + 2 * (iy * SX + xr - nx);
                 } else {
                     it_src[i] = 0;
-                    it_base[i] = 2 * (iy * BX + ix - 1 + GX);
+                    it_base[i] = 2 * (iy * BX + ix - 1 + cofs);
                 }
             }
         }
@@ -207,7 +212,7 @@ __global__ void __launch_bounds__(32 * TY, (kTmaCtas<S, TY, kTauOne>)) step_tma_
                 mbar_expect_tx(b, G::MAIN_BYTES + (left_edge ? G::STRIP_BOX_BYTES : 0u) +
                                       (right_edge ? G::STRIP_BOX_BYTES : 0u));
                 // x coordinates count values (two per node): 16-byte aligned, as the copy requires
-                tma_load_4d(stg, &tmap, b, 2 * (x0 + L.gx - GX), y0, zp, 0);
+                tma_load_4d(stg, &tmap, b, 2 * (x0 + L.gx - cofs), y0, zp, 0);
                 if (left_edge) tma_load_4d(stg + G::MAIN_SPAN, &tstrip, b, 2 * sl, y0, zp, 0);
                 if (right_edge) tma_load_4d(stg + G::MAIN_SPAN + G::STRIP_ELEMS, &tstrip, b, 2 * L.gx, y0, zp, 0);
             }
@@ -231,7 +236,7 @@ __global__ void __launch_bounds__(32 * TY, (kTmaCtas<S, TY, kTauOne>)) step_tma_
                     float w[2][Q];
                     // both components of velocity k in one shared-memory load
                     if (!own_strip) {
-                        const P2* so = (const P2*)(st + 2 * ((ty + 1) * BX + tx + GX));
+                        const P2* so = (const P2*)(st + 2 * ((ty + 1) * BX + tx + cofs));
 #pragma unroll
                         for (int k = 0; k < Q; ++k) {
                             const float2 t = Codec<S>::val2(so[k * HY * BX]);

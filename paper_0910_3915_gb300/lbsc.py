@@ -96,6 +96,8 @@ SIGNATURES = [
     ("lb_sync", _I, [_VP]),
     ("lb_selftest_bounded_wait", _I, [_VP, ctypes.c_uint]),
     ("lb_selftest_psi", _I, [ctypes.POINTER(ctypes.c_float), _I, ctypes.POINTER(ctypes.c_float)]),
+    ("lb_selftest_round", _I, [_I, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_uint), _I,
+                               ctypes.POINTER(ctypes.c_uint)]),
     ("lb_moments", _I, [_VP, _DP, _DP, _DP, _DP]),
     ("lb_conservation", _I, [_VP, _DP]),
     ("lb_reset", _I, [_VP, _DP, _DP]),

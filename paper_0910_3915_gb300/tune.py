@@ -21,6 +21,9 @@ SEGMENTS = (1, 2, 3, 4, 6, 7, 8, 12, 16)
 TMA_PAIRS = ((4, 1), (4, 2), (4, 3), (8, 1), (8, 2), (8, 3), (16, 1), (16, 2))  # (tile height, stages)
 LDG_TILES = (4, 8)
 LDG_CTAS_PER_SM = {4: 3, 8: 2}  # resident CTAs of the tau = 1 load-from-global kernel
+# CTAs per SM whose whole waves the TMA kernel's even splits are sized for (one
+# stage; up to 5 resident 4-row CTAs, 3 FP32 and 4 16-bit 8-row CTAs)
+TMA_CTAS_PER_SM = {4: (3, 4, 5), 8: (2, 3, 4)}
 
 
 def even_splits(nx: int, ny: int, ty: int, ctas: int, segments=SEGMENTS, waves=(1, 2)):
@@ -48,6 +51,10 @@ def candidates(nz_fluid: int, precision: str, segments=SEGMENTS, nx: int = 0, ny
         if ty == 16 and precision == "f32":
             continue  # two FP32 stages of 18 rows exceed shared memory
         out += [("tma", ns, ty, s, 0) for s in segments if nz_fluid // s >= 4]
+        if ns == 1 and ty in TMA_CTAS_PER_SM and n_sm and nx and ny:
+            splits = {sp for c in TMA_CTAS_PER_SM[ty] for sp in even_splits(nx, ny, ty, n_sm * c, segments)}
+            out += [("tma", ns, ty, s, nty) for nty, s in sorted(splits)
+                    if nty != -(-ny // ty) and nz_fluid // s >= 4]
     for ty in LDG_TILES:
         out += [("ldg", 0, ty, s, 0) for s in segments if nz_fluid // s >= 4]
         if n_sm and nx and ny:
