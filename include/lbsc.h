@@ -52,7 +52,7 @@ extern "C" {
 #define LB_BF16 2  /* BF16 deviations, as above */
 
 /* step kernel variants (lb_set_step_variant) */
-#define LB_STEP_AUTO 0  /* the load-from-global kernel (measured the faster one on GB300) */
+#define LB_STEP_AUTO 0  /* the TMA kernel with one stage where it applies, else load-from-global */
 #define LB_STEP_LDG 1   /* every plane loaded from global memory by the compute threads */
 #define LB_STEP_TMA 2   /* planes staged into shared memory by TMA (planar walls only) */
 
@@ -363,11 +363,11 @@ int lb_set_tiling(lb_ctx* ctx, int tile_y, int y_tiles, int z_segments);
 
 /* Choose the step kernel: LB_STEP_AUTO, LB_STEP_LDG or LB_STEP_TMA, and for
  * the TMA kernel the number of shared-memory stages, i.e. planes in flight
- * (1, 2 or 3; 0 = automatic: 3, else 2). One stage leaves room for more
- * resident CTAs per SM.
- * Every variant computes bit-identical results. LB_STEP_TMA with a
- * non-planar geometry, or a (tile height, stages) pair that is not built for
- * the precision, falls back to LB_STEP_LDG. */
+ * (1, 2 or 3; 0 = automatic: 1 for LB_STEP_AUTO, else 3, else 2). One stage
+ * leaves room for more resident CTAs per SM (measured the fastest on GB300).
+ * Every variant computes bit-identical results. LB_STEP_AUTO and LB_STEP_TMA
+ * with a non-planar geometry, a z slab, or a (tile height, stages) pair that
+ * is not built for the precision, fall back to LB_STEP_LDG. */
 int lb_set_step_variant(lb_ctx* ctx, int variant, int stages);
 
 /* ------------------------------------------------------------ adjoint

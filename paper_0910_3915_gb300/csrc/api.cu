@@ -47,11 +47,10 @@ struct lb_ctx {
     static constexpr int kGraphLevels = 6;
     cudaGraphExec_t graph[2][kGraphLevels] = {};
     int variant = LB_STEP_AUTO, stages = 0;  // step kernel selection
-    CUtensorMap tmap[2][3][2];               // per buffer, per tile height 4/8/16: main box, x-edge strip
+    CUtensorMap tmap[2][3][4];               // per buffer, per tile height 4/8/16: main box, x strip, y row, corner
     bool tmap_ok[2][3] = {{false, false, false}, {false, false, false}};
     int* dev_err = nullptr;                  // device status word of the step kernels
     uint32_t* clock = nullptr;               // device step counter {steps mod 2^32, done-ticket}
-    bool ghost_ok = true;                    // ghost images of the current buffer are current
     int halo = 0;                            // z slab: bit 0 plane 0, bit 1 plane nz-1 is a halo plane
     uint32_t hkey = 0;                       // z slab: its planes' offset in the whole lattice (dither key)
     static constexpr int kGraphSteps = 32;
@@ -86,7 +85,7 @@ static size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
 // rows of nx nodes behind 256 bytes of left padding (x = 0 starts a 256-byte
 // unit), at least one node of padding on the right, pitch a multiple of 256
-// bytes; one ghost row above and below each plane. A warp's paired FP32 access
+// bytes; one spare row above and below each plane. A warp's paired FP32 access
 // to one slot is 256 bytes: aligned to 256 bytes the load-from-global step
 // measured 121.2 against 126.1 us at 128^3 (128-byte alignment)
 static Layout make_layout(int nx, int ny, int nz, int prec)
@@ -225,9 +224,11 @@ static cudaError_t tma_prepare(lb_ctx* c)
 // stages used by the TMA kernel for the current schedule, 0 if not available
 static int tma_stages(lb_ctx* c)
 {
-    // AUTO: load-from-global (measured faster); z slabs always load from global
-    if (c->general || c->halo || c->variant != LB_STEP_TMA) return 0;
-    const int want[2] = {c->stages ? c->stages : 3, c->stages ? c->stages : 2};
+    // general geometry and z slabs always load from global; AUTO takes the
+    // TMA kernel with one stage (measured the faster one for both precisions)
+    if (c->general || c->halo || c->variant == LB_STEP_LDG) return 0;
+    const int s0 = c->variant == LB_STEP_AUTO ? 1 : 3, s1 = c->variant == LB_STEP_AUTO ? 1 : 2;
+    const int want[2] = {c->stages ? c->stages : s0, c->stages ? c->stages : s1};
     for (int ns : want) {
         // occupancy 0: the pair is not built for this precision (or does not fit)
         const long long occ = tma_call(2, c, c->tile_y, ns);
@@ -254,10 +255,12 @@ static EncodeTiledFn encode_fn()
     return fn;
 }
 
-// 4-D maps over a population buffer: (x incl. padding, two values per node;
-// y incl. ghost rows; z; k); main box = the 32-node tile plus 16 bytes of
-// columns on each side, TY + 2 rows, one plane, all 19 slots; strip box = 16
-// bytes of columns (the x-edge images)
+// 4-D maps over a population buffer, ordered (x incl. padding, two values per
+// node; storage row, spare rows included; plane; slot k). Boxes: main = the
+// 32-node tile plus 16 bytes of columns on each side, TY + 2 rows; x strip =
+// 16 bytes of columns, TY + 2 rows; y row = the main box's columns, one row;
+// corner = 16 bytes of columns, one row. Every box spans one plane and all 19
+// slots.
 static int tensor_map(lb_ctx* c, int buf, int ty)
 {
     const int ti = tile_index(ty);
@@ -269,18 +272,18 @@ static int tensor_map(lb_ctx* c, int buf, int ty)
     const cuuint64_t dims[4] = {(cuuint64_t)(2 * L.px), (cuuint64_t)(L.ny + 2), (cuuint64_t)L.nz, (cuuint64_t)Q};
     const cuuint64_t strides[3] = {(cuuint64_t)(2 * L.px) * es, (cuuint64_t)(2 * L.plane) * es,
                                    (cuuint64_t)(2 * L.slot) * es};
-    // main box: the tile plus 16 bytes of columns on each side; strip: 16 bytes of columns (x edges).
     // No L2 promotion: fetching whole 256-byte blocks around the boxes' 16-byte edges raised the
     // step's DRAM reads by a tenth (neighbouring tiles did not reuse the rest in time)
     const cuuint32_t gxv = (cuuint32_t)(16 / es);  // values in 16 bytes
-    const cuuint32_t box[4] = {(cuuint32_t)(2 * 32) + 2 * gxv, (cuuint32_t)(ty + 2), 1, (cuuint32_t)Q};
-    const cuuint32_t sbox[4] = {gxv, (cuuint32_t)(ty + 2), 1, (cuuint32_t)Q};
+    const cuuint32_t wide = (cuuint32_t)(2 * 32) + 2 * gxv, rows = (cuuint32_t)(ty + 2);
+    const cuuint32_t boxes[4][4] = {{wide, rows, 1, (cuuint32_t)Q}, {gxv, rows, 1, (cuuint32_t)Q},
+                                    {wide, 1, 1, (cuuint32_t)Q}, {gxv, 1, 1, (cuuint32_t)Q}};
     const cuuint32_t estr[4] = {1, 1, 1, 1};
     const CUtensorMapDataType dt = c->prec == LB_F32   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
                                    : c->prec == LB_F16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
                                                        : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
-    for (int kind = 0; kind < 2; ++kind) {
-        const CUresult r = enc(&c->tmap[buf][ti][kind], dt, 4, c->f[buf], dims, strides, kind ? sbox : box, estr,
+    for (int kind = 0; kind < 4; ++kind) {
+        const CUresult r = enc(&c->tmap[buf][ti][kind], dt, 4, c->f[buf], dims, strides, boxes[kind], estr,
                                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                                CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS) return fail(c, LB_ERR_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
@@ -310,31 +313,12 @@ static StepArgs<S> step_args(lb_ctx* c, int src)
     return A;
 }
 
-// the ghost rows of buffer `buf` (read by the TMA-staged step)
-template <class S>
-static cudaError_t refresh_ghosts(lb_ctx* c, int buf, cudaStream_t st)
-{
-    return launch_ghosts<S>(c->L, (S*)c->f[buf], c->zlo, c->zhi, st);
-}
-
-static cudaError_t refresh_ghosts_any(lb_ctx* c, int buf, cudaStream_t st)
-{
-    switch (c->prec) {
-    case LB_F32: return refresh_ghosts<float>(c, buf, st);
-    case LB_F16: return refresh_ghosts<__half>(c, buf, st);
-    default: return refresh_ghosts<__nv_bfloat16>(c, buf, st);
-    }
-}
-
-// one TMA-staged step, then the ghost rows of its output
+// one TMA-staged step
 template <class S>
 static cudaError_t launch_tma(lb_ctx* c, int parity, int ns, cudaStream_t st)
 {
     const StepArgs<S> A = step_args<S>(c, parity);
-    cudaError_t e =
-        (cudaError_t)tma_step<S>(0, c->tile_y, ns, tau_one(c), c->tmap[parity][tile_index(c->tile_y)], &A, st);
-    if (e != cudaSuccess) return e;
-    return refresh_ghosts<S>(c, 1 - parity, st);
+    return (cudaError_t)tma_step<S>(0, c->tile_y, ns, tau_one(c), c->tmap[parity][tile_index(c->tile_y)], &A, st);
 }
 
 static cudaError_t launch_steps(lb_ctx* c, int n, int& parity, cudaStream_t st)
@@ -629,7 +613,6 @@ int lb_reset(lb_ctx* c, const double* rho_r, const double* rho_b)
     LB_CUDA(c, cudaStreamSynchronize(c->stream));
     c->cur = 0;
     c->steps = 0;
-    c->ghost_ok = true;  // the initial populations fill the ghost images
     int h = 0;
     LB_CUDA(c, cudaMemcpy(&h, c->dev_err, sizeof(int), cudaMemcpyDeviceToHost));
     if (h & kErrInput) {
@@ -771,10 +754,6 @@ int lb_step(lb_ctx* c, int nsteps)
     if (!c || nsteps < 0) return fail(c, LB_ERR_ARG, "lb_step: bad argument");
     if (nsteps == 0) return LB_OK;
     const int ns = tma_stages(c);
-    if (ns && !c->ghost_ok) {  // the TMA path reads the source's ghost images
-        LB_CUDA(c, refresh_ghosts_any(c, c->cur, c->stream));
-        c->ghost_ok = true;
-    }
     // n steps as graphs of 2^i steps: one launch per set bit (and per 32 steps),
     // so that consecutive kernels follow each other without host launch gaps
     const int rc = capture_graphs(c);
@@ -792,7 +771,6 @@ int lb_step(lb_ctx* c, int nsteps)
         }
     c->cur = par;
     c->steps += nsteps;
-    c->ghost_ok = ns != 0;  // only the TMA path leaves the images current
     return LB_OK;
 }
 
@@ -1042,7 +1020,6 @@ int lb_load(lb_ctx* c, const void* host, size_t bytes)
     LB_CUDA(c, launch_clock_set(c->clock, (uint32_t)h.steps, c->stream));
     LB_CUDA(c, cudaStreamSynchronize(c->stream));
     c->steps = h.steps;
-    c->ghost_ok = false;
     return LB_OK;
 }
 
@@ -1335,7 +1312,6 @@ int lb_batch_step(lb_batch* b, int nsteps)
     for (lb_ctx* c : b->box) {
         c->cur = b->cur;
         c->steps += nsteps;
-        if (nsteps > 0) c->ghost_ok = false;
     }
     return LB_OK;
 }

@@ -623,37 +623,6 @@ __global__ void __launch_bounds__(kRedThreads) pressure_radial_kernel(FieldArgs 
         if (sh[b]) atomicAdd(&out[b], sh[b]);
 }
 
-// ---------------------------------------------------------------- ghost rows
-// Refresh the ghost rows y = -1 and y = ny of planes [z0, z0 + nzp) from
-// rows ny-1 and 0 (x = 0 .. nx-1; the TMA-staged step reads them as the
-// periodic images in y, and takes its x images from strips of real columns).
-// One thread per (velocity, plane, x) copies the node's pair of values (both
-// components: P is the raw type of a pair) in both ghost rows.
-template <class P>
-__global__ void ghost_rows_kernel(Layout L, P* __restrict__ f, int z0, int nzp)
-{
-    const int n = Q * nzp * L.nx;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const int x = i % L.nx, t = i / L.nx;
-        const int z = z0 + t % nzp, k = t / nzp;
-        P* p = f + (long long)k * L.slot + (long long)z * L.plane + L.gx + x;  // row y = -1, in pairs
-        const long long row = L.px;
-        p[0] = p[(long long)L.ny * row];          // y = -1  <- y = ny-1
-        p[(long long)(L.ny + 1) * row] = p[row];  // y = ny  <- y = 0
-    }
-}
-
-template <class S>
-cudaError_t launch_ghosts(const Layout& L, S* f, int z0, int z1, cudaStream_t st)
-{
-    if (z1 <= z0) return cudaSuccess;
-    const int nzp = z1 - z0;
-    const long long n = (long long)Q * nzp * L.nx;
-    using P = typename std::conditional<sizeof(S) == 4, uint2, uint32_t>::type;
-    ghost_rows_kernel<P><<<grid_for(n, 256, 8192), 256, 0, st>>>(L, (P*)f, z0, nzp);
-    return cudaGetLastError();
-}
-
 // ---------------------------------------------------------------- population copies
 template <class S>
 __global__ void get_pop_kernel(FieldArgs F, const S* __restrict__ f, double* __restrict__ out)
@@ -790,7 +759,6 @@ cudaError_t launch_pressure_radial(const FieldArgs& F, const void* f, int prec, 
     template cudaError_t launch_phi<S>(const FieldArgs&, const S*, const Scratch&, cudaStream_t);      \
     template cudaError_t launch_get_pop<S>(const FieldArgs&, const S*, double*, cudaStream_t);       \
     template cudaError_t launch_set_pop<S>(const FieldArgs&, S*, const double*, cudaStream_t);   \
-    template cudaError_t launch_ghosts<S>(const Layout&, S*, int, int, cudaStream_t);                 \
     template cudaError_t launch_pressure_field<S>(const FieldArgs&, const S*, const Scratch&, double*, cudaStream_t); \
     template cudaError_t launch_pressure_planes<S>(const FieldArgs&, const S*, const Scratch&, double*, cudaStream_t);
 LBSC_INST(float)

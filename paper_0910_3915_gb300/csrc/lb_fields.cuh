@@ -77,8 +77,6 @@ cudaError_t launch_round_probe(int precision, const float* v, const uint32_t* m,
 // set a lattice's device step counter to v (and its done-ticket to 0)
 cudaError_t launch_clock_set(uint32_t* clk, uint32_t v, cudaStream_t st);
 template <class S>
-cudaError_t launch_ghosts(const Layout& L, S* f, int z0, int z1, cudaStream_t st);
-template <class S>
 cudaError_t launch_init(const FieldArgs& F, S* f, const double* rr, const double* rb, cudaStream_t st,
                         int* err = nullptr);
 // FP64 conservation sums into out[0..7] through 64-bit fixed-point accumulators

@@ -1,5 +1,5 @@
 // Internal definitions of the lbsc CUDA library: the D3Q19 lattice, the
-// population storage codecs, the ghosted storage layout and the argument
+// population storage codecs, the padded storage layout and the argument
 // blocks of the kernels.
 #pragma once
 
@@ -169,14 +169,11 @@ struct Codec<__nv_bfloat16> {
 // (128) contiguous bytes. Inside a slot, node (x, y, z) sits at
 //   o = z*plane + (y + 1)*px + (x + gx),
 // with gx = 256 bytes of row padding on the left (so x = 0 starts a 256-byte
-// unit) and at least one node on the right, and one ghost row above and below
-// each plane. Ghost row y = -1 mirrors y = ny-1 and y = ny mirrors y = 0, so a
-// tile plus its one-node ring is one box across the periodic y edges; the step
-// kernels write real nodes only, and a row copy refreshes the images where a
-// reader needs them (the TMA-staged step, which takes the periodic x images
-// from strips of real columns instead). The initial populations also fill
-// ghost columns x = -1 and x = nx; nothing relies on them afterwards. px,
-// plane and slot count nodes.
+// unit) and at least one node on the right, and one spare row above and
+// below each plane. Nothing reads the padding or the spare rows: the step
+// kernels take the periodic images of edge nodes from the real nodes (the
+// TMA-staged step loads small extra boxes of real columns and rows for them).
+// px, plane and slot count nodes.
 struct Layout {
     int nx, ny, nz, px, gx;
     long long plane, slot;
@@ -188,74 +185,23 @@ struct Layout {
     __host__ __device__ __forceinline__ long long at(int a, int k, long long o) const { return 2 * ((long long)k * slot + o) + a; }
 };
 
-// Element accessor of one (component, velocity): node offset o -> p[2 o]
-// with p = f + L.at(a, k, 0).
-// Write the ghost images (only) of node (x, y) of the plane at zoff.
-template <class S>
-__device__ __forceinline__ void put_ghosts(S* __restrict__ p, const Layout& L, int x, int y, long long zoff, float v)
-{
-    const long long row = zoff + (long long)(y + 1) * L.px + L.gx;
-    const bool xl = x == L.nx - 1, xr = x == 0;
-    if (xl) Codec<S>::store(p + 2 * (row - 1), v);
-    if (xr) Codec<S>::store(p + 2 * (row + L.nx), v);
-    if (y == L.ny - 1) {
-        const long long g = zoff + L.gx;  // row y = -1
-        Codec<S>::store(p + 2 * (g + x), v);
-        if (xl) Codec<S>::store(p + 2 * (g - 1), v);
-        if (xr) Codec<S>::store(p + 2 * (g + L.nx), v);
-    }
-    if (y == 0) {
-        const long long g = zoff + (long long)(L.ny + 1) * L.px + L.gx;  // row y = ny
-        Codec<S>::store(p + 2 * (g + x), v);
-        if (xl) Codec<S>::store(p + 2 * (g - 1), v);
-        if (xr) Codec<S>::store(p + 2 * (g + L.nx), v);
-    }
-}
-
-// 1 if node (x, y) has a ghost image
-__host__ __device__ __forceinline__ bool has_ghost(const Layout& L, int x, int y)
-{
-    return x == 0 || x == L.nx - 1 || y == 0 || y == L.ny - 1;
-}
-
-// Store v for node (x, y) of the plane at zoff through the accessor p
-// (p = f + L.at(a, k, 0)), with the ghost images of edge nodes.
+// Store v for node (x, y) of the plane at zoff through the accessor of one
+// (component, velocity) p = f + L.at(a, k, 0).
 template <class S>
 __device__ __forceinline__ void put(S* __restrict__ p, const Layout& L, int x, int y, long long zoff, float v)
 {
     Codec<S>::store(p + 2 * (zoff + (long long)(y + 1) * L.px + L.gx + x), v);
-    if (has_ghost(L, x, y)) put_ghosts<S>(p, L, x, y, zoff, v);
 }
 
 // Store both components' values (v0, v1) of velocity k for node (x, y) of the
-// plane at zoff (p = f + L.at(0, k, 0)), with the ghost images of edge nodes:
-// one paired store per position.
+// plane at zoff (p = f + L.at(0, k, 0)): one paired store.
 template <class S>
 __device__ __forceinline__ void put_pair(S* __restrict__ p, const Layout& L, int x, int y, long long zoff, float v0,
                                          float v1)
 {
-    auto st = [&](long long o) {
-        if constexpr (sizeof(S) == 4) Codec<S>::store2(p + 2 * o, v0, v1);
-        else Codec<S>::put2(p + 2 * o, Codec<S>::rn(v0), Codec<S>::rn(v1));
-    };
-    const long long row = zoff + (long long)(y + 1) * L.px + L.gx;
-    st(row + x);
-    if (!has_ghost(L, x, y)) return;
-    const bool xl = x == L.nx - 1, xr = x == 0;
-    if (xl) st(row - 1);
-    if (xr) st(row + L.nx);
-    if (y == L.ny - 1) {
-        const long long g = zoff + L.gx;  // row y = -1
-        st(g + x);
-        if (xl) st(g - 1);
-        if (xr) st(g + L.nx);
-    }
-    if (y == 0) {
-        const long long g = zoff + (long long)(L.ny + 1) * L.px + L.gx;  // row y = ny
-        st(g + x);
-        if (xl) st(g - 1);
-        if (xr) st(g + L.nx);
-    }
+    const long long o = zoff + (long long)(y + 1) * L.px + L.gx + x;
+    if constexpr (sizeof(S) == 4) Codec<S>::store2(p + 2 * o, v0, v1);
+    else Codec<S>::put2(p + 2 * o, Codec<S>::rn(v0), Codec<S>::rn(v1));
 }
 
 // Parameters as the kernels use them.
@@ -330,6 +276,6 @@ __device__ __forceinline__ void clock_tick(uint32_t* clk)
 // nodes in 16 bytes (a node holds two values): the ring columns a TMA box
 // carries on each side of a tile
 template <class S>
-__host__ __device__ constexpr int ghost_x() { return 16 / (2 * (int)sizeof(S)); }
+__host__ __device__ constexpr int edge_x() { return 16 / (2 * (int)sizeof(S)); }
 
 }  // namespace lbsc

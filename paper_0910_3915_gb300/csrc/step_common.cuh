@@ -214,10 +214,9 @@ __device__ __forceinline__ float2 psi_pair(float psi_r, float psi_b) { return ma
 __device__ __forceinline__ float* psi_lane(float2* node, int a) { return (float*)node + (1 - a); }
 
 // Where the node's populations go: neighbours (wrapped), the planes of z-1,
-// z, z+1, and which links end on a wall.
-// Ghost images are not written here: the TMA path refreshes them in a
-// separate pass (ghost_rows_kernel) after each step. Addresses are a warp-uniform
-// slot base plus a 32-bit per-thread offset.
+// z, z+1, and which links end on a wall. Only real nodes are written (no
+// periodic images are stored). Addresses are a warp-uniform slot base plus a
+// 32-bit per-thread offset.
 struct Dest {
     int xo[3], yo[3];  // x-1, x, x+1 and y-1, y, y+1, wrapped
     int ro[3];         // row offsets of y-1, y, y+1 (incl. the left padding)

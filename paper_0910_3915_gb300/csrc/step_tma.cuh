@@ -8,10 +8,12 @@
 // cp.async.bulk.tensor, completion tracked by one mbarrier per stage. The
 // compute warps reduce a landed plane to rho, j and psi out of shared memory
 // while the following planes are in flight, then collide and push the plane
-// below. Periodic y comes from the storage's ghost rows (refreshed after each
-// step by a cheap row copy); periodic x from two 16-byte strips that the edge
-// tiles load beside the main box. Every wait is bounded: a wait that gives up
-// writes an error status, drains the CTA's copies in flight and leaves the kernel.
+// below. The periodic images come from small extra boxes of real nodes: two
+// 16-byte column strips at the x edges, one row at the y edges (the row
+// across the periodic boundary) and 16-byte corner pieces of that row, so no
+// image of any node is ever stored. Every wait is bounded: a wait that gives
+// up writes an error status, drains the CTA's copies in flight and leaves the
+// kernel.
 #pragma once
 
 #include <cuda.h>
@@ -68,27 +70,41 @@ __device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, u
         : "memory");
 }
 
-// Geometry of one stage: the main box [k][row][col][a] of 19 x (TY+2) x BX
-// nodes of two values, column c holding x = x0 - GX + c (16 bytes of columns
-// left of the tile, so the box starts on a 16-byte boundary), row r holding
-// y = y0 - 1 + r; then two strips [k][row][SX][a] of 16 bytes of columns
-// each, loaded only by the tiles at the x edges: the left strip holds the
-// columns around x = nx - 1 (the periodic image of x = -1), the right strip
-// x = 0 .. SX - 1 (the image of x = nx). Rows y = -1 and y = ny come from the
-// ghost rows. Element offsets below count values (two per node).
+// Geometry of one stage. The tensor maps order a buffer as (x values, storage
+// row, plane, slot k), so a box of R rows and W columns lands in shared
+// memory as [k][r][c][a]: element (k, r, c, a) at 2 ((k R + r) W + c) + a.
+// (Ordering the slot before the row would make the layouts of all regions
+// alike, but the copies would then walk the 19 slots, hundreds of megabytes
+// apart, row by row: measured 16% slower.) Regions, each 128-byte aligned:
+//   main     HY rows x BX columns: x = x0 - cofs + c (16 bytes of columns on
+//            each side of the tile; edge tiles shift the box inward, see the
+//            kernel), rows from the tile's row window;
+//   xl, xr   HY rows x SX columns (16 bytes), the same rows: the left strip
+//            holds the columns around x = nx - 1 (the images of x = -1), the
+//            right strip x = 0 .. SX - 1 (the images of x >= nx); loaded only by
+//            the tiles at the x edges;
+//   ys       one row x BX columns: the row across the periodic y boundary
+//            (y = ny - 1 for the first row of tiles, y = 0 for the last);
+//   cl, cr   one row x SX columns: the x-edge pieces of that row.
+// Element offsets count values (two per node).
 template <class S, int TY>
 struct TmaGeom {
     static constexpr int TX = 32, HX = TX + 2, HY = TY + 2;
-    static constexpr int GX = ghost_x<S>();                  // nodes in 16 bytes
+    static constexpr int GX = edge_x<S>();                    // nodes in 16 bytes
     static constexpr int BX = TX + 2 * GX;                   // the box's nodes per row: 16 bytes of columns each side
     static constexpr int SX = GX;                            // strip width: 16 bytes of columns
+    static constexpr int al(int elems) { return (elems * (int)sizeof(S) + 127) / 128 * 128 / (int)sizeof(S); }
     static constexpr int MAIN_ELEMS = 2 * Q * HY * BX;
-    static constexpr int MAIN_SPAN = (MAIN_ELEMS * (int)sizeof(S) + 127) / 128 * 128 / (int)sizeof(S);  // 128-B aligned
-    static constexpr int STRIP_BOX_ELEMS = 2 * Q * HY * SX;
-    static constexpr int STRIP_ELEMS = (STRIP_BOX_ELEMS * (int)sizeof(S) + 127) / 128 * 128 / (int)sizeof(S);
-    static constexpr int STAGE_ELEMS = MAIN_SPAN + 2 * STRIP_ELEMS;
+    static constexpr int XS_ELEMS = 2 * Q * HY * SX;
+    static constexpr int YS_ELEMS = 2 * Q * BX;
+    static constexpr int CS_ELEMS = 2 * Q * SX;
+    static constexpr int XL = al(MAIN_ELEMS), XR = XL + al(XS_ELEMS), YS = XR + al(XS_ELEMS);
+    static constexpr int CL = YS + al(YS_ELEMS), CR = CL + al(CS_ELEMS);
+    static constexpr int STAGE_ELEMS = CR + al(CS_ELEMS);
     static constexpr uint32_t MAIN_BYTES = MAIN_ELEMS * sizeof(S);
-    static constexpr uint32_t STRIP_BOX_BYTES = STRIP_BOX_ELEMS * sizeof(S);
+    static constexpr uint32_t XS_BYTES = XS_ELEMS * sizeof(S);
+    static constexpr uint32_t YS_BYTES = YS_ELEMS * sizeof(S);
+    static constexpr uint32_t CS_BYTES = CS_ELEMS * sizeof(S);
     static constexpr uint32_t STAGE_BYTES = STAGE_ELEMS * sizeof(S);
     static constexpr int PSI_FLOATS = 4 * 2 * HY * HX;
     static constexpr size_t smem(int NS) { return 128 + (size_t)NS * STAGE_BYTES + PSI_FLOATS * 4 + NS * 8; }
@@ -101,17 +117,23 @@ struct TmaGeom {
 template <class S, int TY, bool kTauOne>
 constexpr int kTmaCtas = !kTauOne ? 1 : (TY == 8 ? (sizeof(S) == 2 ? 4 : 3) : (TY == 4 ? 5 : 1));
 
+// The four tensor maps of one buffer and tile height: main box, x-edge strip,
+// y-edge row, corner piece (boxes HY x BX, HY x SX, 1 x BX, 1 x SX nodes).
+struct TmaMaps {
+    CUtensorMap m[4];
+};
+
 template <class S, int TY, int NS, bool kTauOne>
-__global__ void __launch_bounds__(32 * TY, (kTmaCtas<S, TY, kTauOne>)) step_tma_kernel(const __grid_constant__ CUtensorMap tmap,
-                                                           const __grid_constant__ CUtensorMap tstrip,
-                                                           const StepArgs<S> A)
+__global__ void __launch_bounds__(32 * TY, (kTmaCtas<S, TY, kTauOne>))
+    step_tma_kernel(const __grid_constant__ TmaMaps maps, const StepArgs<S> A)
 {
     using G = TmaGeom<S, TY>;
     constexpr int TX = 32, NT = TX * TY, HX = G::HX, HY = G::HY, GX = G::GX, BX = G::BX, SX = G::SX;
     constexpr int RING = 2 * HX + 2 * TY;
     constexpr int NIT = (RING + NT - 1) / NT;
-    static_assert(G::STAGE_BYTES % 128 == 0 && (G::MAIN_SPAN * sizeof(S)) % 128 == 0,
-                  "stages and strips stay 128-byte aligned");
+    static_assert(G::STAGE_BYTES % 128 == 0 && (G::XL * sizeof(S)) % 128 == 0 && (G::YS * sizeof(S)) % 128 == 0 &&
+                      (G::CL * sizeof(S)) % 128 == 0 && (G::CR * sizeof(S)) % 128 == 0,
+                  "stages and their regions stay 128-byte aligned");
     static_assert((2 * BX * sizeof(S)) % 16 == 0 && (2 * SX * sizeof(S)) % 16 == 0, "box rows are whole 16-byte units");
     using P2 = typename Codec<S>::Pair;
 
@@ -165,21 +187,39 @@ __global__ void __launch_bounds__(32 * TY, (kTmaCtas<S, TY, kTauOne>)) step_tma_
         // (0 at the left edge, 2 GX at the right edge)
         const int cofs = left_edge ? 0 : (right_edge ? 2 * GX : GX);
         const int sl = (L.gx + nx - 1) / SX * SX, ol = L.gx + nx - 1 - sl;
+        // y edges: the row window of the box, given by the box row of node row
+        // y0 (rofs). A middle tile's box holds rows y0 - 1 .. y0 + TY; the first
+        // row of tiles' rows 0 .. HY - 1 and the last row's the HY rows ending at
+        // its last own row, the ring row across the boundary coming from the
+        // y-edge row (ys, with its corner pieces). With a single row of tiles
+        // (ny <= TY) the box holds every row and the ring rows wrap inside it.
+        const bool single = A.tiles_y == 1;
+        const bool first = tyi == 0 && !single, last = tyi == A.tiles_y - 1 && !single;
+        const int rofs = (first || single) ? 0 : (last ? HY - hgt : 1);
+        const int yrow = first ? ny - 1 : 0;  // the real row in ys (first or last row of tiles)
         // own node: the main box; lanes past x = nx - 1 of a ragged last tile
         // hold the periodic images x - nx from the right strip (the one at
         // x = nx is the +x neighbour of x = nx - 1), as far as the strip reaches
         const bool own_strip = gx >= nx;
         const bool own_rd = active && gx - nx < SX;
+        const int own_off = own_strip ? G::XR + 2 * ((ty + rofs) * SX + gx - nx) : 2 * ((ty + rofs) * BX + tx + cofs);
+        // the copies' coordinates: x of the main box and of the left strip in
+        // values (two per node; 16-byte aligned, as the copy requires), storage
+        // row (real row + 1) of the box's first row and of the y-edge row (-1: none)
+        const int xb = 2 * (x0 + L.gx - cofs), xs = 2 * sl;
+        const int yb = y0 - rofs + 1, ysr = (first || last) ? yrow + 1 : -1;
 
         // ring items (one per ring node, both components): shared-memory
-        // position, stage position of the node's slot-0 pair, source (0 main
-        // box, 1 left strip, 2 right strip)
-        int it_sm[NIT], it_base[NIT], it_src[NIT];
+        // position, stage position of the node's slot-0 pair, and its region's
+        // slot stride: 0 main box (2 HY BX), 1 x strip (2 HY SX), 2 y-edge row
+        // (2 BX), 3 corner piece (2 SX)
+        int it_sm[NIT], it_base[NIT], it_cls[NIT];
         bool it_on[NIT];
 #pragma unroll
         for (int i = 0; i < NIT; ++i) {
             const int r = tid + i * NT;
             it_on[i] = false;
+            it_cls[i] = 0;
             if (r < RING) {
                 int ix, iy;
                 if (r < HX) { ix = r; iy = 0; }
@@ -188,16 +228,18 @@ __global__ void __launch_bounds__(32 * TY, (kTmaCtas<S, TY, kTauOne>)) step_tma_
                 else { ix = HX - 1; iy = r - 2 * HX - TY + 1; }
                 it_on[i] = r < 2 * HX || iy <= hgt;  // side columns: the tile's own rows only
                 it_sm[i] = iy * HX + ix;
-                const int xr = x0 - 1 + ix;  // the ring node's x (unwrapped)
-                if (xr < 0) {
-                    it_src[i] = 1;  // x = -1: the image of x = nx - 1
-                    it_base[i] = G::MAIN_SPAN + 2 * (iy * SX + ol);
-                } else if (xr >= nx && xr - nx < SX) {
-                    it_src[i] = 2;  // x >= nx: the images of x - nx
-                    it_base[i] = G::MAIN_SPAN + G::STRIP_ELEMS + 2 * (iy * SX + xr - nx);
+                const int xr = x0 - 1 + ix, yr = y0 - 1 + iy;  // the ring node (unwrapped)
+                const bool across = (first && yr < 0) || (last && yr >= ny);  // in the y-edge row
+                const int row = wrapi(yr, ny) - y0 + rofs;                   // box row otherwise
+                if (xr < 0) {  // x = -1: the image of x = nx - 1
+                    it_cls[i] = across ? 3 : 1;
+                    it_base[i] = across ? G::CL + 2 * ol : G::XL + 2 * (row * SX + ol);
+                } else if (xr >= nx && xr - nx < SX) {  // x >= nx: the images of x - nx
+                    it_cls[i] = across ? 3 : 1;
+                    it_base[i] = across ? G::CR + 2 * (xr - nx) : G::XR + 2 * (row * SX + xr - nx);
                 } else {
-                    it_src[i] = 0;
-                    it_base[i] = 2 * (iy * BX + ix - 1 + cofs);
+                    it_cls[i] = across ? 2 : 0;
+                    it_base[i] = across ? G::YS + 2 * (ix - 1 + cofs) : 2 * (row * BX + ix - 1 + cofs);
                 }
             }
         }
@@ -208,13 +250,20 @@ __global__ void __launch_bounds__(32 * TY, (kTmaCtas<S, TY, kTauOne>)) step_tma_
                 mbar_arrive(b);  // a solid plane: nothing to load
             } else {
                 S* stg = stages + (size_t)(gi % NS) * G::STAGE_ELEMS;
+                const bool ye = ysr >= 0;
                 fence_proxy_async();
-                mbar_expect_tx(b, G::MAIN_BYTES + (left_edge ? G::STRIP_BOX_BYTES : 0u) +
-                                      (right_edge ? G::STRIP_BOX_BYTES : 0u));
-                // x coordinates count values (two per node): 16-byte aligned, as the copy requires
-                tma_load_4d(stg, &tmap, b, 2 * (x0 + L.gx - cofs), y0, zp, 0);
-                if (left_edge) tma_load_4d(stg + G::MAIN_SPAN, &tstrip, b, 2 * sl, y0, zp, 0);
-                if (right_edge) tma_load_4d(stg + G::MAIN_SPAN + G::STRIP_ELEMS, &tstrip, b, 2 * L.gx, y0, zp, 0);
+                mbar_expect_tx(b, G::MAIN_BYTES + (left_edge ? G::XS_BYTES : 0u) + (right_edge ? G::XS_BYTES : 0u) +
+                                      (ye ? G::YS_BYTES + (left_edge ? G::CS_BYTES : 0u) +
+                                                (right_edge ? G::CS_BYTES : 0u)
+                                          : 0u));
+                tma_load_4d(stg, &maps.m[0], b, xb, yb, zp, 0);
+                if (left_edge) tma_load_4d(stg + G::XL, &maps.m[1], b, xs, yb, zp, 0);
+                if (right_edge) tma_load_4d(stg + G::XR, &maps.m[1], b, 2 * L.gx, yb, zp, 0);
+                if (ye) {
+                    tma_load_4d(stg + G::YS, &maps.m[2], b, xb, ysr, zp, 0);
+                    if (left_edge) tma_load_4d(stg + G::CL, &maps.m[3], b, xs, ysr, zp, 0);
+                    if (right_edge) tma_load_4d(stg + G::CR, &maps.m[3], b, 2 * L.gx, ysr, zp, 0);
+                }
             }
         };
 
@@ -235,8 +284,8 @@ __global__ void __launch_bounds__(32 * TY, (kTmaCtas<S, TY, kTauOne>)) step_tma_
                 if (!solid && own_rd) {
                     float w[2][Q];
                     // both components of velocity k in one shared-memory load
+                    const P2* so = (const P2*)(st + own_off);
                     if (!own_strip) {
-                        const P2* so = (const P2*)(st + 2 * ((ty + 1) * BX + tx + cofs));
 #pragma unroll
                         for (int k = 0; k < Q; ++k) {
                             const float2 t = Codec<S>::val2(so[k * HY * BX]);
@@ -244,7 +293,6 @@ __global__ void __launch_bounds__(32 * TY, (kTmaCtas<S, TY, kTauOne>)) step_tma_
                             w[1][k] = t.y;
                         }
                     } else {
-                        const P2* so = (const P2*)(st + G::MAIN_SPAN + G::STRIP_ELEMS + 2 * ((ty + 1) * SX + gx - nx));
 #pragma unroll
                         for (int k = 0; k < Q; ++k) {
                             const float2 t = Codec<S>::val2(so[k * HY * SX]);
@@ -274,12 +322,19 @@ __global__ void __launch_bounds__(32 * TY, (kTmaCtas<S, TY, kTauOne>)) step_tma_
                         // both components of velocity k in one shared-memory load
                         float2 w[Q];
                         const P2* si = (const P2*)(st + it_base[q]);
-                        if (it_src[q] == 0) {
+                        const int cls = it_cls[q];
+                        if (cls == 0) {
 #pragma unroll
                             for (int k = 0; k < Q; ++k) w[k] = Codec<S>::val2(si[k * HY * BX]);
-                        } else {
+                        } else if (cls == 1) {
 #pragma unroll
                             for (int k = 0; k < Q; ++k) w[k] = Codec<S>::val2(si[k * HY * SX]);
+                        } else if (cls == 2) {
+#pragma unroll
+                            for (int k = 0; k < Q; ++k) w[k] = Codec<S>::val2(si[k * BX]);
+                        } else {
+#pragma unroll
+                            for (int k = 0; k < Q; ++k) w[k] = Codec<S>::val2(si[k * SX]);
                         }
                         float2 unused;
                         pr = psi2_of(rho2_of<S>(w, f2(ref[0], ref[1]), unused));
@@ -354,7 +409,9 @@ static cudaError_t tma_launch_one(const CUtensorMap* m, const StepArgs<S>& A, cu
 {
     const size_t smem = TmaGeom<S, TY>::smem(NS);
     const int items = A.tiles_x * A.tiles_y * A.nseg;
-    step_tma_kernel<S, TY, NS, T1><<<items, 32 * TY, smem, st>>>(m[0], m[1], A);
+    TmaMaps maps;
+    for (int i = 0; i < 4; ++i) maps.m[i] = m[i];
+    step_tma_kernel<S, TY, NS, T1><<<items, 32 * TY, smem, st>>>(maps, A);
     return cudaGetLastError();
 }
 

@@ -93,7 +93,7 @@ def test_argument_errors_before_cuda(lib):
     nb = ctypes.c_size_t()
     assert lib.lb_required_bytes(128, 128, 128, lbsc.LB_F32, ctypes.byref(nb)) == lbsc.LB_OK
     # two population buffers of 38 planes dominate: 304 B per node in FP32
-    assert 304 * 128 ** 3 < nb.value < 600 * 128 ** 3  # aligned rows, ghost columns and rows pad the planes
+    assert 304 * 128 ** 3 < nb.value < 600 * 128 ** 3  # aligned rows and spare rows pad the planes
     assert lib.lb_required_bytes(128, 128, 128, lbsc.LB_BF16, ctypes.byref(nb)) == lbsc.LB_OK
     assert nb.value < 360 * 128 ** 3  # 16-bit: half the population bytes of FP32
     lib.lb_free(None)
