@@ -431,8 +431,7 @@ def run_sweep(args):
     from paper_0910_3915_gb300 import tune
 
     batch = lbsc.Batch(fields, params, wl["precision"])
-    (b_ty, b_planes), _ = tune.tune_batch(batch)
-    best = (None, b_ty, b_planes)
+    best, _ = tune.tune_batch(batch)
     batch.step(Wm)
     torch.cuda.synchronize()
     replicas.barrier()
@@ -481,14 +480,16 @@ def run_sweep(args):
         "dtype": wl["precision"], "data": "synthetic",
         "config": {"workload": f"batched sweep: {len(boxes)} cubic boxes, edges from 48/64/80/96, R = 0.3 edge"
                                + (f", round-robin over {ws} ranks" if ws > 1 else ""),
-                   "fluid_nodes": nf, "schedule": {"tile": f"32x{best[1]}", "planes_per_item": best[2]},
+                   "fluid_nodes": nf,
+                   "schedule": {"variant": best[0], "tile": f"32x{best[1]}", "planes_per_item": best[2]},
                    "l2": "inputs larger than L2"},
         "sequential_mlups": round(nf * K / (ms_seq * 1e-3) / 1e6, 1),
         "speedup_vs_sequential": round(ms_seq / ms_batch, 3),
         "roofline": {"bound": "hbm", "achieved": round(nf * 304 / (ms_batch / K * 1e-3) / 1e9 / ws, 1),
                      "peak": peaks()[0], "unit": "GB/s",
                      "frac": round(nf * 304 / (ms_batch / K * 1e-3) / 1e9 / ws / peaks()[0], 4),
-                     "note": "per GPU" if ws > 1 else None},
+                     "note": "per GPU" if ws > 1 else None,
+                     "kernel": "batch_tma_kernel" if best[0] == "tma" else "batch_step_kernel"},
         "theta_deg": [round(a["theta_deg"], 2) if a["ok"] else None for a in angles],
         "droplets": droplet_validity(boxes, angles),
     }
@@ -1010,7 +1011,7 @@ def throughput_samples(K: int, Wm: int, peak: float):
         params.append(lbsc.Params(g_br=bx.g_br, eta_wall_r=er, eta_wall_b=eb, force_weights=1, force_scale=1.25))
     nf = sum(bx.edge * bx.edge * (bx.edge - 2) for bx in boxes)
     batch = lbsc.Batch(fields, params, wl["precision"])
-    (b_ty, b_planes), _ = tune.tune_batch(batch, steps=32)
+    (b_var, b_ty, b_planes), _ = tune.tune_batch(batch, steps=32)
     batch.step(Wm)
     torch.cuda.synchronize()
     a, b = ev(), ev()
@@ -1024,9 +1025,10 @@ def throughput_samples(K: int, Wm: int, peak: float):
     out["sweep"] = {
         "workload": f"batched sweep: {len(boxes)} cubic boxes, edges from 48/64/80/96, R = 0.3 edge, one launch a step",
         "value": round(nf / (ms * 1e-3) / 1e6, 1), "unit": "MLUPS", "steps": K, "ms_per_step": round(ms, 5),
-        "schedule": {"tile": f"32x{b_ty}", "planes_per_item": b_planes},
+        "schedule": {"variant": b_var, "tile": f"32x{b_ty}", "planes_per_item": b_planes},
         "roofline": {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
-                     "frac": round(ach / peak, 4), "bytes_per_lu": 304, "kernel": "batch_step_kernel"}}
+                     "frac": round(ach / peak, 4), "bytes_per_lu": 304,
+                     "kernel": "batch_tma_kernel" if b_var == "tma" else "batch_step_kernel"}}
     return out
 
 

@@ -420,6 +420,12 @@ int lb_batch_set_params(lb_batch* b, int i, const lb_params* params);
  * the persistent grid (0 = as many as fit). Results do not depend on it. */
 int lb_batch_set_schedule(lb_batch* b, int tile_y, int planes_per_item, int ctas_per_sm);
 
+/* Choose the batch's step kernel: LB_STEP_AUTO (default) and LB_STEP_TMA take
+ * the TMA-staged persistent kernel (one stage; tile heights 4 and 8, else the
+ * load-from-global one), LB_STEP_LDG the load-from-global persistent kernel.
+ * Both compute bit-identical results. LB_ERR_ARG for an unknown variant. */
+int lb_batch_set_step_variant(lb_batch* b, int variant);
+
 /* Advance every box by nsteps (asynchronous). LB_ERR_STATE if a box was
  * stepped on its own in between. */
 int lb_batch_step(lb_batch* b, int nsteps);

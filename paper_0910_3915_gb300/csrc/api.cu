@@ -1110,8 +1110,11 @@ struct lb_batch {
     void* dargs = nullptr;  // StepArgs<S>[2*nbox]: box i read from buffer parity p at 2*i + p
     uint32_t* done = nullptr; // CTAs finished in the current step (the last one advances the boxes' counters)
     int4* ditems = nullptr; // (box, tile column, first plane, end plane)
+    void* dmaps = nullptr;  // TMA variant: the four tensor maps of box i, source buffer p, at 2*i + p
     int nitems = 0;
     int tile_y = 8, seg_planes = 32, ctas_per_sm = 0, grid = 0;
+    int variant = LB_STEP_AUTO;
+    bool tma = false;       // the TMA-staged batch kernel runs the steps
     bool tau1 = true;
     int cur = 0;
     long long steps = 0;
@@ -1164,8 +1167,10 @@ static int batch_build_typed(lb_batch* b)
     }
     if (b->dargs) cudaFree(b->dargs);
     if (b->ditems) cudaFree(b->ditems);
+    if (b->dmaps) cudaFree(b->dmaps);
     b->dargs = nullptr;
     b->ditems = nullptr;
+    b->dmaps = nullptr;
     const size_t abytes = align256(args.size() * sizeof(StepArgs<S>));
     LB_BCUDA(b, cudaMalloc(&b->dargs, abytes + 256));
     b->done = (uint32_t*)((char*)b->dargs + abytes);
@@ -1174,8 +1179,32 @@ static int batch_build_typed(lb_batch* b)
     LB_BCUDA(b, cudaMemcpy(b->dargs, args.data(), args.size() * sizeof(StepArgs<S>), cudaMemcpyHostToDevice));
     LB_BCUDA(b, cudaMemcpy(b->ditems, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice));
     b->nitems = (int)items.size();
-    const int occ = b->ctas_per_sm > 0 ? b->ctas_per_sm : batch_occupancy<S>(b->tile_y, b->tau1);
-    b->grid = b->box[0]->nsm * occ;
+    // AUTO and TMA take the TMA-staged batch kernel where it is built (one
+    // stage, 4- or 8-row tiles); LDG the load-from-global one
+    // (the shared-memory attribute first: the occupancy of a kernel above 48 KB counts 0 without it)
+    b->tma = b->variant != LB_STEP_LDG &&
+             tma_batch<S>(1, b->tile_y, b->tau1, nullptr, nullptr, nullptr, 0, 0, 0, nullptr, 0, nullptr) ==
+                 (long long)cudaSuccess &&
+             tma_batch<S>(2, b->tile_y, b->tau1, nullptr, nullptr, nullptr, 0, 0, 0, nullptr, 0, nullptr) > 0;
+    if (b->tma) {
+        std::vector<CUtensorMap> maps(8 * (size_t)b->nbox);
+        for (int i = 0; i < b->nbox; ++i) {
+            lb_ctx* c = b->box[i];
+            for (int p = 0; p < 2; ++p) {
+                const int rc = tensor_map(c, p, b->tile_y);
+                if (rc != LB_OK) return bfail(b, rc, c->err);
+                for (int k = 0; k < 4; ++k) maps[8 * i + 4 * p + k] = c->tmap[p][tile_index(b->tile_y)][k];
+            }
+        }
+        LB_BCUDA(b, cudaMalloc(&b->dmaps, maps.size() * sizeof(CUtensorMap)));  // 256-byte aligned
+        LB_BCUDA(b, cudaMemcpy(b->dmaps, maps.data(), maps.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice));
+    }
+    const int occ = b->ctas_per_sm > 0
+                        ? b->ctas_per_sm
+                        : (b->tma ? (int)tma_batch<S>(2, b->tile_y, b->tau1, nullptr, nullptr, nullptr, 0, 0, 0,
+                                                      nullptr, 0, nullptr)
+                                  : batch_occupancy<S>(b->tile_y, b->tau1));
+    b->grid = b->box[0]->nsm * (occ > 0 ? occ : 1);
     return LB_OK;
 }
 
@@ -1189,8 +1218,22 @@ static int batch_build(lb_batch* b)
     }
 }
 
+template <class S>
+static cudaError_t batch_launch_tma(lb_batch* b, int parity, cudaStream_t st)
+{
+    return (cudaError_t)tma_batch<S>(0, b->tile_y, b->tau1, b->dmaps, (const StepArgs<S>*)b->dargs, b->ditems,
+                                     b->nitems, parity, b->nbox, b->done, b->grid, st);
+}
+
 static cudaError_t batch_launch(lb_batch* b, int parity, cudaStream_t st)
 {
+    if (b->tma) {
+        switch (b->prec) {
+        case LB_F32: return batch_launch_tma<float>(b, parity, st);
+        case LB_F16: return batch_launch_tma<__half>(b, parity, st);
+        default: return batch_launch_tma<__nv_bfloat16>(b, parity, st);
+        }
+    }
     switch (b->prec) {
     case LB_F32:
         return launch_batch_step<float>((const StepArgs<float>*)b->dargs, b->ditems, b->nitems, parity, b->tile_y,
@@ -1278,6 +1321,14 @@ int lb_batch_set_schedule(lb_batch* b, int tile_y, int planes_per_item, int ctas
     return batch_build(b);
 }
 
+int lb_batch_set_step_variant(lb_batch* b, int variant)
+{
+    if (!b || variant < LB_STEP_AUTO || variant > LB_STEP_TMA)
+        return bfail(b, LB_ERR_ARG, "lb_batch_set_step_variant: unknown variant");
+    b->variant = variant;
+    return batch_build(b);
+}
+
 int lb_batch_step(lb_batch* b, int nsteps)
 {
     if (!b || nsteps < 0) return bfail(b, LB_ERR_ARG, "lb_batch_step: bad argument");
@@ -1357,6 +1408,7 @@ void lb_batch_free(lb_batch* b)
     for (lb_ctx* c : b->box) lb_free(c);
     if (b->dargs) cudaFree(b->dargs);
     if (b->ditems) cudaFree(b->ditems);
+    if (b->dmaps) cudaFree(b->dmaps);
     if (b->mem) cudaFree(b->mem);
     if (b->cap) cudaStreamDestroy(b->cap);
     delete b;

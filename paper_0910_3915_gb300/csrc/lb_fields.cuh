@@ -66,6 +66,13 @@ long long tma_step(int op, int tile_y, int stages, bool tau_one, const CUtensorM
 template <class S>
 cudaError_t launch_batch_step(const StepArgs<S>* args, const int4* items, int nitems, int parity, int tile_y,
                               bool tau_one, int grid, int nbox, uint32_t* done, cudaStream_t st);
+// Batched TMA-staged step (planar walls, one stage, 4- or 8-row tiles): maps
+// is a device array of 2 nbox groups of the four tensor maps (box i, source
+// buffer p at 2 i + p, 64-byte aligned); ops as for tma_step (op 0 launches
+// on `grid` CTAs).
+template <class S>
+long long tma_batch(int op, int tile_y, bool tau_one, const void* maps, const StepArgs<S>* args, const int4* items,
+                    int nitems, int parity, int nbox, uint32_t* done, int grid, cudaStream_t stream);
 template <class S>
 int batch_occupancy(int tile_y, bool tau_one);
 // bounded-wait self-test: a wait nothing satisfies, limit try_wait rounds

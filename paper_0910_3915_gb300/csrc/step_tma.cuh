@@ -123,25 +123,21 @@ struct TmaMaps {
     CUtensorMap m[4];
 };
 
+// One work item: tile column `col` of the lattice A (tile row col / tiles_x,
+// x tile col % tiles_x), fluid planes [za, zb), with the maps of A's source
+// buffer. `stages`, `sp` and `bar` are the CTA's shared stages, psi ring and
+// stage barriers; g counts the planes the CTA has consumed so far (the
+// barriers' phases run on across items). Returns false when a wait gave up
+// (the status word is set and the CTA's copies in flight are drained).
 template <class S, int TY, int NS, bool kTauOne>
-__global__ void __launch_bounds__(32 * TY, (kTmaCtas<S, TY, kTauOne>))
-    step_tma_kernel(const __grid_constant__ TmaMaps maps, const StepArgs<S> A)
+__device__ __forceinline__ bool tma_item(const TmaMaps& maps, const StepArgs<S>& A, int col, int za, int zb, S* stages,
+                                         float* sp, uint64_t* bar, uint32_t& g, uint32_t clk)
 {
     using G = TmaGeom<S, TY>;
     constexpr int TX = 32, NT = TX * TY, HX = G::HX, HY = G::HY, GX = G::GX, BX = G::BX, SX = G::SX;
     constexpr int RING = 2 * HX + 2 * TY;
     constexpr int NIT = (RING + NT - 1) / NT;
-    static_assert(G::STAGE_BYTES % 128 == 0 && (G::XL * sizeof(S)) % 128 == 0 && (G::YS * sizeof(S)) % 128 == 0 &&
-                      (G::CL * sizeof(S)) % 128 == 0 && (G::CR * sizeof(S)) % 128 == 0,
-                  "stages and their regions stay 128-byte aligned");
-    static_assert((2 * BX * sizeof(S)) % 16 == 0 && (2 * SX * sizeof(S)) % 16 == 0, "box rows are whole 16-byte units");
     using P2 = typename Codec<S>::Pair;
-
-    extern __shared__ unsigned char smem_raw[];
-    unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
-    S* stages = (S*)base;
-    float* sp = (float*)(base + (size_t)NS * G::STAGE_BYTES);  // psi ring [4][HY][HX] of pairs (psi^b, psi^r)
-    uint64_t* bar = (uint64_t*)(sp + G::PSI_FLOATS);
 
     const Layout L = A.L;
     const int nx = L.nx, ny = L.ny, nz = L.nz;
@@ -153,10 +149,248 @@ __global__ void __launch_bounds__(32 * TY, (kTmaCtas<S, TY, kTauOne>))
     const float itau[2] = {A.P.itau[0], A.P.itau[1]};
     const float gk = A.P.gk, Gax = A.P.Gax, Gdi = A.P.Gdi;
     const int tid = threadIdx.x, tx = tid % TX, ty = tid / TX;
-    const int ncol = A.tiles_x * A.tiles_y;
-    const int nzf = A.zhi - A.zlo;
 
-    if (tid == 0) {
+    // rows [y0, y0 + hgt) of an even split of ny (hgt <= TY); a row past hgt is an idle warp
+    const int tyi = col / A.tiles_x;
+    const int x0 = (col - tyi * A.tiles_x) * TX;
+    const int y0 = tile_row(tyi, ny, A.tiles_y), hgt = tile_row(tyi + 1, ny, A.tiles_y) - y0;
+    const int gx = x0 + tx, gy = y0 + ty;
+    const bool active = ty < hgt;
+    const bool valid = active && gx < nx;
+    const int np = zb - za + 2;  // planes za-1 .. zb
+    // x edges: the periodic images come from the strips (column of x = nx - 1 in the left strip)
+    const bool left_edge = x0 == 0, right_edge = x0 + TX >= nx;
+    // the box's column of node x0: GX (16 bytes of ring columns on each
+    // side); an edge tile takes its outer ring column from a strip, so its
+    // box is shifted inward and reads no padding columns beyond the lattice
+    // (0 at the left edge, 2 GX at the right edge)
+    const int cofs = left_edge ? 0 : (right_edge ? 2 * GX : GX);
+    const int sl = (L.gx + nx - 1) / SX * SX, ol = L.gx + nx - 1 - sl;
+    // y edges: the row window of the box, given by the box row of node row
+    // y0 (rofs). A middle tile's box holds rows y0 - 1 .. y0 + TY; the first
+    // row of tiles' rows 0 .. HY - 1 and the last row's the HY rows ending at
+    // its last own row, the ring row across the boundary coming from the
+    // y-edge row (ys, with its corner pieces). With a single row of tiles
+    // (ny <= TY) the box holds every row and the ring rows wrap inside it.
+    const bool single = A.tiles_y == 1;
+    const bool first = tyi == 0 && !single, last = tyi == A.tiles_y - 1 && !single;
+    const int rofs = (first || single) ? 0 : (last ? HY - hgt : 1);
+    const int yrow = first ? ny - 1 : 0;  // the real row in ys (first or last row of tiles)
+    // own node: the main box; lanes past x = nx - 1 of a ragged last tile
+    // hold the periodic images x - nx from the right strip (the one at
+    // x = nx is the +x neighbour of x = nx - 1), as far as the strip reaches
+    const bool own_strip = gx >= nx;
+    const bool own_rd = active && gx - nx < SX;
+    const int own_off = own_strip ? G::XR + 2 * ((ty + rofs) * SX + gx - nx) : 2 * ((ty + rofs) * BX + tx + cofs);
+    // the copies' coordinates: x of the main box and of the left strip in
+    // values (two per node; 16-byte aligned, as the copy requires), storage
+    // row (real row + 1) of the box's first row and of the y-edge row (-1: none)
+    const int xb = 2 * (x0 + L.gx - cofs), xs = 2 * sl;
+    const int yb = y0 - rofs + 1, ysr = (first || last) ? yrow + 1 : -1;
+
+    // ring items (one per ring node, both components): shared-memory
+    // position, stage position of the node's slot-0 pair, and its region's
+    // slot stride: 0 main box (2 HY BX), 1 x strip (2 HY SX), 2 y-edge row
+    // (2 BX), 3 corner piece (2 SX)
+    int it_sm[NIT], it_base[NIT], it_cls[NIT];
+    bool it_on[NIT];
+#pragma unroll
+    for (int i = 0; i < NIT; ++i) {
+        const int r = tid + i * NT;
+        it_on[i] = false;
+        it_cls[i] = 0;
+        if (r < RING) {
+            int ix, iy;
+            if (r < HX) { ix = r; iy = 0; }
+            else if (r < 2 * HX) { ix = r - HX; iy = hgt + 1; }
+            else if (r < 2 * HX + TY) { ix = 0; iy = r - 2 * HX + 1; }
+            else { ix = HX - 1; iy = r - 2 * HX - TY + 1; }
+            it_on[i] = r < 2 * HX || iy <= hgt;  // side columns: the tile's own rows only
+            it_sm[i] = iy * HX + ix;
+            const int xr = x0 - 1 + ix, yr = y0 - 1 + iy;  // the ring node (unwrapped)
+            const bool across = (first && yr < 0) || (last && yr >= ny);  // in the y-edge row
+            const int row = wrapi(yr, ny) - y0 + rofs;                   // box row otherwise
+            if (xr < 0) {  // x = -1: the image of x = nx - 1
+                it_cls[i] = across ? 3 : 1;
+                it_base[i] = across ? G::CL + 2 * ol : G::XL + 2 * (row * SX + ol);
+            } else if (xr >= nx && xr - nx < SX) {  // x >= nx: the images of x - nx
+                it_cls[i] = across ? 3 : 1;
+                it_base[i] = across ? G::CR + 2 * (xr - nx) : G::XR + 2 * (row * SX + xr - nx);
+            } else {
+                it_cls[i] = across ? 2 : 0;
+                it_base[i] = across ? G::YS + 2 * (ix - 1 + cofs) : 2 * (row * BX + ix - 1 + cofs);
+            }
+        }
+    }
+
+    auto issue = [&](int zp, uint32_t gi) {
+        uint64_t* b = &bar[gi % NS];
+        if (zp == 0 || zp == nz - 1) {
+            mbar_arrive(b);  // a solid plane: nothing to load
+        } else {
+            S* stg = stages + (size_t)(gi % NS) * G::STAGE_ELEMS;
+            const bool ye = ysr >= 0;
+            fence_proxy_async();
+            mbar_expect_tx(b, G::MAIN_BYTES + (left_edge ? G::XS_BYTES : 0u) + (right_edge ? G::XS_BYTES : 0u) +
+                                  (ye ? G::YS_BYTES + (left_edge ? G::CS_BYTES : 0u) +
+                                            (right_edge ? G::CS_BYTES : 0u)
+                                      : 0u));
+            tma_load_4d(stg, &maps.m[0], b, xb, yb, zp, 0);
+            if (left_edge) tma_load_4d(stg + G::XL, &maps.m[1], b, xs, yb, zp, 0);
+            if (right_edge) tma_load_4d(stg + G::XR, &maps.m[1], b, 2 * L.gx, yb, zp, 0);
+            if (ye) {
+                tma_load_4d(stg + G::YS, &maps.m[2], b, xb, ysr, zp, 0);
+                if (left_edge) tma_load_4d(stg + G::CL, &maps.m[3], b, xs, ysr, zp, 0);
+                if (right_edge) tma_load_4d(stg + G::CR, &maps.m[3], b, 2 * L.gx, ysr, zp, 0);
+            }
+        }
+    };
+
+    // wait for plane i of the item, reduce it to psi (tile + ring) and own
+    // moments, then refill its stage with plane i + NS
+    auto consume = [&](int i, float (&rho)[2], float (&j)[2][3], float (&v)[2][Q], float (&m)[2]) -> bool {
+        const int zp = za - 1 + i;
+        const uint32_t gi = g + i;
+        const bool ok = mbar_wait(&bar[gi % NS], (gi / NS) & 1u);
+        float2* spl = (float2*)sp + (zp & 3) * (HY * HX);
+        const bool solid = zp == 0 || zp == nz - 1;
+        if (ok) {
+            const S* st = stages + (size_t)(gi % NS) * G::STAGE_ELEMS;
+            float ps[2] = {eta[0], eta[1]};
+            rho[0] = rho[1] = m[0] = m[1] = 0.f;
+#pragma unroll
+            for (int a = 0; a < 2; ++a) j[a][0] = j[a][1] = j[a][2] = 0.f;
+            if (!solid && own_rd) {
+                float w[2][Q];
+                // both components of velocity k in one shared-memory load
+                const P2* so = (const P2*)(st + own_off);
+                if (!own_strip) {
+#pragma unroll
+                    for (int k = 0; k < Q; ++k) {
+                        const float2 t = Codec<S>::val2(so[k * HY * BX]);
+                        w[0][k] = t.x;
+                        w[1][k] = t.y;
+                    }
+                } else {
+#pragma unroll
+                    for (int k = 0; k < Q; ++k) {
+                        const float2 t = Codec<S>::val2(so[k * HY * SX]);
+                        w[0][k] = t.x;
+                        w[1][k] = t.y;
+                    }
+                }
+                moments2<S>(w, ref, rho, j, m);
+                const float2 p2 = psi2_of(f2(rho[0], rho[1]));
+                ps[0] = p2.x;
+                ps[1] = p2.y;
+                if constexpr (!kTauOne) {
+#pragma unroll
+                    for (int a = 0; a < 2; ++a)
+#pragma unroll
+                        for (int k = 0; k < Q; ++k) v[a][k] = w[a][k];
+                }
+            }
+            if (active) {
+                spl[(ty + 1) * HX + tx + 1] = psi_pair(ps[0], ps[1]);
+            }
+#pragma unroll
+            for (int q = 0; q < NIT; ++q) {
+                if (!it_on[q]) continue;
+                float2 pr = f2(eta[0], eta[1]);
+                if (!solid) {
+                    // both components of velocity k in one shared-memory load
+                    float2 w[Q];
+                    const P2* si = (const P2*)(st + it_base[q]);
+                    const int cls = it_cls[q];
+                    if (cls == 0) {
+#pragma unroll
+                        for (int k = 0; k < Q; ++k) w[k] = Codec<S>::val2(si[k * HY * BX]);
+                    } else if (cls == 1) {
+#pragma unroll
+                        for (int k = 0; k < Q; ++k) w[k] = Codec<S>::val2(si[k * HY * SX]);
+                    } else if (cls == 2) {
+#pragma unroll
+                        for (int k = 0; k < Q; ++k) w[k] = Codec<S>::val2(si[k * BX]);
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < Q; ++k) w[k] = Codec<S>::val2(si[k * SX]);
+                    }
+                    float2 unused;
+                    pr = psi2_of(rho2_of<S>(w, f2(ref[0], ref[1]), unused));
+                }
+                spl[it_sm[q]] = psi_pair(pr.x, pr.y);
+            }
+        }
+        const bool bad = __syncthreads_or(!ok);
+        if (bad) {
+            if (tid == 0) {
+                atomicOr(A.err, kErrWait);
+                for (int k2 = i; k2 < np && k2 < i + NS; ++k2) mbar_wait(&bar[(g + k2) % NS], ((g + k2) / NS) & 1u);
+            }
+            return false;
+        }
+        if (tid == 0 && i + NS < np) issue(zp + NS, gi + NS);
+        return true;
+    };
+
+    float rc[2], jc[2][3], vc[2][Q], mc[2];
+    float rn[2], jn[2][3], vn[2][Q], mn[2];
+    __syncthreads();  // the previous item's collide is done with the psi ring
+    if (tid == 0)
+        for (int i = 0; i < NS && i < np; ++i) issue(za - 1 + i, g + i);
+    if (!consume(0, rn, jn, vn, mn) || !consume(1, rc, jc, vc, mc)) return false;
+
+    Dest D;
+    D.set_column(L, valid ? gx : 0, valid ? gy : 0);
+    D.err = A.err;
+    D.hoff = A.hkey;
+
+    for (int z = za; z < zb; ++z) {
+        if (!consume(z - za + 2, rn, jn, vn, mn)) return false;
+        if (valid) {
+            float F[2][3];
+            const float2* ring = (const float2*)sp;
+            sc_force<HX, HY>(ring + ((z - 1) & 3) * (HY * HX), ring + (z & 3) * (HY * HX),
+                             ring + ((z + 1) & 3) * (HY * HX), ty, tx, gk, Gax, Gdi, F);
+            D.zo[0] = (int)((z - 1) * plane);
+            D.zo[1] = (int)(z * plane);
+            D.zo[2] = (int)((z + 1) * plane);
+            D.bot = z - 1 == 0;
+            D.top = z + 1 == nz - 1;
+            collide_store<S, false, kTauOne>(rc, jc, vc, F, tau, itau, ref, dst, L, gx, gy, D, mc, clk);
+        }
+#pragma unroll
+        for (int a = 0; a < 2; ++a) {
+            rc[a] = rn[a];
+            mc[a] = mn[a];
+#pragma unroll
+            for (int d = 0; d < 3; ++d) jc[a][d] = jn[a][d];
+            if constexpr (!kTauOne) {
+#pragma unroll
+                for (int k = 0; k < Q; ++k) vc[a][k] = vn[a][k];
+            }
+        }
+    }
+    g += np;
+    return true;
+}
+
+template <class S, int TY, int NS, bool kTauOne>
+__global__ void __launch_bounds__(32 * TY, (kTmaCtas<S, TY, kTauOne>))
+    step_tma_kernel(const __grid_constant__ TmaMaps maps, const StepArgs<S> A)
+{
+    using G = TmaGeom<S, TY>;
+    static_assert(G::STAGE_BYTES % 128 == 0 && (G::XL * sizeof(S)) % 128 == 0 && (G::YS * sizeof(S)) % 128 == 0 &&
+                      (G::CL * sizeof(S)) % 128 == 0 && (G::CR * sizeof(S)) % 128 == 0,
+                  "stages and their regions stay 128-byte aligned");
+    static_assert((2 * G::BX * sizeof(S)) % 16 == 0 && (2 * G::SX * sizeof(S)) % 16 == 0,
+                  "box rows are whole 16-byte units");
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
+    S* stages = (S*)base;
+    float* sp = (float*)(base + (size_t)NS * G::STAGE_BYTES);  // psi ring [4][HY][HX] of pairs (psi^b, psi^r)
+    uint64_t* bar = (uint64_t*)(sp + G::PSI_FLOATS);
+    if (threadIdx.x == 0) {
         for (int s = 0; s < NS; ++s) mbar_init(&bar[s], 1);
         mbar_fence_init();
     }
@@ -164,244 +398,61 @@ __global__ void __launch_bounds__(32 * TY, (kTmaCtas<S, TY, kTauOne>))
     uint32_t g = 0;  // planes this CTA has issued and consumed so far
     uint32_t clk = 0;
     if constexpr (Codec<S>::kDeviation) clk = clock_read(A.clock);
-    bool failed = false;
-
+    const int ncol = A.tiles_x * A.tiles_y;
+    const int nzf = A.zhi - A.zlo;
     for (int item = blockIdx.x; item < ncol * A.nseg; item += gridDim.x) {
         const int col = item % ncol, seg = item / ncol;
         const int za = A.zlo + (int)((long long)seg * nzf / A.nseg);
         const int zb = A.zlo + (int)((long long)(seg + 1) * nzf / A.nseg);
         if (za >= zb) continue;
-        // rows [y0, y0 + hgt) of an even split of ny (hgt <= TY); a row past hgt is an idle warp
-        const int tyi = col / A.tiles_x;
-        const int x0 = (col - tyi * A.tiles_x) * TX;
-        const int y0 = tile_row(tyi, ny, A.tiles_y), hgt = tile_row(tyi + 1, ny, A.tiles_y) - y0;
-        const int gx = x0 + tx, gy = y0 + ty;
-        const bool active = ty < hgt;
-        const bool valid = active && gx < nx;
-        const int np = zb - za + 2;  // planes za-1 .. zb
-        // x edges: the periodic images come from the strips (column of x = nx - 1 in the left strip)
-        const bool left_edge = x0 == 0, right_edge = x0 + TX >= nx;
-        // the box's column of node x0: GX (16 bytes of ring columns on each
-        // side); an edge tile takes its outer ring column from a strip, so its
-        // box is shifted inward and reads no padding columns beyond the lattice
-        // (0 at the left edge, 2 GX at the right edge)
-        const int cofs = left_edge ? 0 : (right_edge ? 2 * GX : GX);
-        const int sl = (L.gx + nx - 1) / SX * SX, ol = L.gx + nx - 1 - sl;
-        // y edges: the row window of the box, given by the box row of node row
-        // y0 (rofs). A middle tile's box holds rows y0 - 1 .. y0 + TY; the first
-        // row of tiles' rows 0 .. HY - 1 and the last row's the HY rows ending at
-        // its last own row, the ring row across the boundary coming from the
-        // y-edge row (ys, with its corner pieces). With a single row of tiles
-        // (ny <= TY) the box holds every row and the ring rows wrap inside it.
-        const bool single = A.tiles_y == 1;
-        const bool first = tyi == 0 && !single, last = tyi == A.tiles_y - 1 && !single;
-        const int rofs = (first || single) ? 0 : (last ? HY - hgt : 1);
-        const int yrow = first ? ny - 1 : 0;  // the real row in ys (first or last row of tiles)
-        // own node: the main box; lanes past x = nx - 1 of a ragged last tile
-        // hold the periodic images x - nx from the right strip (the one at
-        // x = nx is the +x neighbour of x = nx - 1), as far as the strip reaches
-        const bool own_strip = gx >= nx;
-        const bool own_rd = active && gx - nx < SX;
-        const int own_off = own_strip ? G::XR + 2 * ((ty + rofs) * SX + gx - nx) : 2 * ((ty + rofs) * BX + tx + cofs);
-        // the copies' coordinates: x of the main box and of the left strip in
-        // values (two per node; 16-byte aligned, as the copy requires), storage
-        // row (real row + 1) of the box's first row and of the y-edge row (-1: none)
-        const int xb = 2 * (x0 + L.gx - cofs), xs = 2 * sl;
-        const int yb = y0 - rofs + 1, ysr = (first || last) ? yrow + 1 : -1;
-
-        // ring items (one per ring node, both components): shared-memory
-        // position, stage position of the node's slot-0 pair, and its region's
-        // slot stride: 0 main box (2 HY BX), 1 x strip (2 HY SX), 2 y-edge row
-        // (2 BX), 3 corner piece (2 SX)
-        int it_sm[NIT], it_base[NIT], it_cls[NIT];
-        bool it_on[NIT];
-#pragma unroll
-        for (int i = 0; i < NIT; ++i) {
-            const int r = tid + i * NT;
-            it_on[i] = false;
-            it_cls[i] = 0;
-            if (r < RING) {
-                int ix, iy;
-                if (r < HX) { ix = r; iy = 0; }
-                else if (r < 2 * HX) { ix = r - HX; iy = hgt + 1; }
-                else if (r < 2 * HX + TY) { ix = 0; iy = r - 2 * HX + 1; }
-                else { ix = HX - 1; iy = r - 2 * HX - TY + 1; }
-                it_on[i] = r < 2 * HX || iy <= hgt;  // side columns: the tile's own rows only
-                it_sm[i] = iy * HX + ix;
-                const int xr = x0 - 1 + ix, yr = y0 - 1 + iy;  // the ring node (unwrapped)
-                const bool across = (first && yr < 0) || (last && yr >= ny);  // in the y-edge row
-                const int row = wrapi(yr, ny) - y0 + rofs;                   // box row otherwise
-                if (xr < 0) {  // x = -1: the image of x = nx - 1
-                    it_cls[i] = across ? 3 : 1;
-                    it_base[i] = across ? G::CL + 2 * ol : G::XL + 2 * (row * SX + ol);
-                } else if (xr >= nx && xr - nx < SX) {  // x >= nx: the images of x - nx
-                    it_cls[i] = across ? 3 : 1;
-                    it_base[i] = across ? G::CR + 2 * (xr - nx) : G::XR + 2 * (row * SX + xr - nx);
-                } else {
-                    it_cls[i] = across ? 2 : 0;
-                    it_base[i] = across ? G::YS + 2 * (ix - 1 + cofs) : 2 * (row * BX + ix - 1 + cofs);
-                }
-            }
-        }
-
-        auto issue = [&](int zp, uint32_t gi) {
-            uint64_t* b = &bar[gi % NS];
-            if (zp == 0 || zp == nz - 1) {
-                mbar_arrive(b);  // a solid plane: nothing to load
-            } else {
-                S* stg = stages + (size_t)(gi % NS) * G::STAGE_ELEMS;
-                const bool ye = ysr >= 0;
-                fence_proxy_async();
-                mbar_expect_tx(b, G::MAIN_BYTES + (left_edge ? G::XS_BYTES : 0u) + (right_edge ? G::XS_BYTES : 0u) +
-                                      (ye ? G::YS_BYTES + (left_edge ? G::CS_BYTES : 0u) +
-                                                (right_edge ? G::CS_BYTES : 0u)
-                                          : 0u));
-                tma_load_4d(stg, &maps.m[0], b, xb, yb, zp, 0);
-                if (left_edge) tma_load_4d(stg + G::XL, &maps.m[1], b, xs, yb, zp, 0);
-                if (right_edge) tma_load_4d(stg + G::XR, &maps.m[1], b, 2 * L.gx, yb, zp, 0);
-                if (ye) {
-                    tma_load_4d(stg + G::YS, &maps.m[2], b, xb, ysr, zp, 0);
-                    if (left_edge) tma_load_4d(stg + G::CL, &maps.m[3], b, xs, ysr, zp, 0);
-                    if (right_edge) tma_load_4d(stg + G::CR, &maps.m[3], b, 2 * L.gx, ysr, zp, 0);
-                }
-            }
-        };
-
-        // wait for plane i of the item, reduce it to psi (tile + ring) and own
-        // moments, then refill its stage with plane i + NS
-        auto consume = [&](int i, float (&rho)[2], float (&j)[2][3], float (&v)[2][Q], float (&m)[2]) -> bool {
-            const int zp = za - 1 + i;
-            const uint32_t gi = g + i;
-            const bool ok = mbar_wait(&bar[gi % NS], (gi / NS) & 1u);
-            float2* spl = (float2*)sp + (zp & 3) * (HY * HX);
-            const bool solid = zp == 0 || zp == nz - 1;
-            if (ok) {
-                const S* st = stages + (size_t)(gi % NS) * G::STAGE_ELEMS;
-                float ps[2] = {eta[0], eta[1]};
-                rho[0] = rho[1] = m[0] = m[1] = 0.f;
-#pragma unroll
-                for (int a = 0; a < 2; ++a) j[a][0] = j[a][1] = j[a][2] = 0.f;
-                if (!solid && own_rd) {
-                    float w[2][Q];
-                    // both components of velocity k in one shared-memory load
-                    const P2* so = (const P2*)(st + own_off);
-                    if (!own_strip) {
-#pragma unroll
-                        for (int k = 0; k < Q; ++k) {
-                            const float2 t = Codec<S>::val2(so[k * HY * BX]);
-                            w[0][k] = t.x;
-                            w[1][k] = t.y;
-                        }
-                    } else {
-#pragma unroll
-                        for (int k = 0; k < Q; ++k) {
-                            const float2 t = Codec<S>::val2(so[k * HY * SX]);
-                            w[0][k] = t.x;
-                            w[1][k] = t.y;
-                        }
-                    }
-                    moments2<S>(w, ref, rho, j, m);
-                    const float2 p2 = psi2_of(f2(rho[0], rho[1]));
-                    ps[0] = p2.x;
-                    ps[1] = p2.y;
-                    if constexpr (!kTauOne) {
-#pragma unroll
-                        for (int a = 0; a < 2; ++a)
-#pragma unroll
-                            for (int k = 0; k < Q; ++k) v[a][k] = w[a][k];
-                    }
-                }
-                if (active) {
-                    spl[(ty + 1) * HX + tx + 1] = psi_pair(ps[0], ps[1]);
-                }
-#pragma unroll
-                for (int q = 0; q < NIT; ++q) {
-                    if (!it_on[q]) continue;
-                    float2 pr = f2(eta[0], eta[1]);
-                    if (!solid) {
-                        // both components of velocity k in one shared-memory load
-                        float2 w[Q];
-                        const P2* si = (const P2*)(st + it_base[q]);
-                        const int cls = it_cls[q];
-                        if (cls == 0) {
-#pragma unroll
-                            for (int k = 0; k < Q; ++k) w[k] = Codec<S>::val2(si[k * HY * BX]);
-                        } else if (cls == 1) {
-#pragma unroll
-                            for (int k = 0; k < Q; ++k) w[k] = Codec<S>::val2(si[k * HY * SX]);
-                        } else if (cls == 2) {
-#pragma unroll
-                            for (int k = 0; k < Q; ++k) w[k] = Codec<S>::val2(si[k * BX]);
-                        } else {
-#pragma unroll
-                            for (int k = 0; k < Q; ++k) w[k] = Codec<S>::val2(si[k * SX]);
-                        }
-                        float2 unused;
-                        pr = psi2_of(rho2_of<S>(w, f2(ref[0], ref[1]), unused));
-                    }
-                    spl[it_sm[q]] = psi_pair(pr.x, pr.y);
-                }
-            }
-            const bool bad = __syncthreads_or(!ok);
-            if (bad) {
-                if (tid == 0) {
-                    atomicOr(A.err, kErrWait);
-                    for (int k2 = i; k2 < np && k2 < i + NS; ++k2) mbar_wait(&bar[(g + k2) % NS], ((g + k2) / NS) & 1u);
-                }
-                return false;
-            }
-            if (tid == 0 && i + NS < np) issue(zp + NS, gi + NS);
-            return true;
-        };
-
-        float rc[2], jc[2][3], vc[2][Q], mc[2];
-        float rn[2], jn[2][3], vn[2][Q], mn[2];
-        __syncthreads();  // the previous item's collide is done with the psi ring
-        if (tid == 0)
-            for (int i = 0; i < NS && i < np; ++i) issue(za - 1 + i, g + i);
-        if (!consume(0, rn, jn, vn, mn) || !consume(1, rc, jc, vc, mc)) {
-            failed = true;
-            break;
-        }
-
-        Dest D;
-        D.set_column(L, valid ? gx : 0, valid ? gy : 0);
-        D.err = A.err;
-        D.hoff = A.hkey;
-
-        for (int z = za; z < zb; ++z) {
-            if (!consume(z - za + 2, rn, jn, vn, mn)) {
-                failed = true;
-                break;
-            }
-            if (valid) {
-                float F[2][3];
-                const float2* ring = (const float2*)sp;
-                sc_force<HX, HY>(ring + ((z - 1) & 3) * (HY * HX), ring + (z & 3) * (HY * HX),
-                                 ring + ((z + 1) & 3) * (HY * HX), ty, tx, gk, Gax, Gdi, F);
-                D.zo[0] = (int)((z - 1) * plane);
-                D.zo[1] = (int)(z * plane);
-                D.zo[2] = (int)((z + 1) * plane);
-                D.bot = z - 1 == 0;
-                D.top = z + 1 == nz - 1;
-                collide_store<S, false, kTauOne>(rc, jc, vc, F, tau, itau, ref, dst, L, gx, gy, D, mc, clk);
-            }
-#pragma unroll
-            for (int a = 0; a < 2; ++a) {
-                rc[a] = rn[a];
-                mc[a] = mn[a];
-#pragma unroll
-                for (int d = 0; d < 3; ++d) jc[a][d] = jn[a][d];
-                if constexpr (!kTauOne) {
-#pragma unroll
-                    for (int k = 0; k < Q; ++k) vc[a][k] = vn[a][k];
-                }
-            }
-        }
-        if (failed) break;
-        g += np;
+        if (!tma_item<S, TY, NS, kTauOne>(maps, A, col, za, zb, stages, sp, bar, g, clk)) break;
     }
     if constexpr (Codec<S>::kDeviation) clock_tick(A.clock);
+}
+
+// Batched TMA step: a persistent grid walks a work list of (box, tile column,
+// first plane, end plane) items over many planar-wall lattices with their own
+// sizes and parameters; args[2 box + parity] and maps[2 box + parity] describe
+// box `box` for this step (the maps live in global memory, written by the host
+// before the launch). The last CTA out advances every box's step counter.
+template <class S, int TY, int NS, bool kTauOne>
+__global__ void __launch_bounds__(32 * TY, (kTmaCtas<S, TY, kTauOne>))
+    batch_tma_kernel(const TmaMaps* __restrict__ maps, const StepArgs<S>* __restrict__ args,
+                     const int4* __restrict__ items, int nitems, int parity, int nbox, uint32_t* done)
+{
+    using G = TmaGeom<S, TY>;
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
+    S* stages = (S*)base;
+    float* sp = (float*)(base + (size_t)NS * G::STAGE_BYTES);
+    uint64_t* bar = (uint64_t*)(sp + G::PSI_FLOATS);
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < NS; ++s) mbar_init(&bar[s], 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    uint32_t g = 0;
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const int4 w = items[it];
+        const StepArgs<S>& A = args[2 * w.x + parity];
+        const TmaMaps& M = maps[2 * w.x + parity];
+        if (threadIdx.x == 0)
+            for (int i = 0; i < 4; ++i)  // the maps were written through the generic proxy
+                asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&M.m[i]) : "memory");
+        uint32_t clk = 0;
+        if constexpr (Codec<S>::kDeviation) clk = clock_read(A.clock);
+        if (!tma_item<S, TY, NS, kTauOne>(M, A, w.y, w.z, w.w, stages, sp, bar, g, clk)) break;
+    }
+    if constexpr (Codec<S>::kDeviation) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            if (atomicAdd(done, 1u) == gridDim.x - 1) {
+                atomicExch(done, 0u);
+                for (int b = 0; b < nbox; ++b) atomicAdd(args[2 * b].clock, 1u);
+            }
+        }
+    }
 }
 
 template <class S, int TY, int NS, bool T1>
@@ -459,6 +510,43 @@ static long long tma_dispatch(int op, int ty, int ns, bool t1, const CUtensorMap
         LBSC_TMA_CASE(16, 2)
     }
 #undef LBSC_TMA_CASE
+    return op == 2 ? 0 : (long long)cudaErrorInvalidValue;
+}
+
+// The batched TMA kernel for one stage and 4- or 8-row tiles: op 0 launches
+// on `grid` CTAs (returns a cudaError_t), op 1 sets the shared-memory
+// attribute, op 2 returns resident CTAs per SM (0 if not built).
+template <class S, int TY, bool T1>
+static long long tma_batch_one(int op, const TmaMaps* maps, const StepArgs<S>* args, const int4* items, int nitems,
+                               int parity, int nbox, uint32_t* done, int grid, cudaStream_t st)
+{
+    const size_t smem = TmaGeom<S, TY>::smem(1);
+    if (op == 0) {
+        batch_tma_kernel<S, TY, 1, T1><<<grid, 32 * TY, smem, st>>>(maps, args, items, nitems, parity, nbox, done);
+        return cudaGetLastError();
+    }
+    if (op == 1)
+        return cudaFuncSetAttribute(batch_tma_kernel<S, TY, 1, T1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem);
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_tma_kernel<S, TY, 1, T1>, 32 * TY, smem) !=
+        cudaSuccess)
+        return 0;
+    return n;
+}
+
+template <class S>
+static long long tma_batch_dispatch(int op, int ty, bool t1, const void* maps, const StepArgs<S>* args,
+                                    const int4* items, int nitems, int parity, int nbox, uint32_t* done, int grid,
+                                    cudaStream_t st)
+{
+    const TmaMaps* m = (const TmaMaps*)maps;
+    if (ty == 4)
+        return t1 ? tma_batch_one<S, 4, true>(op, m, args, items, nitems, parity, nbox, done, grid, st)
+                  : tma_batch_one<S, 4, false>(op, m, args, items, nitems, parity, nbox, done, grid, st);
+    if (ty == 8)
+        return t1 ? tma_batch_one<S, 8, true>(op, m, args, items, nitems, parity, nbox, done, grid, st)
+                  : tma_batch_one<S, 8, false>(op, m, args, items, nitems, parity, nbox, done, grid, st);
     return op == 2 ? 0 : (long long)cudaErrorInvalidValue;
 }
 

@@ -10,6 +10,14 @@ long long tma_step<float>(int op, int tile_y, int stages, bool tau_one, const CU
     return tma_dispatch<float>(op, tile_y, stages, tau_one, map, args, stream);
 }
 
+template <>
+long long tma_batch<float>(int op, int tile_y, bool tau_one, const void* maps, const StepArgs<float>* args,
+                        const int4* items, int nitems, int parity, int nbox, uint32_t* done, int grid,
+                        cudaStream_t stream)
+{
+    return tma_batch_dispatch<float>(op, tile_y, tau_one, maps, args, items, nitems, parity, nbox, done, grid, stream);
+}
+
 }  // namespace lbsc
 
 namespace lbsc {

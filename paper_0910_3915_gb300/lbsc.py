@@ -128,6 +128,7 @@ SIGNATURES = [
     ("lb_batch_create", _I, [ctypes.POINTER(_VP), _I, ctypes.POINTER(_I), _DP, _DP, ctypes.POINTER(lb_params), _I, _VP]),
     ("lb_batch_set_params", _I, [_VP, _I, ctypes.POINTER(lb_params)]),
     ("lb_batch_set_schedule", _I, [_VP, _I, _I, _I]),
+    ("lb_batch_set_step_variant", _I, [_VP, _I]),
     ("lb_batch_step", _I, [_VP, _I]),
     ("lb_batch_box", _I, [_VP, _I, ctypes.POINTER(_VP)]),
     ("lb_batch_conservation", _I, [_VP, _DP]),
@@ -467,6 +468,12 @@ class Batch:
 
     def set_schedule(self, tile_y: int = 8, planes_per_item: int = 32, ctas_per_sm: int = 0) -> "Batch":
         _bcheck(load().lb_batch_set_schedule(self._b, tile_y, planes_per_item, ctas_per_sm), self._b)
+        return self
+
+    def set_step_variant(self, variant: str = "auto") -> "Batch":
+        """"auto"/"tma": the TMA-staged persistent kernel (4- or 8-row tiles),
+        "ldg": the load-from-global one; both give identical results."""
+        _bcheck(load().lb_batch_set_step_variant(self._b, STEP_VARIANTS[variant]), self._b)
         return self
 
     def set_params(self, i: int, params: Params) -> "Batch":

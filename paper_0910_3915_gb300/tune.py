@@ -137,20 +137,22 @@ def tune(lat, steps: int = 128, segments=SEGMENTS, cache: str | None = None, fin
     return best, timings
 
 
-BATCH_CANDIDATES = ((8, 32), (8, 16), (4, 32), (16, 32), (8, 64))  # (tile height, planes per work item)
+# (kernel variant, tile height, planes per work item)
+BATCH_CANDIDATES = (("tma", 4, 32), ("tma", 4, 16), ("tma", 4, 64), ("tma", 8, 32), ("tma", 8, 16),
+                    ("ldg", 8, 32), ("ldg", 8, 16), ("ldg", 4, 32), ("ldg", 16, 32))
 
 
 def tune_batch(batch, steps: int = 64, candidates=BATCH_CANDIDATES):
-    """Pick the fastest (tile_y, planes_per_item) for a Batch's persistent
-    kernel by timing each on the batch itself; every box's state (and step
-    count) is saved before and restored after. Returns (best, table)."""
+    """Pick the fastest (variant, tile_y, planes_per_item) for a Batch's
+    persistent kernel by timing each on the batch itself; every box's state
+    (and step count) is saved before and restored after. Returns (best, table)."""
     import torch
 
     saved = [batch.box(i).save() for i in range(batch.n)]
     stream = torch.cuda.current_stream()
     table = {}
-    for ty, planes in candidates:
-        batch.set_schedule(ty, planes)
+    for variant, ty, planes in candidates:
+        batch.set_step_variant(variant).set_schedule(ty, planes)
         batch.step(steps)  # warm-up, graph capture
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
@@ -159,10 +161,11 @@ def tune_batch(batch, steps: int = 64, candidates=BATCH_CANDIDATES):
         batch.step(steps)
         e1.record(stream)
         e1.synchronize()
-        table[f"{ty}:{planes}"] = e0.elapsed_time(e1) / steps
+        table[f"{variant}:{ty}:{planes}"] = e0.elapsed_time(e1) / steps
     for i, st in enumerate(saved):
         batch.box(i).load(st)
     best_key = min(table, key=table.get)
-    best = tuple(int(v) for v in best_key.split(":"))
-    batch.set_schedule(*best)
+    v, ty, planes = best_key.split(":")
+    best = (v, int(ty), int(planes))
+    batch.set_step_variant(v).set_schedule(best[1], best[2])
     return best, table

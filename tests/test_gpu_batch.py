@@ -30,10 +30,13 @@ def _boxes(n=6, edges=(24, 33, 40, 48), seed=3):
     return boxes, fields, params
 
 
+@pytest.mark.parametrize("variant", ["auto", "ldg"])
 @pytest.mark.parametrize("precision", ["f32", "f16", "bf16"])
-def test_batch_equals_individual_lattices_bitwise(lbsc, precision):
+def test_batch_equals_individual_lattices_bitwise(lbsc, precision, variant):
+    """The TMA-staged batch kernel (auto) and the load-from-global one, for
+    each storage precision, against each box stepped alone."""
     boxes, fields, params = _boxes()
-    batch = lbsc.Batch(fields, [lbsc.Params(**p) for p in params], precision)
+    batch = lbsc.Batch(fields, [lbsc.Params(**p) for p in params], precision).set_step_variant(variant)
     batch.step(70)  # two graph replays of 32 steps plus 6 single launches
     for i, ((rr, rb), p) in enumerate(zip(fields, params)):
         lat = lbsc.Lattice(rr, rb, precision).set_params(**p)
@@ -51,11 +54,15 @@ def test_batch_schedules_agree_and_match_oracle(lbsc):
     boxes, fields, params = _boxes(n=4, edges=(20, 27), seed=5)
     a = lbsc.Batch(fields, [lbsc.Params(**p) for p in params])
     b = lbsc.Batch(fields, [lbsc.Params(**p) for p in params]).set_schedule(4, 7, 1)
+    c = lbsc.Batch(fields, [lbsc.Params(**p) for p in params]).set_step_variant("ldg").set_schedule(16, 40)
     a.step(100)
     b.step(100)
+    c.step(100)
     for i in range(len(boxes)):
-        ra, rb_ = a.box(i).moments()[:2], b.box(i).moments()[:2]
+        ra, rb_, rc = a.box(i).moments()[:2], b.box(i).moments()[:2], c.box(i).moments()[:2]
         assert np.array_equal(ra[0], rb_[0]) and np.array_equal(ra[1], rb_[1])
+        assert np.array_equal(ra[0], rc[0]) and np.array_equal(ra[1], rc[1])
+    c.close()
     i = 1
     e = boxes[i].edge
     solid = W.wall_mask(e, e, e)
