@@ -48,7 +48,7 @@ WORKLOADS = {
     # z-slab decomposition with a halo exchange every step. One process: the 128^3 droplet as 2 slabs on one
     # GPU (the exchange's cost against the single lattice). Under torchrun: one slab of 126 fluid planes per
     # rank, a 128 x 128 x (126 N + 2) lattice with the droplet on its bottom wall (NCCL messages, weak scaling)
-    "slabs": dict(dims=(128, 128, 128), radius=30.0, precision="f32", w=0.05, nslab=2, schedule=(8, 19, 4)),
+    "slabs": dict(dims=(128, 128, 128), radius=30.0, precision="f32", w=0.05, nslab=2, schedule=(4, 38, 4)),
     "sizes": dict(edges=(32, 64, 128, 256), radius_frac=30.0 / 128.0, precision="f32", steps=20000,
                   w=(0.03, 0.06, 0.09)),
     # the paper's own parameter set (Sec. 4): g = 0.16, W36 weights at force scale 1, a one-sided wall
@@ -564,8 +564,7 @@ def run_slabs(args):
     single = None
     if ws == 1:
         dec.close()
-        # the same load-from-global kernel as the slabs (a slab context never takes the TMA kernel)
-        lat = lbsc.Lattice(rr, rb, prec).set_params(**prm).set_step_variant("ldg").set_tiling(ty, nty, seg)
+        lat = lbsc.Lattice(rr, rb, prec).set_params(**prm).set_tiling(ty, nty, seg)
         lat.step(Wm)
         torch.cuda.synchronize()
         t0.record(stream)

@@ -366,7 +366,7 @@ int lb_set_tiling(lb_ctx* ctx, int tile_y, int y_tiles, int z_segments);
  * (1, 2 or 3; 0 = automatic: 1 for LB_STEP_AUTO, else 3, else 2). One stage
  * leaves room for more resident CTAs per SM (measured the fastest on GB300).
  * Every variant computes bit-identical results. LB_STEP_AUTO and LB_STEP_TMA
- * with a non-planar geometry, a z slab, or a (tile height, stages) pair that
+ * with a non-planar geometry, or a (tile height, stages) pair that
  * is not built for the precision, fall back to LB_STEP_LDG. */
 int lb_set_step_variant(lb_ctx* ctx, int variant, int stages);
 

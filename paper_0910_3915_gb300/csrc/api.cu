@@ -224,9 +224,9 @@ static cudaError_t tma_prepare(lb_ctx* c)
 // stages used by the TMA kernel for the current schedule, 0 if not available
 static int tma_stages(lb_ctx* c)
 {
-    // general geometry and z slabs always load from global; AUTO takes the
-    // TMA kernel with one stage (measured the faster one for both precisions)
-    if (c->general || c->halo || c->variant == LB_STEP_LDG) return 0;
+    // general geometry always loads from global; AUTO takes the TMA kernel
+    // with one stage (measured the faster one for both precisions)
+    if (c->general || c->variant == LB_STEP_LDG) return 0;
     const int s0 = c->variant == LB_STEP_AUTO ? 1 : 3, s1 = c->variant == LB_STEP_AUTO ? 1 : 2;
     const int want[2] = {c->stages ? c->stages : s0, c->stages ? c->stages : s1};
     for (int ns : want) {

@@ -225,8 +225,8 @@ __device__ __forceinline__ bool tma_item(const TmaMaps& maps, const StepArgs<S>&
 
     auto issue = [&](int zp, uint32_t gi) {
         uint64_t* b = &bar[gi % NS];
-        if (zp == 0 || zp == nz - 1) {
-            mbar_arrive(b);  // a solid plane: nothing to load
+        if ((zp == 0 && !(A.halo & 1)) || (zp == nz - 1 && !(A.halo & 2))) {
+            mbar_arrive(b);  // a wall plane: nothing to load (a z slab's halo plane is loaded like fluid)
         } else {
             S* stg = stages + (size_t)(gi % NS) * G::STAGE_ELEMS;
             const bool ye = ysr >= 0;
@@ -253,7 +253,7 @@ __device__ __forceinline__ bool tma_item(const TmaMaps& maps, const StepArgs<S>&
         const uint32_t gi = g + i;
         const bool ok = mbar_wait(&bar[gi % NS], (gi / NS) & 1u);
         float2* spl = (float2*)sp + (zp & 3) * (HY * HX);
-        const bool solid = zp == 0 || zp == nz - 1;
+        const bool solid = (zp == 0 && !(A.halo & 1)) || (zp == nz - 1 && !(A.halo & 2));
         if (ok) {
             const S* st = stages + (size_t)(gi % NS) * G::STAGE_ELEMS;
             float ps[2] = {eta[0], eta[1]};
@@ -355,8 +355,8 @@ __device__ __forceinline__ bool tma_item(const TmaMaps& maps, const StepArgs<S>&
             D.zo[0] = (int)((z - 1) * plane);
             D.zo[1] = (int)(z * plane);
             D.zo[2] = (int)((z + 1) * plane);
-            D.bot = z - 1 == 0;
-            D.top = z + 1 == nz - 1;
+            D.bot = z - 1 == 0 && !(A.halo & 1);  // a halo plane takes pushes like fluid
+            D.top = z + 1 == nz - 1 && !(A.halo & 2);
             collide_store<S, false, kTauOne>(rc, jc, vc, F, tau, itau, ref, dst, L, gx, gy, D, mc, clk);
         }
 #pragma unroll
