@@ -85,7 +85,7 @@ def parse():
                     help="precision workloads: skip the accuracy runs against FP32 and the oracle")
     ap.add_argument("--schedule", default=None,
                     help="fixed step schedule variant:stages:tile_y:z_segments[:y_tiles] (e.g. ldg:0:8:4:19); "
-                         "skips tuning")
+                         "for --workload sweep variant:tile_y:planes_per_item (e.g. tma:4:16); skips tuning")
     return ap.parse_args()
 
 
@@ -431,7 +431,12 @@ def run_sweep(args):
     from paper_0910_3915_gb300 import tune
 
     batch = lbsc.Batch(fields, params, wl["precision"])
-    best, _ = tune.tune_batch(batch)
+    if args.schedule:  # 'variant:tile_y:planes_per_item', e.g. tma:4:16
+        v, ty, planes = args.schedule.split(":")
+        best = (v, int(ty), int(planes))
+        batch.set_step_variant(v).set_schedule(best[1], best[2])
+    else:
+        best, _ = tune.tune_batch(batch)
     batch.step(Wm)
     torch.cuda.synchronize()
     replicas.barrier()
