@@ -43,18 +43,18 @@ __device__ __forceinline__ void block_reduce(double (&acc)[NV], uint32_t is_max,
     }
 }
 
-// Sum (or max) nrows partial rows of NV values: warp v reduces value v, lane
-// l taking rows l, l + 32, ... in order, then a fixed shuffle tree. Launched
-// as one block of 32 NV threads.
+// Sum (or max) nrows partial rows of NV values: block v reduces value v,
+// thread t taking rows t, t + 256, ... in order, then a fixed shuffle tree per
+// warp and the warps in order. Launched as NV blocks of 256 threads.
 template <int NV>
-__global__ void finish_rows_kernel(const double* __restrict__ part, int nrows, uint32_t is_max, double* __restrict__ out)
+__global__ void __launch_bounds__(256) finish_rows_kernel(const double* __restrict__ part, int nrows, uint32_t is_max,
+                                                          double* __restrict__ out)
 {
-    const int v = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int v = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (v >= NV) return;
     const bool mx = (is_max >> v) & 1u;
     double a = mx ? -1e300 : 0.0;
-#pragma unroll 4
-    for (int r = lane; r < nrows; r += 32) {
+    for (int r = threadIdx.x; r < nrows; r += blockDim.x) {
         const double p = part[(long long)r * NV + v];
         a = mx ? fmax(a, p) : a + p;
     }
@@ -63,7 +63,14 @@ __global__ void finish_rows_kernel(const double* __restrict__ part, int nrows, u
         const double w = __shfl_down_sync(0xffffffffu, a, o);
         a = mx ? fmax(a, w) : a + w;
     }
-    if (lane == 0) out[v] = a;
+    __shared__ double sw[8];
+    if (lane == 0) sw[warp] = a;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = sw[0];
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) t = mx ? fmax(t, sw[w]) : t + sw[w];
+        out[v] = t;
+    }
 }
 
 // blocks for n items at `threads` per block, at most cap (grid-stride loops cover the rest)
@@ -680,7 +687,20 @@ template <class S>
 cudaError_t launch_conservation(const FieldArgs& F, const S* f, unsigned long long* acc, unsigned int* ticket,
                                 double* out, cudaStream_t st)
 {
-    cons_kernel<S><<<kConsBlocks, kRedThreads, 0, st>>>(F, f, acc, ticket, out);
+    // one wave of resident blocks (a grid-stride loop over the nodes): a partial
+    // last wave of a fixed grid left most SMs idle at the end
+    static int blocks = 0;
+    if (!blocks) {
+        int dev = 0, nsm = 0, occ = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) ==
+                                                      cudaSuccess &&
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, cons_kernel<S>, kRedThreads, 0) == cudaSuccess &&
+            nsm * occ > 0)
+            blocks = nsm * occ < kConsBlocks ? nsm * occ : kConsBlocks;
+        else
+            blocks = kConsBlocks;
+    }
+    cons_kernel<S><<<blocks, kRedThreads, 0, st>>>(F, f, acc, ticket, out);
     return cudaGetLastError();
 }
 
@@ -705,7 +725,7 @@ cudaError_t launch_angle(const FieldArgs& F, const Scratch& W, double zref, doub
                          cudaStream_t st)
 {
     angle_kernel<<<kAngleBlocks, kRedThreads, 0, st>>>(F, W, zref, level, part);
-    finish_rows_kernel<kAngleVals><<<1, 32 * kAngleVals, 0, st>>>(part, kAngleBlocks, kAngleMaxMask, out);
+    finish_rows_kernel<kAngleVals><<<kAngleVals, 256, 0, st>>>(part, kAngleBlocks, kAngleMaxMask, out);
     return cudaGetLastError();
 }
 

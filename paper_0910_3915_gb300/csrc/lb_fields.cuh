@@ -9,7 +9,7 @@ namespace lbsc {
 
 constexpr int kRedThreads = 256;  // threads per reduction block
 constexpr int kRedBlocks = 512;   // fixed grid of the reductions: fixed summation order
-constexpr int kConsBlocks = 2048;   // grid of the conservation sums (enough loads in flight for HBM)
+constexpr int kConsBlocks = 2048;   // most blocks of the conservation sums (one wave of resident blocks is used)
 constexpr int kAngleBlocks = 1216;  // fixed grid of the contact-angle reduction
 constexpr int kAngleVals = 19;    // contact-angle partial sums per block
 constexpr int kPartRows = kConsBlocks > kAngleBlocks ? kConsBlocks : kAngleBlocks;  // rows of the partials area
