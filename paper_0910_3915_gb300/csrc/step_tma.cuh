@@ -192,34 +192,37 @@ __device__ __forceinline__ bool tma_item(const TmaMaps& maps, const StepArgs<S>&
     // position, stage position of the node's slot-0 pair, and its region's
     // slot stride: 0 main box (2 HY BX), 1 x strip (2 HY SX), 2 y-edge row
     // (2 BX), 3 corner piece (2 SX)
-    int it_sm[NIT], it_base[NIT], it_cls[NIT];
-    bool it_on[NIT];
+    // (packed in one word: stage position in bits 0-16, shared-memory position in
+    // bits 17-26, stride class in bits 27-28; -1 for no item)
+    static_assert(G::STAGE_ELEMS <= (1 << 17) && HY * HX <= (1 << 10), "ring item fields fit their bits");
+    int it_code[NIT];
 #pragma unroll
     for (int i = 0; i < NIT; ++i) {
         const int r = tid + i * NT;
-        it_on[i] = false;
-        it_cls[i] = 0;
+        it_code[i] = -1;
         if (r < RING) {
+            int it_sm, it_base, it_cls;
             int ix, iy;
             if (r < HX) { ix = r; iy = 0; }
             else if (r < 2 * HX) { ix = r - HX; iy = hgt + 1; }
             else if (r < 2 * HX + TY) { ix = 0; iy = r - 2 * HX + 1; }
             else { ix = HX - 1; iy = r - 2 * HX - TY + 1; }
-            it_on[i] = r < 2 * HX || iy <= hgt;  // side columns: the tile's own rows only
-            it_sm[i] = iy * HX + ix;
+            const bool on = r < 2 * HX || iy <= hgt;  // side columns: the tile's own rows only
+            it_sm = iy * HX + ix;
             const int xr = x0 - 1 + ix, yr = y0 - 1 + iy;  // the ring node (unwrapped)
             const bool across = (first && yr < 0) || (last && yr >= ny);  // in the y-edge row
             const int row = wrapi(yr, ny) - y0 + rofs;                   // box row otherwise
             if (xr < 0) {  // x = -1: the image of x = nx - 1
-                it_cls[i] = across ? 3 : 1;
-                it_base[i] = across ? G::CL + 2 * ol : G::XL + 2 * (row * SX + ol);
+                it_cls = across ? 3 : 1;
+                it_base = across ? G::CL + 2 * ol : G::XL + 2 * (row * SX + ol);
             } else if (xr >= nx && xr - nx < SX) {  // x >= nx: the images of x - nx
-                it_cls[i] = across ? 3 : 1;
-                it_base[i] = across ? G::CR + 2 * (xr - nx) : G::XR + 2 * (row * SX + xr - nx);
+                it_cls = across ? 3 : 1;
+                it_base = across ? G::CR + 2 * (xr - nx) : G::XR + 2 * (row * SX + xr - nx);
             } else {
-                it_cls[i] = across ? 2 : 0;
-                it_base[i] = across ? G::YS + 2 * (ix - 1 + cofs) : 2 * (row * BX + ix - 1 + cofs);
+                it_cls = across ? 2 : 0;
+                it_base = across ? G::YS + 2 * (ix - 1 + cofs) : 2 * (row * BX + ix - 1 + cofs);
             }
+            if (on) it_code[i] = it_base | (it_sm << 17) | (it_cls << 27);
         }
     }
 
@@ -295,13 +298,15 @@ __device__ __forceinline__ bool tma_item(const TmaMaps& maps, const StepArgs<S>&
             }
 #pragma unroll
             for (int q = 0; q < NIT; ++q) {
-                if (!it_on[q]) continue;
+                const int code = it_code[q];
+                if (code < 0) continue;
+                const int it_sm = (code >> 17) & 0x3FF;
                 float2 pr = f2(eta[0], eta[1]);
                 if (!solid) {
                     // both components of velocity k in one shared-memory load
                     float2 w[Q];
-                    const P2* si = (const P2*)(st + it_base[q]);
-                    const int cls = it_cls[q];
+                    const P2* si = (const P2*)(st + (code & 0x1FFFF));
+                    const int cls = (code >> 27) & 3;
                     if (cls == 0) {
 #pragma unroll
                         for (int k = 0; k < Q; ++k) w[k] = Codec<S>::val2(si[k * HY * BX]);
@@ -318,7 +323,7 @@ __device__ __forceinline__ bool tma_item(const TmaMaps& maps, const StepArgs<S>&
                     float2 unused;
                     pr = psi2_of(rho2_of<S>(w, f2(ref[0], ref[1]), unused));
                 }
-                spl[it_sm[q]] = psi_pair(pr.x, pr.y);
+                spl[it_sm] = psi_pair(pr.x, pr.y);
             }
         }
         const bool bad = __syncthreads_or(!ok);
