@@ -111,18 +111,28 @@ def step_source_sha256() -> str:
 
 
 def step_kernel_traffic(workload: str, schedule: str | None):
-    """Per-launch DRAM bytes of the step kernel under `schedule` from the
-    committed ncu summary, or None when the kernel's sources changed since it
-    was taken or that schedule was not captured."""
+    """(per-launch DRAM bytes of the step kernel, the schedule they were taken
+    under) from the committed ncu summary: `schedule` itself, else a recorded
+    schedule of the same variant, stages and tile height (the z segments and
+    y-tiles move the bytes by the few halo planes only); (None, None) when the
+    kernel's sources changed since it was taken or nothing close was captured."""
     path = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
     try:
         with open(path) as f:
             rec = json.load(f)
         if rec.get("step_sources_sha256") != step_source_sha256() or not schedule:
-            return None
-        return rec.get("bytes_per_launch", {}).get(f"{workload} {schedule}")
+            return None, None
+        table = rec.get("bytes_per_launch", {})
+        if f"{workload} {schedule}" in table:
+            return table[f"{workload} {schedule}"], schedule
+        family = ":".join(schedule.split(":")[:3])
+        for key, val in sorted(table.items()):
+            wl, sched = key.split(" ", 1)
+            if wl == workload and ":".join(sched.split(":")[:3]) == family:
+                return val, sched
+        return None, None
     except Exception:
-        return None
+        return None, None
 
 
 class ClockSampler:
@@ -265,7 +275,7 @@ def run_ours(args):
     elif not args.no_tune:
         schedule, _ = tune.tune(lat)
     lat.step(Wm)
-    lat.contact_angle(5.0)  # warm-up of the measurement kernels too (their first launch loads them)
+    lat.measure(5.0)  # warm-up of the measurement kernels too (their first launch loads them)
     lat.sync()
 
     try:
@@ -292,9 +302,11 @@ def run_ours(args):
         chunks.append((a, b))
         launches += m
         done += m
-        lat.conservation()
-        launches += 2
-    angle = lat.contact_angle(5.0)
+        if done < K:
+            lat.conservation()  # one kernel
+            launches += 1
+    # the last conservation sums and the contact angle in one pass over the populations
+    cons_end, angle = lat.measure(5.0)  # conservation (with phi), angle and finish kernels
     launches += 3
     t1.record(stream)
     torch.cuda.synchronize()
@@ -318,7 +330,7 @@ def run_ours(args):
     if schedule:
         tune.apply(lat2, schedule)
     lat2.step(Wm)
-    lat2.contact_angle(5.0)
+    lat2.measure(5.0)
     torch.cuda.synchronize()
     replicas.barrier()
     te = time.perf_counter()
@@ -327,10 +339,11 @@ def run_ours(args):
     while done < K:
         m = min(CONS_EVERY, K - done)
         lat2.step(m)
-        lat2.conservation()
-        n_cons += 1
         done += m
-    lat2.contact_angle(5.0)
+        n_cons += 1
+        if done < K:
+            lat2.conservation()
+    lat2.measure(5.0)
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - te
     lat2.close()
@@ -347,9 +360,11 @@ def run_ours(args):
     peak, peak_kind = peaks()
     bpl = BYTES_PER_LU[prec]
     achieved = nf * bpl / (step_ms * 1e-3) / 1e9
+    traffic, traffic_sched = step_kernel_traffic(args.workload, tune.name(schedule) if schedule else None)
     roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
             "frac": round(achieved / peak, 4),
-            "traffic": step_kernel_traffic(args.workload, tune.name(schedule) if schedule else None),
+            "traffic": traffic,
+            "traffic_schedule": traffic_sched,
             "peak_source": peak_kind,
             "kernel": "step_tma_kernel" if schedule and schedule[0] == "tma" else "step_kernel",
             "algorithmic_bytes_per_launch": nf * bpl}
@@ -372,7 +387,8 @@ def run_ours(args):
                                  "z_segments": schedule[3],
                                  "y_tiles": schedule[4] or -(-ny // schedule[2])} if schedule else "default"),
                    "l2": "inputs larger than L2 (state %.0f MB, L2 129 MB)" % (nx * ny * nz * bpl / 1e6),
-                   "timed": f"{K} steps + FP64 conservation every {CONS_EVERY} + 1 contact angle"},
+                   "timed": f"{K} steps + FP64 conservation every {CONS_EVERY} + 1 contact angle "
+                            "(the last sums and the angle in one pass)"},
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": {"value": round(e2e, 1), "unit": "MLUPS", "h2d_bytes_per_step": round(h2d / K, 1),

@@ -276,6 +276,15 @@ int lb_contact_angle(lb_ctx* ctx, double offset, lb_droplet* out);
  * maximum |phi|: level = +max(phi)/2 and level = min(phi)/2. */
 int lb_contact_angle_at(lb_ctx* ctx, double offset, double level, lb_droplet* out);
 
+/* The conservation sums (as lb_conservation, into cons[8]) and the droplet's
+ * geometric contact angle at level 0 (as lb_contact_angle, into out) of the
+ * current state, in one read of the populations: the sums' pass also forms
+ * phi = rho_r - rho_b for the angle. The results are those of the two calls
+ * made one after the other. Synchronous. Errors as lb_conservation and
+ * lb_contact_angle (LB_ERR_ARG for NULL arguments or an offset that is
+ * negative or not finite). */
+int lb_measure(lb_ctx* ctx, double cons[8], double offset, lb_droplet* out);
+
 /* ------------------------------------------------------------ pressure tensor and surface tension
  * The pressure tensor of Sec. 4.1 at a fluid node x:
  *   P_ij = sum_a sum_k (c_ki - u_i)(c_kj - u_j) n_k^a

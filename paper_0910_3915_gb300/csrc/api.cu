@@ -785,10 +785,10 @@ int lb_sync(lb_ctx* c)
 }  // extern "C"
 
 template <class S>
-static cudaError_t run_cons(lb_ctx* c)
+static cudaError_t run_cons(lb_ctx* c, float* phi)
 {
     return launch_conservation<S>(field_args(c), (const S*)c->f[c->cur], (unsigned long long*)(c->red + 32),
-                                  (unsigned int*)(c->red + 40), c->red, c->stream);
+                                  (unsigned int*)(c->red + 40), c->red, c->stream, phi);
 }
 template <class S>
 static cudaError_t run_fields(lb_ctx* c, bool vel)
@@ -796,12 +796,12 @@ static cudaError_t run_fields(lb_ctx* c, bool vel)
     return launch_fields<S>(field_args(c), (const S*)c->f[c->cur], c->W, vel, c->stream);
 }
 
-static cudaError_t dispatch_cons(lb_ctx* c)
+static cudaError_t dispatch_cons(lb_ctx* c, float* phi = nullptr)
 {
     switch (c->prec) {
-    case LB_F32: return run_cons<float>(c);
-    case LB_F16: return run_cons<__half>(c);
-    default: return run_cons<__nv_bfloat16>(c);
+    case LB_F32: return run_cons<float>(c, phi);
+    case LB_F16: return run_cons<__half>(c, phi);
+    default: return run_cons<__nv_bfloat16>(c, phi);
     }
 }
 template <class S>
@@ -828,10 +828,11 @@ static cudaError_t dispatch_fields(lb_ctx* c, bool vel)
 
 extern "C" {
 
-int lb_conservation(lb_ctx* c, double cons[8])
+// the conservation sums (and, with phi, the contact angle's phi field) of the
+// current state into cons[8]
+static int conservation_impl(lb_ctx* c, double cons[8], float* phi)
 {
-    if (!c || !cons) return fail(c, LB_ERR_ARG, "lb_conservation: NULL argument");
-    LB_CUDA(c, dispatch_cons(c));
+    LB_CUDA(c, dispatch_cons(c, phi));
     LB_CUDA(c, cudaMemcpyAsync(c->h_red, c->red, 8 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     LB_CUDA(c, cudaStreamSynchronize(c->stream));
     for (int i = 0; i < 7; ++i) cons[i] = c->h_red[i];
@@ -840,6 +841,12 @@ int lb_conservation(lb_ctx* c, double cons[8])
     if (st != LB_OK) return st;
     if (cons[5] > 0) return fail(c, LB_ERR_NAN, "non-finite populations in the state");
     return LB_OK;
+}
+
+int lb_conservation(lb_ctx* c, double cons[8])
+{
+    if (!c || !cons) return fail(c, LB_ERR_ARG, "lb_conservation: NULL argument");
+    return conservation_impl(c, cons, nullptr);
 }
 
 int lb_moments(lb_ctx* c, double* rho_r, double* rho_b, double* u, double cons[8])
@@ -893,15 +900,33 @@ static int solve4(double M[4][4], double v[4], double s[4])
     return 0;
 }
 
+// the droplet of the phi field in c->W (written by the phi pass or the
+// conservation pass of the current state)
+static int angle_from_phi(lb_ctx* c, double offset, double level, lb_droplet* out);
+
 int lb_contact_angle(lb_ctx* c, double offset, lb_droplet* out) { return lb_contact_angle_at(c, offset, 0.0, out); }
 
 int lb_contact_angle_at(lb_ctx* c, double offset, double level, lb_droplet* out)
 {
     if (!c || !out || !(offset >= 0) || !std::isfinite(offset) || !std::isfinite(level))
         return fail(c, LB_ERR_ARG, "lb_contact_angle: bad argument");
+    LB_CUDA(c, dispatch_phi(c));
+    return angle_from_phi(c, offset, level, out);
+}
+
+int lb_measure(lb_ctx* c, double cons[8], double offset, lb_droplet* out)
+{
+    if (!c || !cons || !out || !(offset >= 0) || !std::isfinite(offset))
+        return fail(c, LB_ERR_ARG, "lb_measure: bad argument");
+    const int rc = conservation_impl(c, cons, c->W.rho[0]);
+    if (rc != LB_OK) return rc;
+    return angle_from_phi(c, offset, 0.0, out);
+}
+
+static int angle_from_phi(lb_ctx* c, double offset, double level, lb_droplet* out)
+{
     memset(out, 0, sizeof(*out));
     const double zw = 0.5, zref = zw + offset;
-    LB_CUDA(c, dispatch_phi(c));
     LB_CUDA(c, launch_angle(field_args(c), c->W, zref, level, c->part, c->red, c->stream));
     LB_CUDA(c, cudaMemcpyAsync(c->h_red, c->red, kAngleVals * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     LB_CUDA(c, cudaStreamSynchronize(c->stream));

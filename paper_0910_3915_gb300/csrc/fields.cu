@@ -94,8 +94,10 @@ __device__ __forceinline__ void decode2(const S* p, int k, const float (&ref)[2]
 {
     const float2 v = Codec<S>::load2(p);
     if constexpr (Codec<S>::kDeviation) {
-        n0 = zeta(k) * (ref[0] + v.x);
-        n1 = zeta(k) * (ref[1] + v.y);
+        // explicitly rounded, so that no kernel fuses the product into a later
+        // sum: every readback pass sees the same n_k (and the same rho)
+        n0 = __fmul_rn(zeta(k), __fadd_rn(ref[0], v.x));
+        n1 = __fmul_rn(zeta(k), __fadd_rn(ref[1], v.y));
     } else {
         n0 = v.x;
         n1 = v.y;
@@ -149,24 +151,30 @@ __global__ void init_kernel(FieldArgs F, S* __restrict__ f, const double* __rest
 // the accumulators (acc[0..7], ticket) for the next call.
 __device__ __forceinline__ long long to_fix(float v) { return __float2ll_rn(v * kConsFix); }
 
+// With phi non-NULL the same pass also writes phi = rho_r - rho_b of every
+// node (0 on solid nodes), summed as the contact angle's phi pass sums it, so
+// a measurement of both needs one read of the populations.
 template <class S>
 __global__ void __launch_bounds__(kRedThreads) cons_kernel(FieldArgs F, const S* __restrict__ f,
                                                            unsigned long long* __restrict__ acc,
-                                                           unsigned int* __restrict__ ticket, double* __restrict__ out)
+                                                           unsigned int* __restrict__ ticket, double* __restrict__ out,
+                                                           float* __restrict__ phi)
 {
     float m[2] = {0.f, 0.f}, j[3] = {0.f, 0.f, 0.f};
     int bad = 0, fluid = 0;
     const int nx = F.L.nx, ny = F.L.ny;
-    const int zlo = F.general ? 0 : 1, zhi = F.general ? F.L.nz : F.L.nz - 1;
     const unsigned nxy = (unsigned)nx * (unsigned)ny;
-    const unsigned n = nxy * (unsigned)(zhi - zlo);  // below 2^31 (the layout's limit)
+    const unsigned n = nxy * (unsigned)F.L.nz;  // below 2^31 (the layout's limit)
     const unsigned T = gridDim.x * blockDim.x;
     const float ref[2] = {F.P.ref[0], F.P.ref[1]};
     for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += T) {
         const unsigned zr = i / nxy, rem = i - zr * nxy;
-        const int y = (int)(rem / (unsigned)nx), x = (int)(rem - (unsigned)y * nx), z = zlo + (int)zr;
+        const int y = (int)(rem / (unsigned)nx), x = (int)(rem - (unsigned)y * nx), z = (int)zr;
         const long long off = F.L.off(x, y, z);
-        if (F.general && (F.nbmask[off] & kSelfSolid)) continue;
+        if (node_solid(F, x, y, z, off)) {
+            if (phi) phi[i] = 0.f;
+            continue;
+        }
         ++fluid;
         float v[2][Q];
 #pragma unroll
@@ -179,13 +187,14 @@ __global__ void __launch_bounds__(kRedThreads) cons_kernel(FieldArgs F, const S*
             for (int k = 0; k < Q; ++k) {
                 const float nk = v[a][k];
                 bad += isfinite(nk) ? 0 : 1;
-                s += nk;
+                s = __fadd_rn(s, nk);  // as the phi pass
                 if (cx(k)) jn[0] += cx(k) * nk;
                 if (cy(k)) jn[1] += cy(k) * nk;
                 if (cz(k)) jn[2] += cz(k) * nk;
             }
             rho[a] = s;
         }
+        if (phi) phi[i] = rho[0] - rho[1];
         m[0] += rho[0];
         m[1] += rho[1];
 #pragma unroll
@@ -309,7 +318,7 @@ __global__ void phi_kernel(FieldArgs F, const S* __restrict__ f, Scratch W)
 #pragma unroll
             for (int a = 0; a < 2; ++a)
 #pragma unroll
-                for (int k = 0; k < Q; ++k) rho[a] += v[a][k];
+                for (int k = 0; k < Q; ++k) rho[a] = __fadd_rn(rho[a], v[a][k]);  // as the conservation pass
         }
         W.rho[0][i] = rho[0] - rho[1];
     }
@@ -685,7 +694,7 @@ cudaError_t launch_init(const FieldArgs& F, S* f, const double* rr, const double
 
 template <class S>
 cudaError_t launch_conservation(const FieldArgs& F, const S* f, unsigned long long* acc, unsigned int* ticket,
-                                double* out, cudaStream_t st)
+                                double* out, cudaStream_t st, float* phi)
 {
     // one wave of resident blocks (a grid-stride loop over the nodes): a partial
     // last wave of a fixed grid left most SMs idle at the end
@@ -700,7 +709,7 @@ cudaError_t launch_conservation(const FieldArgs& F, const S* f, unsigned long lo
         else
             blocks = kConsBlocks;
     }
-    cons_kernel<S><<<blocks, kRedThreads, 0, st>>>(F, f, acc, ticket, out);
+    cons_kernel<S><<<blocks, kRedThreads, 0, st>>>(F, f, acc, ticket, out, phi);
     return cudaGetLastError();
 }
 
@@ -774,7 +783,7 @@ cudaError_t launch_pressure_radial(const FieldArgs& F, const void* f, int prec, 
 #define LBSC_INST(S)                                                                                  \
     template cudaError_t launch_init<S>(const FieldArgs&, S*, const double*, const double*, cudaStream_t, int*); \
     template cudaError_t launch_conservation<S>(const FieldArgs&, const S*, unsigned long long*, unsigned int*, \
-                                                double*, cudaStream_t);                                        \
+                                                double*, cudaStream_t, float*);                                \
     template cudaError_t launch_fields<S>(const FieldArgs&, const S*, const Scratch&, bool, cudaStream_t); \
     template cudaError_t launch_phi<S>(const FieldArgs&, const S*, const Scratch&, cudaStream_t);      \
     template cudaError_t launch_get_pop<S>(const FieldArgs&, const S*, double*, cudaStream_t);       \

@@ -89,9 +89,10 @@ cudaError_t launch_init(const FieldArgs& F, S* f, const double* rr, const double
 // FP64 conservation sums into out[0..7] through 64-bit fixed-point accumulators
 // acc[0..6] and a block ticket, both zero between calls (the kernel clears them)
 constexpr float kConsFix = 268435456.0f;  // 2^28: the accumulators' unit is 2^-28
+// phi (optional): also write phi = rho_r - rho_b of every node, as launch_phi does
 template <class S>
 cudaError_t launch_conservation(const FieldArgs& F, const S* f, unsigned long long* acc, unsigned int* ticket,
-                                double* out, cudaStream_t st);
+                                double* out, cudaStream_t st, float* phi = nullptr);
 template <class S>
 cudaError_t launch_fields(const FieldArgs& F, const S* f, const Scratch& W, bool velocity, cudaStream_t st);
 // phi = rho_r - rho_b of every node into W.rho[0] (the contact angle's input)

@@ -109,6 +109,7 @@ SIGNATURES = [
     ("lb_slabs_step", _I, [ctypes.POINTER(_VP), _I, _I]),
     ("lb_contact_angle", _I, [_VP, ctypes.c_double, ctypes.POINTER(lb_droplet)]),
     ("lb_contact_angle_at", _I, [_VP, ctypes.c_double, ctypes.c_double, ctypes.POINTER(lb_droplet)]),
+    ("lb_measure", _I, [_VP, ctypes.POINTER(ctypes.c_double), ctypes.c_double, ctypes.POINTER(lb_droplet)]),
     ("lb_state_bytes", _I, [_VP, ctypes.POINTER(ctypes.c_size_t)]),
     ("lb_save", _I, [_VP, _VP, ctypes.c_size_t]),
     ("lb_load", _I, [_VP, _VP, ctypes.c_size_t]),
@@ -329,6 +330,14 @@ class Lattice:
         d = lb_droplet()
         _check(load().lb_contact_angle_at(self._ctx, float(offset), float(level), ctypes.byref(d)), self._ctx)
         return {f: getattr(d, f) for f, _ in lb_droplet._fields_}
+
+    def measure(self, offset: float = 5.0):
+        """(conservation sums, contact angle at level 0) in one pass over the
+        populations: the results of conservation() and contact_angle(offset)."""
+        cons = np.empty(8)
+        d = lb_droplet()
+        _check(load().lb_measure(self._ctx, _dp(cons), float(offset), ctypes.byref(d)), self._ctx)
+        return cons, {f: getattr(d, f) for f, _ in lb_droplet._fields_}
 
     def pressure_tensor(self) -> np.ndarray:
         """P (6, nz, ny, nx): xx, yy, zz, xy, xz, yz of the pressure tensor (Sec. 4.1)."""

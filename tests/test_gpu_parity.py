@@ -276,6 +276,22 @@ def test_contact_angle_measurement_on_analytic_caps(lbsc):
         assert abs(gl["h"] - g["h"]) > 0.05  # a different surface
 
 
+@pytest.mark.parametrize("precision", ["f32", "bf16"])
+def test_measure_equals_conservation_and_angle(lbsc, precision):
+    """lb_measure (the conservation sums and the contact angle from one pass
+    over the populations) gives exactly what lb_conservation and
+    lb_contact_angle give one after the other, on an evolved droplet."""
+    rr, rb = W.droplet_fields(48, 40, 36, 11.0, seed=2)
+    lat = lbsc.Lattice(rr, rb, precision).set_params(**CONTACT, eta_wall_b=0.04, eta_wall_r=-0.04)
+    lat.step(60)
+    c1 = lat.conservation()
+    d1 = lat.contact_angle(4.0)
+    c2, d2 = lat.measure(4.0)
+    lat.close()
+    assert np.array_equal(c1, c2)
+    assert d1["ok"] == 1 and d1 == d2
+
+
 def test_contact_angle_status_reasons(lbsc):
     """lb_droplet.status says why an angle is missing, and phi_max / phi_min
     give the phase contrast: a cap (ok), a box with no droplet phase, a drop
