@@ -362,11 +362,18 @@ __device__ __forceinline__ bool tma_item(const TmaMaps& maps, const StepArgs<S>&
             D.zo[2] = (int)((z + 1) * plane);
             D.bot = z - 1 == 0 && !(A.halo & 1);  // a halo plane takes pushes like fluid
             D.top = z + 1 == nz - 1 && !(A.halo & 2);
-            collide_store<S, false, kTauOne>(rc, jc, vc, F, tau, itau, ref, dst, L, gx, gy, D, mc, clk);
+            if constexpr (Codec<S>::kDeviation) {
+                // rho = rho_ref + m36 / 36, as moments2 forms it: not held across the plane
+                const float2 r = fma2(f2(mc[0], mc[1]), sp2(1.0f / 36.0f), f2(ref[0], ref[1]));
+                const float rr[2] = {r.x, r.y};
+                collide_store<S, false, kTauOne>(rr, jc, vc, F, tau, itau, ref, dst, L, gx, gy, D, mc, clk);
+            } else {
+                collide_store<S, false, kTauOne>(rc, jc, vc, F, tau, itau, ref, dst, L, gx, gy, D, mc, clk);
+            }
         }
 #pragma unroll
         for (int a = 0; a < 2; ++a) {
-            rc[a] = rn[a];
+            if constexpr (!Codec<S>::kDeviation) rc[a] = rn[a];
             mc[a] = mn[a];
 #pragma unroll
             for (int d = 0; d < 3; ++d) jc[a][d] = jn[a][d];
