@@ -37,7 +37,26 @@ def test_batch_argument_errors_before_cuda(lib):
     assert b.value is None
     assert b"dimensions" in lib.lb_batch_last_error(None) or b"argument" in lib.lb_batch_last_error(None)
     assert lib.lb_batch_step(None, 1) == lbsc.LB_ERR_ARG
+    assert lib.lb_batch_set_step_variant(None, lbsc.LB_STEP_TMA) == lbsc.LB_ERR_ARG
     lib.lb_batch_free(None)
+
+
+def test_measure_and_round_selftest_argument_errors_before_cuda(lib):
+    """lb_measure and lb_selftest_round refuse bad arguments before any CUDA call."""
+    from paper_0910_3915_gb300 import lbsc
+    cons = np.zeros(8)
+    d = lbsc.lb_droplet()
+    dp = cons.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    assert lib.lb_measure(None, dp, 5.0, ctypes.byref(d)) == lbsc.LB_ERR_ARG
+    v = np.zeros(4, np.float32)
+    m = np.zeros(2, np.uint32)
+    out = np.zeros(6, np.uint32)
+    fp = v.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+    up = m.ctypes.data_as(ctypes.POINTER(ctypes.c_uint))
+    op = out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint))
+    assert lib.lb_selftest_round(lbsc.LB_F32, fp, up, 2, op) == lbsc.LB_ERR_ARG  # 16-bit formats only
+    assert lib.lb_selftest_round(lbsc.LB_BF16, fp, up, 0, op) == lbsc.LB_ERR_ARG
+    assert lib.lb_selftest_round(lbsc.LB_BF16, None, up, 2, op) == lbsc.LB_ERR_ARG
 
 
 def test_header_declares_the_boundary():
